@@ -1,0 +1,308 @@
+"""Oracle for the ensemble SSA: TEST INFRASTRUCTURE, not part of the product.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  The CUDA library never does, and this package
+never imports the CUDA library.
+
+``ssa_oracle.cpp`` holds the plain single-threaded FP64 statement of the
+method (Gillespie direct method, Sec. 2; mass-action model format, Sec. 3.2;
+selective memory with average as combining function, Sec. 3.2.1 / Fig. 3).
+This module builds it with g++ (``-O2 -ffp-contract=off``), computes the
+integer constants of its fixed-point logarithm with Python integers, and wraps
+it with numpy.
+
+Pins (see ``tests/test_oracle_*.py``): Philox4x64-10 against numpy's
+independent ``Philox`` bit generator; the logarithm against mpmath and libm;
+the sampler against closed forms (birth-death Poisson law, isomerisation
+binomial law, expected event count), the exact CTMC transient by matrix
+exponential on tiny networks, and the first-step law.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ssa_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+SCHEDULE_L = 0     # left-to-right a0 / prefix sums
+SCHEDULE_W32 = 1   # 32-lane chunked sums + Kogge-Stone scan
+FLAG_TRUNCATED = 1
+FLAG_OVERFLOW = 2
+
+
+# ---------------------------------------------------------------- constants
+def _atanh_ratio_scaled(a: int, b: int, bits: int) -> int:
+    """floor-sum approximation of atanh(a/b) * 2**bits (0 < a < b), Python ints.
+
+    Series atanh(z) = sum_k z^(2k+1) / (2k+1); every term is floored, so the
+    error is below (number of terms) * 2**-bits."""
+    total = 0
+    k = 0
+    num = a
+    den = b
+    while True:
+        term = (num << bits) // (den * (2 * k + 1))
+        if term == 0:
+            break
+        total += term
+        num *= a * a
+        den *= b * b
+        k += 1
+    return total
+
+
+def _round_shift(v: int, shift: int) -> int:
+    """round(v / 2**shift), halves up (no exact halves occur here)."""
+    return (v + (1 << (shift - 1))) >> shift
+
+
+def log_constants():
+    """Integer constants of the fixed-point -ln(u) (Tang-style table method).
+
+    F_i = 1 + (2i+1)/256 for i in 0..127.
+      inv[i]    = round(2^64 / F_i) = round(2^72 / (257 + 2i))
+      lnf[i]    = round(2^64 ln F_i), ln F_i = 2 atanh((2i+1) / (513 + 2i))
+      ln2       = round(2^64 ln 2),   ln 2 = 2 atanh(1/3)
+      horner[m] = round((-1)^(m+1) 2^62 / m), m = 1..7 (index 0 unused)
+    """
+    W = 256
+    inv = [_round_shift((1 << 73) // (257 + 2 * i), 1) for i in range(128)]
+    lnf = [_round_shift(2 * _atanh_ratio_scaled(2 * i + 1, 513 + 2 * i, W), W - 64) for i in range(128)]
+    ln2 = _round_shift(2 * _atanh_ratio_scaled(1, 3, W), W - 64)
+    horner = [0]
+    for m in range(1, 8):
+        mag = _round_shift((1 << 63) // m, 1) if (1 << 63) % m else (1 << 62) // m
+        horner.append(mag if m % 2 == 1 else -mag)
+    return inv, lnf, ln2, horner
+
+
+# ---------------------------------------------------------------- build / load
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (g++, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c++17", "-shared", "-fPIC",
+           "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _u64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+
+
+def _i64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def _i32p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _f64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = build()
+        L = ctypes.CDLL(path)
+        vp = ctypes.c_void_p
+        i32, i64, u64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        L.oracle_init_log.argtypes = [vp, vp, u64, vp]
+        L.oracle_init_log.restype = ctypes.c_int
+        L.oracle_philox4x64.argtypes = [vp, vp, vp]
+        L.oracle_philox4x64.restype = None
+        L.oracle_neg_log_u.argtypes = [u64]
+        L.oracle_neg_log_u.restype = f64
+        L.oracle_neg_log_u_many.argtypes = [i64, vp, vp]
+        L.oracle_neg_log_u_many.restype = None
+        L.oracle_uniform_grid.argtypes = [ctypes.c_int, f64, vp]
+        L.oracle_uniform_grid.restype = None
+        L.oracle_run.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, i64, i64, f64, ctypes.c_int, vp,
+                                 u64, u64, i64, ctypes.c_int, vp, vp, vp, vp, vp, vp]
+        L.oracle_run.restype = ctypes.c_int
+        L.oracle_trace.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, i64, f64, ctypes.c_int, vp, u64,
+                                   u64, i64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
+        L.oracle_trace.restype = ctypes.c_int
+        L.oracle_prefix.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, vp]
+        L.oracle_prefix.restype = None
+        L.oracle_finalize.argtypes = [i64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
+        L.oracle_finalize.restype = None
+        inv, lnf, ln2, horner = log_constants()
+        a_inv = np.array(inv, dtype=np.uint64)
+        a_lnf = np.array(lnf, dtype=np.uint64)
+        a_h = np.array(horner, dtype=np.int64)
+        rc = L.oracle_init_log(a_inv.ctypes.data, a_lnf.ctypes.data, ln2, a_h.ctypes.data)
+        if rc != 0:
+            raise RuntimeError("oracle_init_log failed")
+        _lib = L
+        return L
+
+
+# ---------------------------------------------------------------- wrappers
+def philox4x64(ctr, key) -> np.ndarray:
+    """Philox4x64-10 block for a 4-word counter and 2-word key."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    lib().oracle_philox4x64(c.ctypes.data, k.ctypes.data, out.ctypes.data)
+    return out
+
+
+def neg_log_u(q) -> np.ndarray:
+    """-ln(q * 2^-53) for odd q in [1, 2^53) (fixed-point method)."""
+    qa = np.ascontiguousarray(np.atleast_1d(q), dtype=np.uint64)
+    out = np.empty(qa.shape[0], dtype=np.float64)
+    lib().oracle_neg_log_u_many(qa.shape[0], qa.ctypes.data, out.ctypes.data)
+    return out
+
+
+def uniform_grid(n_grid: int, t_end: float) -> np.ndarray:
+    g = np.empty(n_grid, dtype=np.float64)
+    lib().oracle_uniform_grid(n_grid, float(t_end), g.ctypes.data)
+    return g
+
+
+def _model_arrays(net):
+    R = np.ascontiguousarray(net.reactants, dtype=np.int32)
+    P = np.ascontiguousarray(net.products, dtype=np.int32)
+    c = np.ascontiguousarray(net.rates, dtype=np.float64)
+    x0 = np.ascontiguousarray(net.x0, dtype=np.int32)
+    return R, P, c, x0
+
+
+class OracleResult:
+    def __init__(self, S1, S2, totals, traj_events=None, traj_hash=None, traj_flags=None):
+        self.S1, self.S2 = S1, S2
+        self.events, self.truncated, self.overflowed, self.max_x = (int(v) for v in totals)
+        self.traj_events, self.traj_hash, self.traj_flags = traj_events, traj_hash, traj_flags
+
+
+def run(net, n_traj: int, t_end: float, n_grid: int, seed: int, grid=None, traj_begin: int = 0,
+        stream: int = 0, max_events: int = 1 << 62, schedule: int = SCHEDULE_L,
+        per_traj: bool = False, threads: int = 1, ids=None) -> OracleResult:
+    """Runs trajectory ids [traj_begin, traj_begin + n_traj) (or the explicit
+    list ``ids``) and returns the exact int64 grid sums S1 = sum x,
+    S2 = sum x^2 (shape [G, S]) plus totals.  ``threads`` > 1 splits the ids
+    over Python threads (the C call releases the GIL) and adds the int64
+    partial sums, which is exact and order-independent."""
+    L = lib()
+    R, P, c, x0 = _model_arrays(net)
+    S, M = net.n_species, net.n_reactions
+    g = uniform_grid(n_grid, t_end) if grid is None else np.ascontiguousarray(grid, dtype=np.float64)
+    G = int(g.shape[0])
+    if ids is not None:
+        spans = [(int(i), int(i) + 1) for i in ids]
+    else:
+        spans = [(traj_begin, traj_begin + n_traj)]
+    n_total = sum(e - b for b, e in spans)
+
+    def work(span_list):
+        s1 = np.zeros((G, S), dtype=np.int64)
+        s2 = np.zeros((G, S), dtype=np.int64)
+        tot = np.zeros(4, dtype=np.int64)
+        cnt = sum(e - b for b, e in span_list)
+        ev = np.zeros(cnt, dtype=np.int64) if per_traj else None
+        hs = np.zeros(cnt, dtype=np.uint64) if per_traj else None
+        fl = np.zeros(cnt, dtype=np.int32) if per_traj else None
+        off = 0
+        for b, e in span_list:
+            n = e - b
+            rc = L.oracle_run(S, M, R.ctypes.data, P.ctypes.data, c.ctypes.data, x0.ctypes.data, b, e,
+                              float(t_end), G, g.ctypes.data, int(seed), int(stream), int(max_events),
+                              int(schedule), s1.ctypes.data, s2.ctypes.data,
+                              ev[off:].ctypes.data if per_traj else None,
+                              hs[off:].ctypes.data if per_traj else None,
+                              fl[off:].ctypes.data if per_traj else None, tot.ctypes.data)
+            if rc != 0:
+                raise ValueError("oracle_run rejected its arguments")
+            off += n
+        return s1, s2, tot, ev, hs, fl
+
+    if threads <= 1 or n_total < 2:
+        parts = [work(spans)]
+    else:
+        # split ids into `threads` contiguous chunks
+        flat = []
+        for b, e in spans:
+            flat.append((b, e))
+        if len(flat) == 1:
+            b, e = flat[0]
+            bounds = np.linspace(b, e, threads + 1).astype(np.int64)
+            chunks = [[(int(bounds[i]), int(bounds[i + 1]))] for i in range(threads) if bounds[i + 1] > bounds[i]]
+        else:
+            per = (len(flat) + threads - 1) // threads
+            chunks = [flat[i:i + per] for i in range(0, len(flat), per)]
+        with ThreadPoolExecutor(max_workers=len(chunks)) as ex:
+            parts = list(ex.map(work, chunks))
+    S1 = np.zeros((G, S), dtype=np.int64)
+    S2 = np.zeros((G, S), dtype=np.int64)
+    tot = np.zeros(4, dtype=np.int64)
+    with np.errstate(over="ignore"):
+        for s1, s2, t, _, _, _ in parts:
+            S1 = (S1.view(np.uint64) + s1.view(np.uint64)).view(np.int64)
+            S2 = (S2.view(np.uint64) + s2.view(np.uint64)).view(np.int64)
+            tot[:3] += t[:3]
+            tot[3] = max(tot[3], t[3])
+    if per_traj:
+        ev = np.concatenate([p[3] for p in parts])
+        hs = np.concatenate([p[4] for p in parts])
+        fl = np.concatenate([p[5] for p in parts])
+        return OracleResult(S1, S2, tot, ev, hs, fl)
+    return OracleResult(S1, S2, tot)
+
+
+def trace(net, traj_id: int, t_end: float, n_grid: int, seed: int, grid=None, stream: int = 0,
+          max_events: int = 1 << 62, schedule: int = SCHEDULE_L, record_max: int = 100000):
+    """One trajectory: (event times, reaction indices, per-grid states [G, S], flags)."""
+    L = lib()
+    R, P, c, x0 = _model_arrays(net)
+    g = uniform_grid(n_grid, t_end) if grid is None else np.ascontiguousarray(grid, dtype=np.float64)
+    G = int(g.shape[0])
+    rt = np.zeros(record_max, dtype=np.float64)
+    rj = np.zeros(record_max, dtype=np.int32)
+    xs = np.zeros((G, net.n_species), dtype=np.int64)
+    ne = np.zeros(1, dtype=np.int64)
+    flags = L.oracle_trace(net.n_species, net.n_reactions, R.ctypes.data, P.ctypes.data, c.ctypes.data,
+                           x0.ctypes.data, int(traj_id), float(t_end), G, g.ctypes.data, int(seed), int(stream),
+                           int(max_events), int(schedule), record_max, rt.ctypes.data, rj.ctypes.data,
+                           xs.ctypes.data, ne.ctypes.data)
+    n = int(min(ne[0], record_max))
+    return rt[:n], rj[:n], xs, int(flags), int(ne[0])
+
+
+def prefix_sums(a, schedule: int = SCHEDULE_L):
+    """(prefix, a0) of propensities ``a`` in the given summation schedule."""
+    av = np.ascontiguousarray(a, dtype=np.float64)
+    pre = np.empty_like(av)
+    a0 = np.zeros(1, dtype=np.float64)
+    lib().oracle_prefix(int(av.shape[0]), av.ctypes.data, int(schedule), pre.ctypes.data, a0.ctypes.data)
+    return pre, float(a0[0])
+
+
+def finalize(n_traj: int, S1: np.ndarray, S2: np.ndarray):
+    """mean = S1/N, var = (N S2 - S1^2)/(N(N-1)) with an exact int128 numerator."""
+    G, S = S1.shape
+    s1 = np.ascontiguousarray(S1, dtype=np.int64)
+    s2 = np.ascontiguousarray(S2, dtype=np.int64)
+    mean = np.empty((G, S), dtype=np.float64)
+    var = np.empty((G, S), dtype=np.float64)
+    lib().oracle_finalize(int(n_traj), G, S, s1.ctypes.data, s2.ctypes.data, mean.ctypes.data, var.ctypes.data)
+    return mean, var

@@ -1,0 +1,390 @@
+// Oracle: a plain, slow, single-threaded CPU statement of the ensemble SSA with
+// time-aligned mean / variance reduction.
+//
+// TEST INFRASTRUCTURE ONLY.  Only tests, the smoke check and the benchmark's
+// CPU-baseline leg load this file's library.  It shares no code, header, table
+// or constant generator with the CUDA library; the constants of its fixed-point
+// logarithm are computed by oracle/__init__.py with Python integers and handed
+// in through oracle_init_log().
+//
+// What it computes, per trajectory id i in [traj_begin, traj_end):
+//   * Gillespie's direct method (Sec. 2: the next transition and its time are
+//     drawn exactly from the CTMC's law; "a single transition amongst the
+//     possible ones is selected, and the state updated accordingly").
+//   * Mass-action propensities over an integer state and integer
+//     stoichiometry (Sec. 3.2, model files: state vector, stoichiometric
+//     matrix, propensity vector; "the more the reactants (and the rate) the
+//     highest the probability").
+//   * Selective memory with average as combining function (Sec. 3.2.1 and
+//     Fig. 3): every trajectory's state is aligned on common simulation-time
+//     points and reduced across trajectories by associative, commutative sums
+//     (sum of x and of x^2, from which mean and variance follow; Sec. 4 reports
+//     average and variance).
+//
+// Readings where the paper is silent (each also listed in the design notes):
+//   * the random source is Philox4x64-10 (Salmon et al., SC'11), key =
+//     (seed, stream), counter = (event pair index, trajectory id, domain, 0);
+//     event n uses words (0,1) of pair n/2 when n is even, (2,3) when odd;
+//   * u(w) = (2*(w >> 12) + 1) * 2^-53, exactly representable, in (0, 1);
+//   * -ln(r1) is a fixed-point table-driven logarithm (Tang, ACM TOMS 16(4),
+//     1990: table of ln F_i and 1/F_i, short series for ln(1+r));
+//   * h_j = prod_s C(x_s, R_js); a_j = c_j * (double)h_j;
+//     a0 and the selection prefix sums are left-to-right FP64 sums (schedule
+//     L) or the 32-lane chunked scan described at w32_prefix() (schedule W32);
+//   * selection: smallest j with prefix_j > r2 * a0; if rounding leaves none,
+//     the last j with a_j > 0;
+//   * grid value at g_k is the state after all events with time <= g_k
+//     (right-continuous); an event whose time exceeds t_end is not fired;
+//   * a0 == 0 makes the state absorbing (t_next = +inf).
+//
+// Build: g++ -O2 -ffp-contract=off (no FMA contraction), no -ffast-math.
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+namespace {
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+// ---------------------------------------------------------------- Philox4x64-10
+// Round function and key schedule as published by Salmon, Moraes, Dror and
+// Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11 (Philox-4x64,
+// multipliers 0xD2E7470EE14C6C93 / 0xCA5A826395121157, Weyl increments from
+// the golden ratio and sqrt(3) - 1).
+const uint64_t kPhiloxM0 = 0xD2E7470EE14C6C93ULL;
+const uint64_t kPhiloxM1 = 0xCA5A826395121157ULL;
+const uint64_t kPhiloxW0 = 0x9E3779B97F4A7C15ULL;
+const uint64_t kPhiloxW1 = 0xBB67AE8584CAA73BULL;
+
+void philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4]) {
+  uint64_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint64_t k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += kPhiloxW0;
+      k1 += kPhiloxW1;
+    }
+    u128 p0 = (u128)kPhiloxM0 * c0;
+    u128 p1 = (u128)kPhiloxM1 * c2;
+    uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+    uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+    uint64_t n0 = hi1 ^ c1 ^ k0;
+    uint64_t n1 = lo1;
+    uint64_t n2 = hi0 ^ c3 ^ k1;
+    uint64_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// ------------------------------------------------------- fixed-point -ln(u)
+// Constants handed in by the Python side (integers, see oracle/__init__.py):
+//   inv[i] = round(2^64 / F_i), lnf[i] = round(2^64 ln F_i), F_i = 1 + (2i+1)/256,
+//   ln2 = round(2^64 ln 2), horner[m] = round((-1)^(m+1) 2^62 / m), m = 1..7.
+struct LogTables {
+  uint64_t inv[128];
+  uint64_t lnf[128];
+  uint64_t ln2;
+  int64_t horner[8];
+  bool ready;
+};
+LogTables g_log = {};
+
+// E = -ln(q * 2^-53) for odd q in [1, 2^53).
+//   q = 2^e (1 + f), f in [0, 1) held as Q0.64;
+//   1 + f = F_i (1 + r), F_i the table point of f's top 7 bits, r = (f - c_i) / F_i;
+//   -ln(u) = (53 - e) ln 2 - ln F_i - ln(1 + r), ln(1 + r) by its Taylor series
+//   to r^7 (|r| < 2^-8, remainder < 2^-67), evaluated in Q1.62 by Horner.
+// The result is formed in Q.64 (units of 2^-64) and rounded once to double.
+double neg_log_u(uint64_t q) {
+  int e = 63 - __builtin_clzll(q);                 // floor(log2 q), 0..52
+  uint64_t f = (q << (63 - e)) << 1;               // fraction bits of q / 2^e
+  int i = (int)(f >> 57);                          // table index, top 7 bits
+  uint64_t center = ((uint64_t)(2 * i + 1)) << 56; // (2i+1)/256 in Q.64
+  int64_t d = (int64_t)(f - center);               // f - c_i, |d| < 2^-8
+  // r = d / F_i  ~  floor(d * inv_i / 2^64)
+  int64_t r = (int64_t)(((i128)d * (i128)(u128)g_log.inv[i]) >> 64);
+  int64_t acc = g_log.horner[7];
+  for (int m = 6; m >= 1; --m) acc = g_log.horner[m] + (int64_t)(((i128)acc * (i128)r) >> 64);
+  int64_t ln1p = (int64_t)(((i128)acc * (i128)r) >> 62);  // r * acc in Q.64
+  i128 E = (i128)(53 - e) * (i128)(u128)g_log.ln2 - (i128)(u128)g_log.lnf[i] - (i128)ln1p;
+  u128 Eu = (u128)E;
+  if ((Eu >> 64) == 0) return (double)(uint64_t)Eu * 0x1p-64;
+  return (double)(uint64_t)(Eu >> 6) * 0x1p-58;
+}
+
+// u(w) = (2 * (w >> 12) + 1) * 2^-53
+inline uint64_t odd53(uint64_t w) { return ((w >> 12) << 1) | 1ULL; }
+inline double uniform_open(uint64_t w) { return (double)odd53(w) * 0x1p-53; }
+
+// --------------------------------------------------------------- model
+struct Model {
+  int S = 0, M = 0;
+  std::vector<int32_t> R, P, nu;  // M x S
+  std::vector<double> c;          // M
+  std::vector<int32_t> x0;        // S
+};
+
+// Mass-action combinatorial factor: h_j(x) = prod_s C(x_s, R_js)  (R_js in 0..2).
+int64_t mass_action_h(const Model& m, int j, const std::vector<int64_t>& x) {
+  int64_t h = 1;
+  for (int s = 0; s < m.S; ++s) {
+    int r = m.R[(size_t)j * m.S + s];
+    if (r == 1) h *= x[s];
+    else if (r == 2) h *= x[s] * (x[s] - 1) / 2;
+  }
+  return h;
+}
+
+// Schedule W32: 32 lanes; lane l owns the contiguous chunk of ceil(M/32)
+// reactions starting at l * ceil(M/32); each lane sums its chunk left to right;
+// lane partials are combined by an inclusive Kogge-Stone scan with offsets
+// 1, 2, 4, 8, 16 (v[l] = v[l] + v[l - off] for l >= off, all lanes reading the
+// previous step's values).  The prefix of reaction j is (scan of lanes before
+// j's lane) + (left-to-right sum inside j's chunk up to j), formed as
+// excl + inner with excl = 0 for lane 0.  a0 is lane 31's inclusive value.
+void w32_prefix(const std::vector<double>& a, int M, std::vector<double>& prefix, double* a0) {
+  const int chunk = (M + 31) / 32;
+  double part[32];
+  for (int l = 0; l < 32; ++l) {
+    double s = 0.0;
+    for (int q = 0; q < chunk; ++q) {
+      int j = l * chunk + q;
+      if (j < M) s = (q == 0) ? a[j] : s + a[j];
+    }
+    part[l] = s;
+  }
+  double scan[32];
+  for (int l = 0; l < 32; ++l) scan[l] = part[l];
+  for (int off = 1; off < 32; off <<= 1) {
+    double prev[32];
+    for (int l = 0; l < 32; ++l) prev[l] = scan[l];
+    for (int l = off; l < 32; ++l) scan[l] = prev[l] + prev[l - off];
+  }
+  for (int l = 0; l < 32; ++l) {
+    double excl = (l == 0) ? 0.0 : scan[l - 1];
+    double inner = 0.0;
+    for (int q = 0; q < chunk; ++q) {
+      int j = l * chunk + q;
+      if (j >= M) break;
+      inner = (q == 0) ? a[j] : inner + a[j];
+      prefix[j] = (l == 0) ? inner : excl + inner;
+    }
+  }
+  *a0 = scan[31];
+}
+
+const int kFlagTruncated = 1;
+const int kFlagOverflow = 2;
+const int64_t kStateLimit = 2147483647LL;  // int32 state
+const uint64_t kFnvOffset = 0xcbf29ce484222325ULL;
+const uint64_t kFnvPrime = 0x100000001b3ULL;
+
+inline uint64_t dbits(double v) { uint64_t b; std::memcpy(&b, &v, 8); return b; }
+
+struct TrajResult {
+  int64_t events = 0;
+  uint64_t hash = kFnvOffset;
+  int flags = 0;
+  int64_t max_x = 0;
+};
+
+// One trajectory of the direct method with grid alignment (emission into
+// S1 / S2 of x and x^2 at every grid point, right-continuous).
+TrajResult run_one(const Model& m, uint64_t traj_id, double t_end, int G, const double* grid,
+                   uint64_t seed, uint64_t stream, int64_t max_events, int schedule,
+                   uint64_t* S1, uint64_t* S2,
+                   int record_max, double* rec_t, int32_t* rec_j) {
+  TrajResult res;
+  std::vector<int64_t> x(m.S);
+  for (int s = 0; s < m.S; ++s) { x[s] = m.x0[s]; if (x[s] > res.max_x) res.max_x = x[s]; }
+  std::vector<double> a(m.M), prefix(m.M);
+  const uint64_t key[2] = {seed, stream};
+  uint64_t words[4] = {0, 0, 0, 0};
+  double t = 0.0;
+  int64_t n = 0;
+  int k = 0;
+  auto emit_until = [&](double t_next) {  // grid points with g_k < t_next see the current x
+    while (k < G && grid[k] < t_next) {
+      for (int s = 0; s < m.S; ++s) {
+        S1[(size_t)k * m.S + s] += (uint64_t)x[s];
+        S2[(size_t)k * m.S + s] += (uint64_t)(x[s] * x[s]);
+      }
+      ++k;
+    }
+  };
+  for (;;) {
+    // propensities (Sec. 3.2: mass action), a0 and selection prefix sums
+    for (int j = 0; j < m.M; ++j) a[j] = m.c[j] * (double)mass_action_h(m, j, x);
+    double a0 = 0.0;
+    if (schedule == 0) {
+      for (int j = 0; j < m.M; ++j) { a0 = (j == 0) ? a[0] : a0 + a[j]; prefix[j] = a0; }
+    } else {
+      w32_prefix(a, m.M, prefix, &a0);
+    }
+    // random numbers for event n
+    if ((n & 1) == 0) {
+      const uint64_t ctr[4] = {(uint64_t)(n >> 1), traj_id, 0, 0};
+      philox4x64_10(ctr, key, words);
+    }
+    const uint64_t wa = (n & 1) ? words[2] : words[0];
+    const uint64_t wb = (n & 1) ? words[3] : words[1];
+    // next event time (Sec. 2: the time at which the next transition occurs)
+    double t_next;
+    if (a0 > 0.0) {
+      double E = neg_log_u(odd53(wa));
+      t_next = t + E / a0;
+    } else {
+      t_next = std::numeric_limits<double>::infinity();
+    }
+    emit_until(t_next);
+    if (t_next > t_end) break;
+    // select the transition: smallest j with prefix_j > r2 * a0
+    const double target = uniform_open(wb) * a0;
+    int jsel = -1;
+    for (int j = 0; j < m.M; ++j) {
+      if (prefix[j] > target) { jsel = j; break; }
+    }
+    if (jsel < 0) {
+      for (int j = m.M - 1; j >= 0; --j) if (a[j] > 0.0) { jsel = j; break; }
+    }
+    // state update, refusing to leave the int32 range
+    bool over = false;
+    for (int s = 0; s < m.S; ++s) {
+      int64_t v = x[s] + m.nu[(size_t)jsel * m.S + s];
+      if (v > kStateLimit) over = true;
+    }
+    if (over) { res.flags |= kFlagOverflow; break; }
+    for (int s = 0; s < m.S; ++s) {
+      x[s] += m.nu[(size_t)jsel * m.S + s];
+      if (x[s] > res.max_x) res.max_x = x[s];
+    }
+    t = t_next;
+    if (n < record_max) { rec_t[n] = t; rec_j[n] = jsel; }
+    res.hash = (res.hash ^ (uint64_t)jsel) * kFnvPrime;
+    res.hash = (res.hash ^ dbits(t)) * kFnvPrime;
+    ++n;
+    if (n == max_events) { res.flags |= kFlagTruncated; break; }
+  }
+  // points not yet emitted keep the last state (truncation, overflow, t_end)
+  emit_until(std::numeric_limits<double>::infinity());
+  res.events = n;
+  return res;
+}
+
+bool build_model(int S, int M, const int32_t* R, const int32_t* P, const double* c,
+                 const int32_t* x0, Model* m) {
+  if (S <= 0 || M <= 0) return false;
+  m->S = S; m->M = M;
+  m->R.assign(R, R + (size_t)M * S);
+  m->P.assign(P, P + (size_t)M * S);
+  m->nu.resize((size_t)M * S);
+  for (size_t q = 0; q < (size_t)M * S; ++q) m->nu[q] = P[q] - R[q];
+  m->c.assign(c, c + M);
+  m->x0.assign(x0, x0 + S);
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int oracle_init_log(const uint64_t* inv, const uint64_t* lnf, uint64_t ln2, const int64_t* horner) {
+  for (int i = 0; i < 128; ++i) { g_log.inv[i] = inv[i]; g_log.lnf[i] = lnf[i]; }
+  g_log.ln2 = ln2;
+  for (int m = 0; m < 8; ++m) g_log.horner[m] = horner[m];
+  g_log.ready = true;
+  return 0;
+}
+
+void oracle_philox4x64(const uint64_t* ctr, const uint64_t* key, uint64_t* out) {
+  philox4x64_10(ctr, key, out);
+}
+
+double oracle_neg_log_u(uint64_t q) { return neg_log_u(q); }
+
+void oracle_neg_log_u_many(int64_t n, const uint64_t* q, double* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = neg_log_u(q[i]);
+}
+
+// Uniform grid reading: g_k = ((double)k * t_end) / (double)(G - 1).
+void oracle_uniform_grid(int G, double t_end, double* grid) {
+  if (G == 1) { grid[0] = t_end; return; }
+  for (int k = 0; k < G; ++k) grid[k] = ((double)k * t_end) / (double)(G - 1);
+}
+
+// Runs trajectories [traj_begin, traj_end) and ADDS their x and x^2 grid sums
+// into S1 / S2 (int64, wrapping, G x S row-major).  Per-trajectory outputs are
+// indexed by id - traj_begin and may be null.  totals[0..3] receive (added):
+// events, truncated trajectories, overflowed trajectories, max state seen.
+// Returns 0, or -1 on bad arguments / uninitialised tables.
+int oracle_run(int S, int M, const int32_t* R, const int32_t* P, const double* c, const int32_t* x0,
+               int64_t traj_begin, int64_t traj_end, double t_end, int G, const double* grid,
+               uint64_t seed, uint64_t stream, int64_t max_events, int schedule,
+               int64_t* S1, int64_t* S2,
+               int64_t* traj_events, uint64_t* traj_hash, int32_t* traj_flags, int64_t* totals) {
+  if (!g_log.ready || traj_end < traj_begin || G < 1 || (schedule != 0 && schedule != 1)) return -1;
+  Model m;
+  if (!build_model(S, M, R, P, c, x0, &m)) return -1;
+  for (int64_t id = traj_begin; id < traj_end; ++id) {
+    TrajResult r = run_one(m, (uint64_t)id, t_end, G, grid, seed, stream, max_events, schedule,
+                           (uint64_t*)S1, (uint64_t*)S2, 0, nullptr, nullptr);
+    const int64_t o = id - traj_begin;
+    if (traj_events) traj_events[o] = r.events;
+    if (traj_hash) traj_hash[o] = r.hash;
+    if (traj_flags) traj_flags[o] = r.flags;
+    if (totals) {
+      totals[0] += r.events;
+      totals[1] += (r.flags & kFlagTruncated) ? 1 : 0;
+      totals[2] += (r.flags & kFlagOverflow) ? 1 : 0;
+      if (r.max_x > totals[3]) totals[3] = r.max_x;
+    }
+  }
+  return 0;
+}
+
+// Records the event times and reaction indices of one trajectory (first
+// record_max events) and its per-grid states into xs (G x S).
+int oracle_trace(int S, int M, const int32_t* R, const int32_t* P, const double* c, const int32_t* x0,
+                 int64_t traj_id, double t_end, int G, const double* grid, uint64_t seed,
+                 uint64_t stream, int64_t max_events, int schedule, int record_max,
+                 double* rec_t, int32_t* rec_j, int64_t* xs, int64_t* n_events) {
+  if (!g_log.ready) return -1;
+  Model m;
+  if (!build_model(S, M, R, P, c, x0, &m)) return -1;
+  std::vector<uint64_t> s1((size_t)G * S, 0), s2((size_t)G * S, 0);
+  TrajResult r = run_one(m, (uint64_t)traj_id, t_end, G, grid, seed, stream, max_events, schedule,
+                         s1.data(), s2.data(), record_max, rec_t, rec_j);
+  for (size_t q = 0; q < (size_t)G * S; ++q) xs[q] = (int64_t)s1[q];
+  *n_events = r.events;
+  return r.flags;
+}
+
+// Prefix sums of a[0..M) in the given schedule (0 = L, 1 = W32); for tests.
+void oracle_prefix(int M, const double* a, int schedule, double* prefix, double* a0) {
+  std::vector<double> av(a, a + M), pv(M);
+  if (schedule == 0) {
+    double s = 0.0;
+    for (int j = 0; j < M; ++j) { s = (j == 0) ? av[0] : s + av[j]; pv[j] = s; }
+    *a0 = s;
+  } else {
+    w32_prefix(av, M, pv, a0);
+  }
+  for (int j = 0; j < M; ++j) prefix[j] = pv[j];
+}
+
+// mean = S1 / N; var = (N S2 - S1^2) / (N (N - 1)), numerator exact in int128
+// and rounded once to double (var is NaN for N < 2).
+void oracle_finalize(int64_t N, int G, int S, const int64_t* S1, const int64_t* S2,
+                     double* mean, double* var) {
+  for (size_t q = 0; q < (size_t)G * S; ++q) {
+    mean[q] = (double)S1[q] / (double)N;
+    if (N < 2) { var[q] = std::numeric_limits<double>::quiet_NaN(); continue; }
+    i128 num = (i128)N * (i128)S2[q] - (i128)S1[q] * (i128)S1[q];
+    var[q] = (double)num / ((double)N * (double)(N - 1));
+  }
+}
+
+}  // extern "C"
