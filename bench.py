@@ -1,0 +1,318 @@
+#!/usr/bin/env python3
+"""Throughput of the ensemble SSA hot path on one GB300: reaction events/s
+including grid alignment and the mean/variance reduction.
+
+A step is one full ssa_ensemble_run of the HIV-shaped four-species model
+(65,536 trajectories per GPU, t_end = 30, 3001-point grid, FP64 exact mode):
+work-counter reset, grid, the simulation kernel (direct method + on-device
+time-aligned difference sums), and the finalisation kernel (grid scans,
+sums, mean, variance).  Inputs are resident on the device; each step uses a
+new seed.  L2 is flushed (256 MiB write) between timed steps, outside the
+timed events.
+
+--impl reference times the oracle (plain single-threaded C++ per trajectory,
+run on all host cores over trajectory-id ranges) on a bounded sample of the
+same workload.
+
+With torchrun (N > 1) every rank runs its own shard (trajectory ids offset by
+rank * 65,536): weak scaling, no data-path collective; a barrier brackets
+the timed region and the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SSA reaction events/s incl. grid align+mean/var reduce, 1 GB300, vs plain FP64"
+UNIT = "events/s"
+SMS_GB300 = 152
+FP64_OPS_PER_SM_CLK = 2.0  # 1.25 TFLOP/s dense FP64 (FMA = 2 flops) / (152 SMs * 2.07 GHz)
+
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n-traj", type=int, default=65536, help="trajectories per GPU")
+    p.add_argument("--e2e-steps", type=int, default=20)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile-small", action="store_true",
+                   help="one small step (16,384 trajectories) for an ncu capture; prints no bench line")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={CLOCK_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [v.strip() for v in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def fp64_ops_per_event(n_reactions: int) -> int:
+    """Algorithmic FP64 operations of one direct-method event in exact mode:
+    M products c_j * h_j, M - 1 sums for a0 and the prefix sums, the product
+    r2 * a0, the quotient -ln(r1) / a0 and the sum t + tau."""
+    return 2 * n_reactions + 2
+
+
+def cpu_baseline(w, n_traj_sample: int):
+    """The oracle as it stands, on all host cores (one thread per id range)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = oracle.run(w.net, n_traj_sample, w.t_end, w.n_grid, w.seed, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": r.events / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"trajectories 0..{n_traj_sample - 1} of the workload (seed {w.seed}), "
+                      f"{r.events} events in {dt:.3f} s on {cores} threads"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import workloads as W
+    w = W.workload_hiv_shaped(args.n_traj)
+    oracle.lib()
+    cores = os.cpu_count() or 1
+    sample = min(args.n_traj, 4096)
+    for i in range(args.warmup):
+        oracle.run(w.net, sample, w.t_end, w.n_grid, 1 + i, threads=cores)
+    events = 0
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        r = oracle.run(w.net, sample, w.t_end, w.n_grid, 1000 + i, threads=cores)
+        events += r.events
+    dt = time.perf_counter() - t0
+    value = events / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "hiv_shaped_S4_M10_G3001_T30", "n_traj": args.n_traj, "n_grid": w.n_grid,
+                   "t_end": w.t_end, "precision": "fp64", "sample_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} trajectories per step (seeds 1000..), {cores} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1007_1768_gb300 as ssa
+    import workloads as W
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+
+    n = args.n_traj if not args.profile_small else 16384
+    w = W.workload_hiv_shaped(n)
+    model = ssa.Model.from_network(w.net)
+    G, S, M = w.n_grid, w.net.n_species, w.net.n_reactions
+    stream = torch.cuda.current_stream(dev)
+    mean = torch.empty((G, S), dtype=torch.float64, device=dev)
+    var = torch.empty((G, S), dtype=torch.float64, device=dev)
+    totals = torch.zeros(4, dtype=torch.int64, device=dev)
+    base_opts = ssa.make_opts(memory=ssa.binding.MEM_DEVICE, cuda_stream=stream.cuda_stream,
+                              traj_offset=rank * n)
+    ws_bytes = ssa.workspace_bytes(model, n, G, base_opts)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    L = ssa.lib()
+
+    def run_step(seed, ev_begin=None, ev_end=None):
+        o = ssa.make_opts(memory=ssa.binding.MEM_DEVICE, cuda_stream=stream.cuda_stream, traj_offset=rank * n,
+                          workspace=ws.data_ptr(), workspace_bytes=ws_bytes, device_totals=totals.data_ptr(),
+                          sim_event_begin=ev_begin, sim_event_end=ev_end)
+        st = L.ssa_ensemble_run(model.handle, n, w.t_end, G, None, seed, o, mean.data_ptr(), var.data_ptr(),
+                                None, None, None)
+        if st != 0:
+            raise RuntimeError(f"ssa_ensemble_run failed: {L.ssa_last_error().decode()}")
+
+    if args.profile_small:
+        run_step(1)
+        torch.cuda.synchronize()
+        return 0
+
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for i in range(args.warmup):
+        run_step(1 + i)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    k_s = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    k_e = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    for e in k_s + k_e:  # create the underlying cudaEvent_t handles
+        e.record(stream)
+    torch.cuda.synchronize()
+    totals.zero_()
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for i in range(K):
+        flush.fill_(i & 0xFF)  # L2 flush, outside the step's events
+        ev_s[i].record(stream)
+        run_step(1000 + i, k_s[i].cuda_event, k_e[i].cuda_event)
+        ev_e[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    if pg:
+        pg.barrier()
+    step_ms = [ev_s[i].elapsed_time(ev_e[i]) for i in range(K)]
+    kern_ms = [k_s[i].elapsed_time(k_e[i]) for i in range(K)]
+    tot = totals.cpu().tolist()
+    events = int(tot[0])
+    total_ms = sum(step_ms)
+    if pg:
+        t = torch.tensor([total_ms, float(events)], dtype=torch.float64)
+        mx = t.clone()
+        pg.all_reduce(mx, op=pg.ReduceOp.MAX)
+        sm = t.clone()
+        pg.all_reduce(sm, op=pg.ReduceOp.SUM)
+        total_ms, events_all = float(mx[0]), float(sm[1])
+    else:
+        events_all = float(events)
+    value = events_all / (total_ms * 1e-3)
+
+    # roofline of the simulation kernel: FP64 pipe (ALU bound)
+    ops = fp64_ops_per_event(M) * (events / K)
+    kern_avg = statistics.mean(kern_ms)
+    achieved = ops / (kern_avg * 1e-3) * 1e-9
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    peak = FP64_OPS_PER_SM_CLK * SMS_GB300 * sm_mhz * 1e6 * 1e-9
+
+    result = None
+    if rank == 0:
+        # end to end through the C ABI with host buffers: grid in, mean/var out
+        import numpy as np
+        grid_h = (np.arange(G, dtype=np.float64) * w.t_end) / (G - 1)
+        e_ev = 0
+        for i in range(2):
+            ssa.ensemble_run(model, n, w.t_end, G, 1 + i, grid=grid_h, want_sums=False, traj_offset=rank * n)
+        t0 = time.perf_counter()
+        for i in range(args.e2e_steps):
+            r = ssa.ensemble_run(model, n, w.t_end, G, 5000 + i, grid=grid_h, want_sums=False,
+                                 traj_offset=rank * n)
+            e_ev += r.events
+        e_dt = time.perf_counter() - t0
+        e2e = {"value": e_ev / e_dt, "unit": UNIT, "h2d_bytes_per_step": int(grid_h.nbytes),
+               "d2h_bytes_per_step": int(2 * G * S * 8 + 8 * 8), "steps": args.e2e_steps}
+        cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(w, min(n, 16384))
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "hiv_shaped_S4_M10_G3001_T30", "n_traj_per_gpu": n, "n_grid": G,
+                       "t_end": w.t_end, "precision": "fp64-exact", "seeds": "1000+step",
+                       "l2": "flushed between timed steps (256 MiB write outside the step events)",
+                       "parallelism": f"replicas x{world} (trajectory-id shards)"},
+            "traj_per_s": world * n / (total_ms * 1e-3 / K) if K else None,
+            "events_per_step": events_all / K,
+            "wall_s_timed_region": wall,
+            "roofline": {"bound": "alu", "kernel": "k_ssa_thread", "achieved": achieved, "peak": peak,
+                         "unit": "GFLOP/s (FP64 ops)", "frac": achieved / peak, "traffic": None,
+                         "kernel_ms": kern_avg, "ops_per_event": fp64_ops_per_event(M),
+                         "peak_basis": "2 FP64 ops/clk/SM x 152 SMs x median SM clock (nominal 1.25 TFLOP/s dense)"},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 3 * K,
+            "clocks": clk,
+        }
+        print(json.dumps(result))
+    model.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * ssa.h — C ABI of libssa: ensembles of Gillespie direct-method trajectories of
+ * a mass-action reaction network on one sm_103a GPU, with every trajectory's
+ * state aligned on a common simulation-time grid and reduced across
+ * trajectories into exact int64 sums, mean and variance.
+ *
+ * Paper: Aldinucci, Bracciali, Lio, Sorathiya, Torquati, "StochKit-FF:
+ * Efficient Systems Biology on Multicore Architectures" (arXiv:1007.1768).
+ *   - Sec. 2: the direct method picks the next transition and its time from
+ *     the CTMC's law and updates the state; one such run is a trajectory.
+ *   - Sec. 3.2 (model files): a model is an integer state vector, an integer
+ *     stoichiometric matrix, a propensity vector following mass action, the
+ *     rate constants and the simulated duration.
+ *   - Sec. 3.2 (StochRxn_ff): many copies of one simulation, or a parameter
+ *     sweep, run in parallel.
+ *   - Sec. 3.2.1 and Fig. 3 ("selective memory"): points of different
+ *     trajectories are aligned by simulation time and reduced by associative,
+ *     commutative functions; Sec. 4 uses average and variance.
+ *
+ * Conventions for every call:
+ *   - No call throws; each returns an ssa_status.  On failure a message for
+ *     the calling thread is available from ssa_last_error().
+ *   - Arrays are dense, row-major, C order.  "G x S" means index k * S + s.
+ *   - The library copies every input it keeps (models); the caller owns every
+ *     output buffer.
+ *   - opts->memory selects where grid and output arrays live: SSA_MEM_HOST
+ *     (plain host memory; the call copies in and out and is synchronous) or
+ *     SSA_MEM_DEVICE (device memory of the current CUDA device; the call only
+ *     enqueues work on opts->cuda_stream and returns, unless `stats` is
+ *     non-NULL, in which case it waits for the stream).
+ *   - The current CUDA device at the time of the call is used.
+ */
+#ifndef SSA_H_
+#define SSA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ssa_status {
+  SSA_OK = 0,
+  SSA_EINVAL = 1,       /* an argument is out of its documented range */
+  SSA_ENOMEM = 2,       /* a device or host allocation failed */
+  SSA_ECUDA = 3,        /* a CUDA runtime call failed */
+  SSA_EOVERFLOW = 4,    /* a count would leave int32, or sum x^2 could leave int64 */
+  SSA_ETRUNCATED = 5,   /* reserved: some trajectory hit max_events (reported in stats) */
+  SSA_ETIMEOUT = 6,     /* reserved for bounded device waits */
+  SSA_EUNSUPPORTED = 7  /* valid request this build does not implement */
+} ssa_status;
+
+/* Precision of the propensity arithmetic.  Time is FP64 in every mode. */
+enum { SSA_PREC_FP64 = 0, SSA_PREC_FP32 = 1 };
+/* Kernel shape: one trajectory per thread, or one per warp. */
+enum { SSA_SCHED_AUTO = 0, SSA_SCHED_THREAD = 1, SSA_SCHED_WARP = 2 };
+/* Where grid / outputs live. */
+enum { SSA_MEM_HOST = 0, SSA_MEM_DEVICE = 1 };
+/* Where the per-CTA difference arrays of the reduction live. */
+enum { SSA_REDUCE_AUTO = 0, SSA_REDUCE_SHARED = 1, SSA_REDUCE_GLOBAL = 2 };
+
+/* Largest state count; an event that would exceed it is not fired and the
+ * trajectory stops with the overflow flag. */
+#define SSA_STATE_MAX 2147483647
+#define SSA_DEFAULT_MAX_EVENTS ((int64_t)100000000)
+
+/* Per-trajectory flag bits (opts->traj_flags). */
+#define SSA_TRAJ_TRUNCATED 1
+#define SSA_TRAJ_OVERFLOW 2
+
+typedef struct ssa_model ssa_model; /* opaque, owned by the library */
+
+/* Options of one ensemble run.  Initialise with ssa_run_opts_init(). */
+typedef struct ssa_run_opts {
+  int32_t precision;      /* SSA_PREC_FP64 (bit-exact with the oracle) or SSA_PREC_FP32 */
+  int32_t schedule;       /* SSA_SCHED_* */
+  int32_t memory;         /* SSA_MEM_HOST or SSA_MEM_DEVICE */
+  int32_t reduce;         /* SSA_REDUCE_* */
+  int32_t block_threads;  /* threads per CTA; 0 = choose */
+  int32_t grid_blocks;    /* CTAs; 0 = choose */
+  int64_t max_events;     /* events per trajectory before it is truncated; <= 0: SSA_DEFAULT_MAX_EVENTS */
+  uint64_t traj_offset;   /* id of the first trajectory; ids are traj_offset .. traj_offset + n_traj - 1 */
+  uint64_t stream_id;     /* second word of the random key (the first is the seed) */
+  void* cuda_stream;      /* cudaStream_t to run on; NULL = the legacy default stream */
+  void* workspace;        /* device scratch of workspace_bytes; NULL = allocated and freed on the stream */
+  size_t workspace_bytes;
+  /* Optional per-trajectory outputs, [n_traj] each, in opts->memory's space; NULL to skip:
+   * events fired, a 64-bit hash of the (reaction index, event time bits) sequence, flag bits. */
+  int64_t* traj_events;
+  uint64_t* traj_hash;
+  int32_t* traj_flags;
+  /* Optional device int64[4] (device memory even with SSA_MEM_HOST): the run
+   * adds its event, truncated and overflowed counts to [0], [1], [2] and
+   * raises [3] to its largest count, without waiting for the stream. */
+  int64_t* device_totals;
+  /* Optional cudaEvent_t handles recorded on the stream immediately before and
+   * after the simulation kernel (for timing it alone); NULL to skip. */
+  void* sim_event_begin;
+  void* sim_event_end;
+} ssa_run_opts;
+
+/* Totals of one run (host struct). */
+typedef struct ssa_run_stats {
+  int64_t events;       /* reaction events fired over all trajectories */
+  int64_t truncated;    /* trajectories stopped by max_events */
+  int64_t overflowed;   /* trajectories stopped by SSA_STATE_MAX */
+  int64_t max_x;        /* largest count seen in any trajectory */
+  double kernel_ms;     /* device time of the simulation + reduction kernels */
+} ssa_run_stats;
+
+/* Text for a status code (static storage). */
+const char* ssa_status_string(ssa_status status);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* ssa_last_error(void);
+
+/* Fills *opts with the defaults: FP64, AUTO schedule and reduction, host
+ * memory, default max_events, offset 0, stream id 0, default CUDA stream,
+ * library-managed workspace, no per-trajectory outputs. */
+void ssa_run_opts_init(ssa_run_opts* opts);
+
+/*
+ * Creates a model (Sec. 3.2 model files).
+ *   n_species S >= 1, n_reactions M >= 1.
+ *   reactants [M x S]: multiplicity of species s consumed by reaction j,
+ *     entries 0..2 with row sum <= 2 (mass-action orders 0, 1, 2).
+ *   products  [M x S]: molecules of s produced by j, entries 0..SSA_STATE_MAX.
+ *   rates     [M]: stochastic rate constants c_j, finite and >= 0.
+ *   x0        [S]: initial counts, 0..SSA_STATE_MAX.
+ * The propensity of j in state x is c_j * prod_s C(x_s, reactants[j][s]);
+ * the state change of j is products[j] - reactants[j].
+ * All arrays are host memory and are copied.  *out receives the model.
+ * Errors: SSA_EINVAL (bad sizes or entries), SSA_ENOMEM.
+ */
+ssa_status ssa_model_create(int32_t n_species, int32_t n_reactions, const int32_t* reactants,
+                            const int32_t* products, const double* rates, const int32_t* x0,
+                            ssa_model** out);
+
+/* Releases a model and its device copies.  NULL is ignored.  No run using the
+ * model may be pending on any stream. */
+void ssa_model_destroy(ssa_model* model);
+
+/* Sizes of a model. */
+ssa_status ssa_model_info(const ssa_model* model, int32_t* n_species, int32_t* n_reactions);
+
+/* Device scratch bytes ssa_ensemble_run needs for these arguments (the
+ * per-grid difference sums, the work counter and the totals). */
+ssa_status ssa_ensemble_workspace_size(const ssa_model* model, int64_t n_traj, int32_t n_grid,
+                                       const ssa_run_opts* opts, size_t* bytes);
+
+/*
+ * Runs n_traj independent trajectories (Sec. 2) of `model` from its x0 over
+ * [0, t_end] and reduces them on the grid (Sec. 3.2.1):
+ *   sum1[k][s] = sum_i X_i,s(g_k),  sum2[k][s] = sum_i X_i,s(g_k)^2   (int64)
+ *   mean = sum1 / N,  var = (N sum2 - sum1^2) / (N (N - 1))           (FP64)
+ * where X_i(g) is trajectory i's state after every event with time <= g.
+ * Trajectory i uses the Philox4x64-10 stream keyed by (seed, opts->stream_id)
+ * with counter (event pair, traj_offset + i, 0, 0), so any trajectory can be
+ * reproduced alone and shards by traj_offset add up exactly.
+ *   n_traj >= 1 (var is NaN when n_traj == 1); t_end > 0 and finite;
+ *   n_grid >= 1; grid [n_grid] ascending, grid[0] >= 0, grid[n_grid-1] <= t_end,
+ *     or NULL for g_k = (k * t_end) / (n_grid - 1) (g_0 = t_end if n_grid == 1).
+ *   mean, var [G x S] doubles; sum1, sum2 [G x S] int64 or NULL.
+ *   stats: host struct or NULL.
+ * In SSA_PREC_FP64 the results are bit-identical to the plain CPU statement
+ * of the same arithmetic (the oracle shipped with the tests).
+ * Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA, SSA_EUNSUPPORTED,
+ * SSA_EOVERFLOW (only detectable when the call waits: host memory or stats).
+ */
+ssa_status ssa_ensemble_run(const ssa_model* model, int64_t n_traj, double t_end, int32_t n_grid,
+                            const double* grid, uint64_t seed, const ssa_run_opts* opts,
+                            double* mean, double* var, int64_t* sum1, int64_t* sum2,
+                            ssa_run_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSA_H_ */
