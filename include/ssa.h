@@ -173,6 +173,46 @@ ssa_status ssa_ensemble_run(const ssa_model* model, int64_t n_traj, double t_end
                             double* mean, double* var, int64_t* sum1, int64_t* sum2,
                             ssa_run_stats* stats);
 
+/*
+ * Size of the fixed device scratch used by ssa_ensemble_run_noalloc: 4 MiB,
+ * held by every GPU that loads the library until the process exits.
+ */
+#define SSA_NOALLOC_SCRATCH_BYTES ((size_t)4 << 20)
+
+/*
+ * ssa_ensemble_run_noalloc — the same computation as ssa_ensemble_run, for
+ * callers that cannot allocate device memory during the call.  The paper has
+ * no counterpart; this exists for deployment.  Such callers include code whose
+ * device memory is owned and pre-sized by another runtime, plugins that the
+ * host process bars from the allocator, and latency-bound loops that must not
+ * block on an allocation.
+ *
+ * It calls no cudaMalloc, cudaMallocAsync, cudaFree or other allocating
+ * routine.  Its scratch (work counter, totals, per-grid difference sums, the
+ * uniform grid and the model's tables) lives in one fixed device array of
+ * SSA_NOALLOC_SCRATCH_BYTES per GPU.  The caller passes all inputs and outputs:
+ *   opts->memory must be SSA_MEM_DEVICE; grid (NULL for the uniform grid),
+ *   mean, var [G x S] and the optional sum1, sum2 [G x S] and per-trajectory
+ *   outputs are device pointers on the current device.  stats is a host
+ *   struct or NULL; when non-NULL the call waits for the stream (kernel_ms is
+ *   reported as 0).  opts->workspace is ignored.
+ * Limits: 16 * n_grid * n_species + 8 * n_grid + the model's tables (plus
+ * alignment) must fit in SSA_NOALLOC_SCRATCH_BYTES, else SSA_EINVAL with a
+ * message giving the bytes needed.  Networks with at most 16 reactions, FP64.
+ * Sharing: every call uses the same array and overwrites what the previous
+ * call left there; each call clears what must start at zero on its own stream.
+ * Calls whose GPU work overlaps (several streams or host threads on one
+ * device) race and give wrong results, so serialise them.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current).  Make that first call
+ * before any stream capture on the device.
+ * Results are bit-identical to ssa_ensemble_run with the same arguments.
+ */
+ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n_traj, double t_end, int32_t n_grid,
+                                    const double* grid, uint64_t seed, const ssa_run_opts* opts,
+                                    double* mean, double* var, int64_t* sum1, int64_t* sum2,
+                                    ssa_run_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ TRAJ_TRUNCATED, TRAJ_OVERFLOW = 1, 2
 # Functions declared in include/ssa.h.
 EXPORTS = [
     "ssa_status_string", "ssa_last_error", "ssa_run_opts_init", "ssa_model_create", "ssa_model_destroy",
-    "ssa_model_info", "ssa_ensemble_workspace_size", "ssa_ensemble_run",
+    "ssa_model_info", "ssa_ensemble_workspace_size", "ssa_ensemble_run", "ssa_ensemble_run_noalloc",
 ]
 
 
@@ -88,6 +88,8 @@ def lib():
         L.ssa_ensemble_run.argtypes = [vp, i64, f64, i32, vp, u64, ctypes.POINTER(RunOpts), vp, vp, vp, vp,
                                        ctypes.POINTER(RunStats)]
         L.ssa_ensemble_run.restype = ctypes.c_int
+        L.ssa_ensemble_run_noalloc.argtypes = L.ssa_ensemble_run.argtypes
+        L.ssa_ensemble_run_noalloc.restype = ctypes.c_int
         _lib = L
         return L
 

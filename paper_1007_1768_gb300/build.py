@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libssa.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["ssa_api.cu", "ssa_kernels.cu"]
+SOURCES = ["ssa_api.cu", "ssa_kernels.cu", "ssa_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

@@ -509,3 +509,32 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ internal accessors
+// Used by entry points defined in other translation units (ssa_noalloc.cu).
+namespace ssa_impl {
+
+ssa_status record_error(ssa_status st, const char* msg) { return fail(st, "%s", msg); }
+
+void clear_error() { g_last_error.clear(); }
+
+bool model_image_view(const ssa_model* m, ModelImageView* v) {
+  if (!m || !v) return false;
+  v->S = m->S;
+  v->M = m->M;
+  v->nnz = (int32_t)m->nu_idx.size();
+  v->ndep = (int32_t)m->dep_idx.size();
+  v->image = m->image.data();
+  v->bytes = m->image.size();
+  v->off_c = m->off_c;
+  v->off_rinfo = m->off_rinfo;
+  v->off_nu_ptr = m->off_nu_ptr;
+  v->off_nu_idx = m->off_nu_idx;
+  v->off_nu_val = m->off_nu_val;
+  v->off_x0 = m->off_x0;
+  v->off_dep_ptr = m->off_dep_ptr;
+  v->off_dep_idx = m->off_dep_idx;
+  return true;
+}
+
+}  // namespace ssa_impl

@@ -106,6 +106,22 @@ cudaError_t launch_uniform_grid(double* grid, int G, double t_end, cudaStream_t 
 constexpr int kThreadMaxM = 16;
 cudaError_t thread_kernel_set_smem(int M, bool shared_d, size_t smem_bytes);
 
+// Host image of a model's device tables (see DevModel for the layout), for
+// entry points that place the tables themselves.
+struct ModelImageView {
+  int32_t S, M, nnz, ndep;
+  const unsigned char* image;
+  size_t bytes;
+  size_t off_c, off_rinfo, off_nu_ptr, off_nu_idx, off_nu_val, off_x0, off_dep_ptr, off_dep_idx;
+};
+
+}  // namespace ssa_impl
+
+struct ssa_model;
+
+namespace ssa_impl {
+// Accessors implemented in ssa_api.cu.
+bool model_image_view(const ssa_model* m, ModelImageView* v);
 }  // namespace ssa_impl
 
 #endif  // SSA_INTERNAL_H_

@@ -1,0 +1,226 @@
+// ssa_ensemble_run_noalloc: the ensemble run for callers that must not
+// allocate device memory.
+//
+// Some hosts cannot call cudaMalloc at the moment they want a result.  Examples:
+// code running inside a memory pool that another runtime owns and sizes up
+// front; plugins that a host process forbids from touching the allocator;
+// real-time loops that must not block on allocation.  This entry point
+// serves them.  It allocates nothing: no cudaMalloc, no cudaMallocAsync, no
+// cudaFree, no allocating library call.  Its scratch memory (work counter,
+// totals, per-grid difference sums, the uniform grid and the model tables)
+// lives in one file-scope device array of fixed size, kNoAllocScratchBytes,
+// that every GPU loading the library holds until the process exits.  The
+// caller passes every input and output buffer.
+//
+// Because every call shares that one array, calls whose work overlaps on the
+// GPU (different streams, or different host threads, on the same device) race
+// and give wrong results.  Calls must be serialised: issue them on one stream,
+// or wait for one before starting the next.  Each call clears the parts that
+// must start at zero (counter, totals, difference sums) on its own stream
+// before its kernels run.
+//
+// The first call on a device looks up the device address of the array with
+// cudaGetSymbolAddress (with that device current) and caches it.  That first
+// call should therefore come before any stream capture on that device.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ssa.h"
+#include "ssa_internal.h"
+
+namespace ssa_impl {
+ssa_status record_error(ssa_status st, const char* msg);
+void clear_error();
+}  // namespace ssa_impl
+
+using namespace ssa_impl;
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = SSA_NOALLOC_SCRATCH_BYTES;
+constexpr int kMaxDevices = 64;
+
+// The scratch array.  Host code must not use its name as an address: on the
+// host it is only a stand-in for the device symbol.  The device address comes
+// from cudaGetSymbolAddress in scratch_on_device().
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_mu;
+unsigned char* g_scratch_ptr[kMaxDevices] = {};
+int g_sms[kMaxDevices] = {};
+size_t g_smem_optin[kMaxDevices] = {};
+
+ssa_status scratch_on_device(int dev, unsigned char** out, int* sms, size_t* smem_optin) {
+  if (dev < 0 || dev >= kMaxDevices) return record_error(SSA_EUNSUPPORTED, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      return record_error(SSA_ECUDA, "cudaGetSymbolAddress(noalloc scratch) failed");
+    int n_sms = 0, smem = 0;
+    e = cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return record_error(SSA_ECUDA, "cudaDeviceGetAttribute failed");
+    g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+    g_sms[dev] = n_sms;
+    g_smem_optin[dev] = (size_t)smem;
+  }
+  *out = g_scratch_ptr[dev];
+  *sms = g_sms[dev];
+  *smem_optin = g_smem_optin[dev];
+  return SSA_OK;
+}
+
+}  // namespace
+
+extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n_traj, double t_end,
+                                               int32_t n_grid, const double* grid, uint64_t seed,
+                                               const ssa_run_opts* opts, double* mean, double* var,
+                                               int64_t* sum1, int64_t* sum2, ssa_run_stats* stats) {
+  clear_error();
+  ssa_run_opts o;
+  if (opts) o = *opts; else ssa_run_opts_init(&o);
+  ModelImageView mv;
+  if (!model || !model_image_view(model, &mv)) return record_error(SSA_EINVAL, "model is NULL");
+  if (n_traj < 1) return record_error(SSA_EINVAL, "n_traj must be >= 1");
+  if (!(t_end > 0.0) || !std::isfinite(t_end)) return record_error(SSA_EINVAL, "t_end must be finite and > 0");
+  if (n_grid < 1) return record_error(SSA_EINVAL, "n_grid must be >= 1");
+  if (!mean || !var) return record_error(SSA_EINVAL, "mean and var must not be NULL");
+  if (o.memory != SSA_MEM_DEVICE)
+    return record_error(SSA_EINVAL, "ssa_ensemble_run_noalloc takes device buffers only (memory = SSA_MEM_DEVICE)");
+  if (o.precision != SSA_PREC_FP64) return record_error(SSA_EUNSUPPORTED, "only SSA_PREC_FP64 is built");
+  if (o.schedule == SSA_SCHED_WARP || mv.M > kThreadMaxM)
+    return record_error(SSA_EUNSUPPORTED, "networks with more than 16 reactions are not supported here");
+  if (o.block_threads < 0 || o.block_threads > 512 || (o.block_threads % 32) != 0)
+    return record_error(SSA_EINVAL, "block_threads must be 0 or a multiple of 32 up to 512");
+  if (o.grid_blocks < 0) return record_error(SSA_EINVAL, "grid_blocks must be >= 0");
+
+  // scratch layout inside the fixed array
+  const size_t gs = (size_t)n_grid * (size_t)mv.S;
+  auto up = [](size_t v) { return align_up(v, 256); };
+  const size_t off_counter = 0;
+  const size_t off_stats = up(off_counter + 8);
+  const size_t off_d1 = up(off_stats + 8 * kStatCount);
+  const size_t off_d2 = up(off_d1 + 8 * gs);
+  const size_t off_grid = up(off_d2 + 8 * gs);
+  const size_t off_model = up(off_grid + 8 * (size_t)n_grid);
+  const size_t need = up(off_model + mv.bytes);
+  if (gs > ((size_t)1 << 31) || need > kNoAllocScratchBytes) {
+    char msg[256];
+    snprintf(msg, sizeof msg,
+             "ssa_ensemble_run_noalloc needs %zu bytes of scratch for n_grid = %d and %d species; its fixed "
+             "scratch holds %zu bytes (SSA_NOALLOC_SCRATCH_BYTES)",
+             need, n_grid, mv.S, kNoAllocScratchBytes);
+    return record_error(SSA_EINVAL, msg);
+  }
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return record_error(SSA_ECUDA, "cudaGetDevice failed");
+  unsigned char* scratch = nullptr;
+  int sms = 0;
+  size_t smem_optin = 0;
+  ssa_status st = scratch_on_device(dev, &scratch, &sms, &smem_optin);
+  if (st != SSA_OK) return st;
+  cudaStream_t stream = static_cast<cudaStream_t>(o.cuda_stream);
+
+  // launch shape (same rule as ssa_ensemble_run)
+  int threads = o.block_threads;
+  if (threads == 0) {
+    const int64_t per_sm = (n_traj + sms - 1) / sms;
+    threads = (int)std::min<int64_t>(512, std::max<int64_t>(64, (per_sm + 31) / 32 * 32));
+  }
+  ThreadSmem lay_sh = thread_smem_layout(mv.S, mv.M, mv.nnz, n_grid, threads, true);
+  bool shared_d;
+  if (o.reduce == SSA_REDUCE_SHARED) {
+    if (lay_sh.total > smem_optin) return record_error(SSA_EINVAL, "shared reduction does not fit");
+    shared_d = true;
+  } else if (o.reduce == SSA_REDUCE_GLOBAL) {
+    shared_d = false;
+  } else {
+    shared_d = lay_sh.total <= smem_optin;
+  }
+  const ThreadSmem lay = shared_d ? lay_sh : thread_smem_layout(mv.S, mv.M, mv.nnz, n_grid, threads, false);
+  int blocks = o.grid_blocks;
+  if (blocks == 0) {
+    const int64_t want = (n_traj + threads - 1) / threads;
+    const int per_sm = shared_d ? 1 : std::max(1, std::min(8, (int)(smem_optin / std::max<size_t>(lay.total, 1))));
+    blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per_sm));
+  }
+
+  auto cuda_fail = [](cudaError_t e, const char* what) {
+    char msg[256];
+    snprintf(msg, sizeof msg, "%s: %s", what, cudaGetErrorString(e));
+    return record_error(SSA_ECUDA, msg);
+  };
+  cudaError_t e = thread_kernel_set_smem(mv.M, shared_d, lay.total);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  // counter, totals and difference sums start at zero on every call
+  e = cudaMemsetAsync(scratch, 0, off_grid, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(scratch)");
+  e = cudaMemcpyAsync(scratch + off_model, mv.image, mv.bytes, cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(model tables)");
+  const double* d_grid = grid;
+  if (!d_grid) {
+    double* g = reinterpret_cast<double*>(scratch + off_grid);
+    e = launch_uniform_grid(g, n_grid, t_end, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "uniform grid kernel");
+    d_grid = g;
+  }
+
+  const unsigned char* b = scratch + off_model;
+  RunArgs a;
+  a.m.S = mv.S;
+  a.m.M = mv.M;
+  a.m.nnz = mv.nnz;
+  a.m.ndep = mv.ndep;
+  a.m.c = reinterpret_cast<const double*>(b + mv.off_c);
+  a.m.rinfo = reinterpret_cast<const int32_t*>(b + mv.off_rinfo);
+  a.m.nu_ptr = reinterpret_cast<const int32_t*>(b + mv.off_nu_ptr);
+  a.m.nu_idx = reinterpret_cast<const int32_t*>(b + mv.off_nu_idx);
+  a.m.nu_val = reinterpret_cast<const int32_t*>(b + mv.off_nu_val);
+  a.m.x0 = reinterpret_cast<const int32_t*>(b + mv.off_x0);
+  a.m.dep_ptr = reinterpret_cast<const int32_t*>(b + mv.off_dep_ptr);
+  a.m.dep_idx = reinterpret_cast<const int32_t*>(b + mv.off_dep_idx);
+  a.G = n_grid;
+  a.N = n_traj;
+  a.traj_offset = o.traj_offset;
+  a.seed = seed;
+  a.stream_id = o.stream_id;
+  a.max_events = (o.max_events > 0) ? o.max_events : SSA_DEFAULT_MAX_EVENTS;
+  a.t_end = t_end;
+  a.grid = d_grid;
+  a.D1 = reinterpret_cast<unsigned long long*>(scratch + off_d1);
+  a.D2 = reinterpret_cast<unsigned long long*>(scratch + off_d2);
+  a.counter = reinterpret_cast<unsigned long long*>(scratch + off_counter);
+  a.stats = reinterpret_cast<unsigned long long*>(scratch + off_stats);
+  a.traj_events = o.traj_events;
+  a.traj_hash = o.traj_hash;
+  a.traj_flags = o.traj_flags;
+  a.device_totals = reinterpret_cast<unsigned long long*>(o.device_totals);
+
+  e = launch_thread_kernel(a, blocks, threads, shared_d, lay.total, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "simulation kernel");
+  e = launch_finalize(a.D1, a.D2, n_grid, mv.S, n_traj, a.m.x0, mean, var, sum1, sum2, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
+  if (!stats) return SSA_OK;
+
+  unsigned long long h[kStatCount] = {};
+  e = cudaMemcpyAsync(h, a.stats, sizeof h, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading totals");
+  stats->events = (int64_t)h[kStatEvents];
+  stats->truncated = (int64_t)h[kStatTruncated];
+  stats->overflowed = (int64_t)h[kStatOverflowed];
+  stats->max_x = (int64_t)h[kStatMaxX];
+  stats->kernel_ms = 0.0;
+  if (h[kStatOverflowed] > 0) return record_error(SSA_EOVERFLOW, "a trajectory stopped at the int32 state limit");
+  const long double bound = (long double)n_traj * (long double)h[kStatMaxX] * (long double)h[kStatMaxX];
+  if (bound >= 9.2233720368547758e18L) return record_error(SSA_EOVERFLOW, "N * max_x^2 may exceed int64 sums");
+  return SSA_OK;
+}
