@@ -53,7 +53,8 @@ def parse_args():
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--profile-small", action="store_true",
-                   help="one small step (16,384 trajectories) for an ncu capture; prints no bench line")
+                   help="one small step for an ncu capture (--profile-n trajectories); prints no bench line")
+    p.add_argument("--profile-n", type=int, default=16384)
     return p.parse_args()
 
 
@@ -182,7 +183,7 @@ def run_ours(args):
         dist.init_process_group("gloo")
         pg = dist
 
-    n = args.n_traj if not args.profile_small else 16384
+    n = args.n_traj if not args.profile_small else args.profile_n
     w = W.workload_hiv_shaped(n)
     model = ssa.Model.from_network(w.net)
     G, S, M = w.n_grid, w.net.n_species, w.net.n_reactions

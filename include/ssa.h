@@ -79,9 +79,9 @@ typedef struct ssa_run_opts {
   int32_t reduce;         /* SSA_REDUCE_* */
   int32_t block_threads;  /* threads per CTA; 0 = choose */
   int32_t grid_blocks;    /* CTAs; 0 = choose */
-  int64_t max_events;     /* events per trajectory before it is truncated; <= 0: SSA_DEFAULT_MAX_EVENTS */
+  int64_t max_events;     /* events per trajectory before it is truncated, < 2^32; <= 0: SSA_DEFAULT_MAX_EVENTS */
   uint64_t traj_offset;   /* id of the first trajectory; ids are traj_offset .. traj_offset + n_traj - 1 */
-  uint64_t stream_id;     /* second word of the random key (the first is the seed) */
+  uint64_t stream_id;     /* fourth word of the random counter, < 2^32 (e.g. a network index) */
   void* cuda_stream;      /* cudaStream_t to run on; NULL = the legacy default stream */
   void* workspace;        /* device scratch of workspace_bytes; NULL = allocated and freed on the stream */
   size_t workspace_bytes;
@@ -155,9 +155,10 @@ ssa_status ssa_ensemble_workspace_size(const ssa_model* model, int64_t n_traj, i
  *   sum1[k][s] = sum_i X_i,s(g_k),  sum2[k][s] = sum_i X_i,s(g_k)^2   (int64)
  *   mean = sum1 / N,  var = (N sum2 - sum1^2) / (N (N - 1))           (FP64)
  * where X_i(g) is trajectory i's state after every event with time <= g.
- * Trajectory i uses the Philox4x64-10 stream keyed by (seed, opts->stream_id)
- * with counter (event pair, traj_offset + i, 0, 0), so any trajectory can be
- * reproduced alone and shards by traj_offset add up exactly.
+ * Event n of trajectory id = traj_offset + i draws one Philox4x32-10 block
+ * with key (seed low word, seed high word) and counter (n, id low word, id
+ * high word, opts->stream_id), so any trajectory can be reproduced alone and
+ * shards by traj_offset add up exactly.
  *   n_traj >= 1 (var is NaN when n_traj == 1); t_end > 0 and finite;
  *   n_grid >= 1; grid [n_grid] ascending, grid[0] >= 0, grid[n_grid-1] <= t_end,
  *     or NULL for g_k = (k * t_end) / (n_grid - 1) (g_0 = t_end if n_grid == 1).

@@ -11,8 +11,9 @@ This module builds it with g++ (``-O2 -ffp-contract=off``), computes the
 integer constants of its fixed-point logarithm with Python integers, and wraps
 it with numpy.
 
-Pins (see ``tests/test_oracle_*.py``): Philox4x64-10 against numpy's
-independent ``Philox`` bit generator; the logarithm against mpmath and libm;
+Pins (see ``tests/test_oracle_*.py``): Philox4x32-10 against triton's
+independent implementation (run by its CPU interpreter); the logarithm
+against mpmath and libm;
 the sampler against closed forms (birth-death Poisson law, isomerisation
 binomial law, expected event count), the exact CTMC transient by matrix
 exponential on tiny networks, and the first-step law.
@@ -38,6 +39,7 @@ SCHEDULE_L = 0     # left-to-right a0 / prefix sums
 SCHEDULE_W32 = 1   # 32-lane chunked sums + Kogge-Stone scan
 FLAG_TRUNCATED = 1
 FLAG_OVERFLOW = 2
+MAX_EVENTS = (1 << 32) - 1  # the event index is a 32-bit Philox counter word
 
 
 # ---------------------------------------------------------------- constants
@@ -69,21 +71,19 @@ def _round_shift(v: int, shift: int) -> int:
 def log_constants():
     """Integer constants of the fixed-point -ln(u) (Tang-style table method).
 
-    F_i = 1 + (2i+1)/256 for i in 0..127.
-      inv[i]    = round(2^64 / F_i) = round(2^72 / (257 + 2i))
-      lnf[i]    = round(2^64 ln F_i), ln F_i = 2 atanh((2i+1) / (513 + 2i))
-      ln2       = round(2^64 ln 2),   ln 2 = 2 atanh(1/3)
-      horner[m] = round((-1)^(m+1) 2^62 / m), m = 1..7 (index 0 unused)
+    F_i = 1 + (2i+1)/1024 for i in 0..511.
+      inv[i] = round(2^64 / F_i) = round(2^74 / (1025 + 2i))
+      lnf[i] = round(2^64 ln F_i), ln F_i = 2 atanh((2i+1) / (2049 + 2i))
+      ln2    = round(2^64 ln 2),   ln 2 = 2 atanh(1/3)
+      k3, k5 = round(2^31 / 3), round(2^31 / 5)
     """
     W = 256
-    inv = [_round_shift((1 << 73) // (257 + 2 * i), 1) for i in range(128)]
-    lnf = [_round_shift(2 * _atanh_ratio_scaled(2 * i + 1, 513 + 2 * i, W), W - 64) for i in range(128)]
+    inv = [_round_shift((1 << 75) // (1025 + 2 * i), 1) for i in range(512)]
+    lnf = [_round_shift(2 * _atanh_ratio_scaled(2 * i + 1, 2049 + 2 * i, W), W - 64) for i in range(512)]
     ln2 = _round_shift(2 * _atanh_ratio_scaled(1, 3, W), W - 64)
-    horner = [0]
-    for m in range(1, 8):
-        mag = _round_shift((1 << 63) // m, 1) if (1 << 63) % m else (1 << 62) // m
-        horner.append(mag if m % 2 == 1 else -mag)
-    return inv, lnf, ln2, horner
+    k3 = _round_shift((1 << 32) // 3, 1)
+    k5 = _round_shift((1 << 32) // 5, 1)
+    return inv, lnf, ln2, k3, k5
 
 
 # ---------------------------------------------------------------- build / load
@@ -125,10 +125,10 @@ def lib():
         L = ctypes.CDLL(path)
         vp = ctypes.c_void_p
         i32, i64, u64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
-        L.oracle_init_log.argtypes = [vp, vp, u64, vp]
+        L.oracle_init_log.argtypes = [vp, vp, u64, i64, i64]
         L.oracle_init_log.restype = ctypes.c_int
-        L.oracle_philox4x64.argtypes = [vp, vp, vp]
-        L.oracle_philox4x64.restype = None
+        L.oracle_philox4x32.argtypes = [vp, vp, vp]
+        L.oracle_philox4x32.restype = None
         L.oracle_neg_log_u.argtypes = [u64]
         L.oracle_neg_log_u.restype = f64
         L.oracle_neg_log_u_many.argtypes = [i64, vp, vp]
@@ -145,11 +145,10 @@ def lib():
         L.oracle_prefix.restype = None
         L.oracle_finalize.argtypes = [i64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
         L.oracle_finalize.restype = None
-        inv, lnf, ln2, horner = log_constants()
+        inv, lnf, ln2, k3, k5 = log_constants()
         a_inv = np.array(inv, dtype=np.uint64)
         a_lnf = np.array(lnf, dtype=np.uint64)
-        a_h = np.array(horner, dtype=np.int64)
-        rc = L.oracle_init_log(a_inv.ctypes.data, a_lnf.ctypes.data, ln2, a_h.ctypes.data)
+        rc = L.oracle_init_log(a_inv.ctypes.data, a_lnf.ctypes.data, ln2, k3, k5)
         if rc != 0:
             raise RuntimeError("oracle_init_log failed")
         _lib = L
@@ -157,12 +156,12 @@ def lib():
 
 
 # ---------------------------------------------------------------- wrappers
-def philox4x64(ctr, key) -> np.ndarray:
-    """Philox4x64-10 block for a 4-word counter and 2-word key."""
-    c = np.ascontiguousarray(ctr, dtype=np.uint64)
-    k = np.ascontiguousarray(key, dtype=np.uint64)
-    out = np.zeros(4, dtype=np.uint64)
-    lib().oracle_philox4x64(c.ctypes.data, k.ctypes.data, out.ctypes.data)
+def philox4x32(ctr, key) -> np.ndarray:
+    """Philox4x32-10 block for a 4-word counter and 2-word key (uint32)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().oracle_philox4x32(c.ctypes.data, k.ctypes.data, out.ctypes.data)
     return out
 
 
@@ -196,7 +195,7 @@ class OracleResult:
 
 
 def run(net, n_traj: int, t_end: float, n_grid: int, seed: int, grid=None, traj_begin: int = 0,
-        stream: int = 0, max_events: int = 1 << 62, schedule: int = SCHEDULE_L,
+        stream: int = 0, max_events: int = MAX_EVENTS, schedule: int = SCHEDULE_L,
         per_traj: bool = False, threads: int = 1, ids=None) -> OracleResult:
     """Runs trajectory ids [traj_begin, traj_begin + n_traj) (or the explicit
     list ``ids``) and returns the exact int64 grid sums S1 = sum x,
@@ -270,7 +269,7 @@ def run(net, n_traj: int, t_end: float, n_grid: int, seed: int, grid=None, traj_
 
 
 def trace(net, traj_id: int, t_end: float, n_grid: int, seed: int, grid=None, stream: int = 0,
-          max_events: int = 1 << 62, schedule: int = SCHEDULE_L, record_max: int = 100000):
+          max_events: int = MAX_EVENTS, schedule: int = SCHEDULE_L, record_max: int = 100000):
     """One trajectory: (event times, reaction indices, per-grid states [G, S], flags)."""
     L = lib()
     R, P, c, x0 = _model_arrays(net)

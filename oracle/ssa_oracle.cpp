@@ -22,12 +22,13 @@
 //     average and variance).
 //
 // Readings where the paper is silent (each also listed in the design notes):
-//   * the random source is Philox4x64-10 (Salmon et al., SC'11), key =
-//     (seed, stream), counter = (event pair index, trajectory id, domain, 0);
-//     event n uses words (0,1) of pair n/2 when n is even, (2,3) when odd;
-//   * u(w) = (2*(w >> 12) + 1) * 2^-53, exactly representable, in (0, 1);
+//   * the random source is Philox4x32-10 (Salmon et al., SC'11), one block
+//     per event: key = (seed low word, seed high word), counter = (event
+//     index n, trajectory id low word, trajectory id high word, stream id);
+//   * r1 = u(w0, w1), r2 = u(w2, w3) with u(a, b) = (2 m + 1) 2^-53,
+//     m = (a << 20) | (b >> 12), exactly representable, in (0, 1);
 //   * -ln(r1) is a fixed-point table-driven logarithm (Tang, ACM TOMS 16(4),
-//     1990: table of ln F_i and 1/F_i, short series for ln(1+r));
+//     1990: 512-cell table of ln F_i and 1/F_i, short series for ln(1+r));
 //   * h_j = prod_s C(x_s, R_js); a_j = c_j * (double)h_j;
 //     a0 and the selection prefix sums are left-to-right FP64 sums (schedule
 //     L) or the 32-lane chunked scan described at w32_prefix() (schedule W32);
@@ -48,76 +49,88 @@ namespace {
 typedef unsigned __int128 u128;
 typedef __int128 i128;
 
-// ---------------------------------------------------------------- Philox4x64-10
+// ---------------------------------------------------------------- Philox4x32-10
 // Round function and key schedule as published by Salmon, Moraes, Dror and
-// Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11 (Philox-4x64,
-// multipliers 0xD2E7470EE14C6C93 / 0xCA5A826395121157, Weyl increments from
-// the golden ratio and sqrt(3) - 1).
-const uint64_t kPhiloxM0 = 0xD2E7470EE14C6C93ULL;
-const uint64_t kPhiloxM1 = 0xCA5A826395121157ULL;
-const uint64_t kPhiloxW0 = 0x9E3779B97F4A7C15ULL;
-const uint64_t kPhiloxW1 = 0xBB67AE8584CAA73BULL;
+// Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11 (Philox-4x32:
+// multipliers 0xD2511F53 / 0xCD9E8D57, Weyl key increments 0x9E3779B9 /
+// 0xBB67AE85, ten rounds).
+const uint32_t kPhiloxM0 = 0xD2511F53u;
+const uint32_t kPhiloxM1 = 0xCD9E8D57u;
+const uint32_t kPhiloxW0 = 0x9E3779B9u;
+const uint32_t kPhiloxW1 = 0xBB67AE85u;
 
-void philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4]) {
-  uint64_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
-  uint64_t k0 = key_in[0], k1 = key_in[1];
+void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
   for (int round = 0; round < 10; ++round) {
     if (round > 0) {
       k0 += kPhiloxW0;
       k1 += kPhiloxW1;
     }
-    u128 p0 = (u128)kPhiloxM0 * c0;
-    u128 p1 = (u128)kPhiloxM1 * c2;
-    uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
-    uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
-    uint64_t n0 = hi1 ^ c1 ^ k0;
-    uint64_t n1 = lo1;
-    uint64_t n2 = hi0 ^ c3 ^ k1;
-    uint64_t n3 = lo0;
-    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * c0;
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
   }
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
 // ------------------------------------------------------- fixed-point -ln(u)
 // Constants handed in by the Python side (integers, see oracle/__init__.py):
-//   inv[i] = round(2^64 / F_i), lnf[i] = round(2^64 ln F_i), F_i = 1 + (2i+1)/256,
-//   ln2 = round(2^64 ln 2), horner[m] = round((-1)^(m+1) 2^62 / m), m = 1..7.
+//   inv[i] = round(2^64 / F_i), lnf[i] = round(2^64 ln F_i), F_i = 1 + (2i+1)/1024,
+//   i = 0..511; ln2 = round(2^64 ln 2); k3 = round(2^31 / 3), k5 = round(2^31 / 5).
 struct LogTables {
-  uint64_t inv[128];
-  uint64_t lnf[128];
+  uint64_t inv[512];
+  uint64_t lnf[512];
   uint64_t ln2;
-  int64_t horner[8];
+  int64_t k3, k5;
   bool ready;
 };
 LogTables g_log = {};
 
 // E = -ln(q * 2^-53) for odd q in [1, 2^53).
 //   q = 2^e (1 + f), f in [0, 1) held as Q0.64;
-//   1 + f = F_i (1 + r), F_i the table point of f's top 7 bits, r = (f - c_i) / F_i;
-//   -ln(u) = (53 - e) ln 2 - ln F_i - ln(1 + r), ln(1 + r) by its Taylor series
-//   to r^7 (|r| < 2^-8, remainder < 2^-67), evaluated in Q1.62 by Horner.
-// The result is formed in Q.64 (units of 2^-64) and rounded once to double.
+//   1 + f = F_i (1 + r), F_i the centre of f's cell (top 9 bits of f),
+//   r = (f - c_i) / F_i, |r| < 2^-10, formed as floor(d * inv_i / 2^64);
+//   -ln(u) = (53 - e) ln 2 - ln F_i - ln(1 + r);
+//   ln(1 + r) = r - r^2/2 + r^3 w,  w = 1/3 - r/4 + r^2/5 (series of ln(1 + r);
+//   the omitted terms are below 2^-62), with r^2 and r^3 in Q.64 and w in
+//   Q1.31 (32-bit; its error times |r^3| < 2^-30 stays below 2^-61).
+// Every floor below is an arithmetic shift of a two's-complement value.  The
+// sum is formed in Q.64 (units of 2^-64) and rounded once to double.
 double neg_log_u(uint64_t q) {
-  int e = 63 - __builtin_clzll(q);                 // floor(log2 q), 0..52
-  uint64_t f = (q << (63 - e)) << 1;               // fraction bits of q / 2^e
-  int i = (int)(f >> 57);                          // table index, top 7 bits
-  uint64_t center = ((uint64_t)(2 * i + 1)) << 56; // (2i+1)/256 in Q.64
-  int64_t d = (int64_t)(f - center);               // f - c_i, |d| < 2^-8
-  // r = d / F_i  ~  floor(d * inv_i / 2^64)
-  int64_t r = (int64_t)(((i128)d * (i128)(u128)g_log.inv[i]) >> 64);
-  int64_t acc = g_log.horner[7];
-  for (int m = 6; m >= 1; --m) acc = g_log.horner[m] + (int64_t)(((i128)acc * (i128)r) >> 64);
-  int64_t ln1p = (int64_t)(((i128)acc * (i128)r) >> 62);  // r * acc in Q.64
-  i128 E = (i128)(53 - e) * (i128)(u128)g_log.ln2 - (i128)(u128)g_log.lnf[i] - (i128)ln1p;
-  u128 Eu = (u128)E;
+  const int e = 63 - __builtin_clzll(q);                 // floor(log2 q), 0..52
+  const uint64_t f = (q << (63 - e)) << 1;               // fraction bits of q / 2^e
+  const int i = (int)(f >> 55);                          // cell index, top 9 bits
+  const uint64_t center = ((uint64_t)(2 * i + 1)) << 54; // (2i+1)/1024 in Q.64
+  const int64_t d = (int64_t)(f - center);               // f - c_i, |d| <= 2^-10
+  const int64_t r = (int64_t)(((i128)d * (i128)(u128)g_log.inv[i]) >> 64);
+  const int64_t r2 = (int64_t)(((i128)r * (i128)r) >> 64);
+  const int64_t r3 = (int64_t)(((i128)r2 * (i128)r) >> 64);
+  // w = 1/3 - r/4 + r^2/5 in Q1.31
+  const int32_t rq = (int32_t)(r >> 33);                 // r in Q.31
+  const int32_t r2q = (int32_t)(r2 >> 33);               // r^2 in Q.31
+  const int32_t w = (int32_t)g_log.k3 - (rq >> 2) + (int32_t)(((int64_t)r2q * g_log.k5) >> 31);
+  // r^3 w in Q.64: (r3 >> 4) * w >> 27
+  const int64_t t3 = ((r3 >> 4) * (int64_t)w) >> 27;
+  const int64_t ln1p = r - (r2 >> 1) + t3;
+  const i128 E = (i128)(53 - e) * (i128)(u128)g_log.ln2 - (i128)(u128)g_log.lnf[i] - (i128)ln1p;
+  const u128 Eu = (u128)E;
   if ((Eu >> 64) == 0) return (double)(uint64_t)Eu * 0x1p-64;
   return (double)(uint64_t)(Eu >> 6) * 0x1p-58;
 }
 
-// u(w) = (2 * (w >> 12) + 1) * 2^-53
-inline uint64_t odd53(uint64_t w) { return ((w >> 12) << 1) | 1ULL; }
-inline double uniform_open(uint64_t w) { return (double)odd53(w) * 0x1p-53; }
+// u(a, b) = (2 * ((a << 20) | (b >> 12)) + 1) * 2^-53 from two 32-bit words:
+// 52 random bits, exact in double, strictly inside (0, 1).
+inline uint64_t odd53(uint32_t a, uint32_t b) {
+  return ((((uint64_t)a << 20) | (uint64_t)(b >> 12)) << 1) | 1ULL;
+}
 
 // --------------------------------------------------------------- model
 struct Model {
@@ -201,8 +214,8 @@ TrajResult run_one(const Model& m, uint64_t traj_id, double t_end, int G, const 
   std::vector<int64_t> x(m.S);
   for (int s = 0; s < m.S; ++s) { x[s] = m.x0[s]; if (x[s] > res.max_x) res.max_x = x[s]; }
   std::vector<double> a(m.M), prefix(m.M);
-  const uint64_t key[2] = {seed, stream};
-  uint64_t words[4] = {0, 0, 0, 0};
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t words[4] = {0, 0, 0, 0};
   double t = 0.0;
   int64_t n = 0;
   int k = 0;
@@ -225,16 +238,12 @@ TrajResult run_one(const Model& m, uint64_t traj_id, double t_end, int G, const 
       w32_prefix(a, m.M, prefix, &a0);
     }
     // random numbers for event n
-    if ((n & 1) == 0) {
-      const uint64_t ctr[4] = {(uint64_t)(n >> 1), traj_id, 0, 0};
-      philox4x64_10(ctr, key, words);
-    }
-    const uint64_t wa = (n & 1) ? words[2] : words[0];
-    const uint64_t wb = (n & 1) ? words[3] : words[1];
+    const uint32_t ctr[4] = {(uint32_t)n, (uint32_t)traj_id, (uint32_t)(traj_id >> 32), (uint32_t)stream};
+    philox4x32_10(ctr, key, words);
     // next event time (Sec. 2: the time at which the next transition occurs)
     double t_next;
     if (a0 > 0.0) {
-      double E = neg_log_u(odd53(wa));
+      double E = neg_log_u(odd53(words[0], words[1]));
       t_next = t + E / a0;
     } else {
       t_next = std::numeric_limits<double>::infinity();
@@ -242,7 +251,7 @@ TrajResult run_one(const Model& m, uint64_t traj_id, double t_end, int G, const 
     emit_until(t_next);
     if (t_next > t_end) break;
     // select the transition: smallest j with prefix_j > r2 * a0
-    const double target = uniform_open(wb) * a0;
+    const double target = ((double)odd53(words[2], words[3]) * 0x1p-53) * a0;
     int jsel = -1;
     for (int j = 0; j < m.M; ++j) {
       if (prefix[j] > target) { jsel = j; break; }
@@ -291,16 +300,17 @@ bool build_model(int S, int M, const int32_t* R, const int32_t* P, const double*
 
 extern "C" {
 
-int oracle_init_log(const uint64_t* inv, const uint64_t* lnf, uint64_t ln2, const int64_t* horner) {
-  for (int i = 0; i < 128; ++i) { g_log.inv[i] = inv[i]; g_log.lnf[i] = lnf[i]; }
+int oracle_init_log(const uint64_t* inv, const uint64_t* lnf, uint64_t ln2, int64_t k3, int64_t k5) {
+  for (int i = 0; i < 512; ++i) { g_log.inv[i] = inv[i]; g_log.lnf[i] = lnf[i]; }
   g_log.ln2 = ln2;
-  for (int m = 0; m < 8; ++m) g_log.horner[m] = horner[m];
+  g_log.k3 = k3;
+  g_log.k5 = k5;
   g_log.ready = true;
   return 0;
 }
 
-void oracle_philox4x64(const uint64_t* ctr, const uint64_t* key, uint64_t* out) {
-  philox4x64_10(ctr, key, out);
+void oracle_philox4x32(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  philox4x32_10(ctr, key, out);
 }
 
 double oracle_neg_log_u(uint64_t q) { return neg_log_u(q); }

@@ -11,7 +11,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/ssa.h"
+#include "ssa.h"
 #include "ssa_internal.h"
 
 using namespace ssa_impl;
@@ -73,6 +73,8 @@ struct ssa_model {
   std::vector<unsigned char> image;
   size_t off_c = 0, off_rinfo = 0, off_nu_ptr = 0, off_nu_idx = 0, off_nu_val = 0, off_x0 = 0, off_dep_ptr = 0,
          off_dep_idx = 0;
+  SmallModel small = {};
+  bool has_small = false;
   std::mutex mu;
   void* dev_image[kMaxDevices] = {};
 };
@@ -141,6 +143,21 @@ void plan_model(ssa_model* m) {
     std::sort(deps.begin(), deps.end());
     for (int k : deps) m->dep_idx.push_back(k);
     m->dep_ptr[j + 1] = (int32_t)m->dep_idx.size();
+  }
+  // by-value tables of the thread kernel
+  m->has_small = (M <= kSmallMax && S <= kSmallMax);
+  if (m->has_small) {
+    SmallModel& sm = m->small;
+    std::memset(&sm, 0, sizeof sm);
+    for (int j = 0; j < M; ++j) {
+      sm.rinfo[j] = m->rinfo[j];
+      std::memcpy(&sm.cbits[j], &m->c[j], 8);
+      uint32_t mask = 0;
+      for (int q = m->dep_ptr[j]; q < m->dep_ptr[j + 1]; ++q) mask |= 1u << m->dep_idx[q];
+      sm.depmask[j] = mask;
+      for (int s = 0; s < S; ++s) sm.nu[j * kSmallMax + s] = m->P[(size_t)j * S + s] - m->R[(size_t)j * S + s];
+    }
+    for (int s = 0; s < S; ++s) sm.x0[s] = m->x0[s];
   }
   std::vector<unsigned char>& img = m->image;
   img.clear();
@@ -230,6 +247,8 @@ ssa_status check_run_args(const ssa_model* m, int64_t n_traj, double t_end, int3
   if (o.block_threads < 0 || o.block_threads > 512 || (o.block_threads % 32) != 0)
     return fail(SSA_EINVAL, "block_threads must be 0 or a multiple of 32 up to 512");
   if (o.grid_blocks < 0) return fail(SSA_EINVAL, "grid_blocks must be >= 0");
+  if (o.max_events > (int64_t)0xFFFFFFFFLL) return fail(SSA_EINVAL, "max_events must be below 2^32");
+  if (o.stream_id > 0xFFFFFFFFULL) return fail(SSA_EINVAL, "stream_id must be below 2^32");
   return SSA_OK;
 }
 
@@ -351,8 +370,9 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
     if (st != SSA_OK) return st;
   }
   if (o.precision != SSA_PREC_FP64) return fail(SSA_EUNSUPPORTED, "only SSA_PREC_FP64 is built");
-  if (o.schedule == SSA_SCHED_WARP || m->M > kThreadMaxM)
-    return fail(SSA_EUNSUPPORTED, "networks with more than %d reactions need the warp schedule", kThreadMaxM);
+  if (o.schedule == SSA_SCHED_WARP || !m->has_small)
+    return fail(SSA_EUNSUPPORTED, "networks with more than %d reactions or species need the warp schedule",
+                kThreadMaxM);
   const int64_t max_events = (o.max_events > 0) ? o.max_events : SSA_DEFAULT_MAX_EVENTS;
 
   int dev = 0;
@@ -365,34 +385,13 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
   if (st != SSA_OK) return st;
   cudaStream_t stream = static_cast<cudaStream_t>(o.cuda_stream);
 
-  // launch shape: enough lanes for the trajectories, at most one CTA per SM
-  // when the difference arrays are staged in shared memory
+  // launch shape
   const int S = m->S, G = n_grid;
-  int threads = o.block_threads;
-  if (threads == 0) {
-    const int64_t per_sm = (n_traj + di.sms - 1) / di.sms;
-    threads = (int)std::min<int64_t>(512, std::max<int64_t>(64, (per_sm + 31) / 32 * 32));
-  }
-  ThreadSmem lay_sh = thread_smem_layout(S, m->M, (int)m->nu_idx.size(), G, threads, true);
-  bool shared_d;
-  if (o.reduce == SSA_REDUCE_SHARED) {
-    if (lay_sh.total > di.smem_optin)
-      return fail(SSA_EINVAL, "shared reduction needs %zu bytes of shared memory (limit %zu)", lay_sh.total,
-                  di.smem_optin);
-    shared_d = true;
-  } else if (o.reduce == SSA_REDUCE_GLOBAL) {
-    shared_d = false;
-  } else {
-    shared_d = lay_sh.total <= di.smem_optin;
-  }
-  const ThreadSmem lay = shared_d ? lay_sh : thread_smem_layout(S, m->M, (int)m->nu_idx.size(), G, threads, false);
-  int blocks = o.grid_blocks;
-  if (blocks == 0) {
-    const int64_t need = (n_traj + threads - 1) / threads;
-    const int per_sm = shared_d ? 1 : std::max(1, std::min(8, (int)(di.smem_optin / std::max<size_t>(lay.total, 1))));
-    blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)di.sms * per_sm));
-  }
-  SSA_CUDA_TRY(thread_kernel_set_smem(m->M, shared_d, lay.total));
+  LaunchPlan plan;
+  if (const char* msg = plan_thread_launch(S, m->M, G, n_traj, di.sms, di.smem_optin, o.reduce, o.block_threads,
+                                           o.grid_blocks, &plan))
+    return fail(SSA_EINVAL, "%s", msg);
+  SSA_CUDA_TRY(thread_kernel_set_smem(m->M, S, plan.shared_d, plan.smem));
 
   // workspace
   const Workspace wl = workspace_layout(S, G, n_traj, o);
@@ -432,6 +431,7 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
   }
 
   RunArgs a;
+  a.sm = m->small;
   a.m = dm;
   a.G = G;
   a.N = n_traj;
@@ -449,6 +449,9 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
   a.traj_hash = host ? (o.traj_hash ? reinterpret_cast<uint64_t*>(ws + wl.thash) : nullptr) : o.traj_hash;
   a.traj_flags = host ? (o.traj_flags ? reinterpret_cast<int32_t*>(ws + wl.tflags) : nullptr) : o.traj_flags;
   a.device_totals = reinterpret_cast<unsigned long long*>(o.device_totals);
+  a.grid_uniform = (!grid && G >= 2 && G <= (1 << 20) && t_end < 1e30) ? 1 : 0;
+  a.grid_scale = (float)((double)(G - 1) / t_end);
+  a.grid_margin = (float)((double)G * 0x1p-21);
 
   double* d_mean = host ? reinterpret_cast<double*>(ws + wl.mean) : mean;
   double* d_var = host ? reinterpret_cast<double*>(ws + wl.var) : var;
@@ -462,7 +465,7 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
     SSA_RUN_TRY(cudaEventRecord(ev0, stream));
   }
   if (o.sim_event_begin) SSA_RUN_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.sim_event_begin), stream));
-  SSA_RUN_TRY(launch_thread_kernel(a, blocks, threads, shared_d, lay.total, stream));
+  SSA_RUN_TRY(launch_thread_kernel(a, plan.blocks, plan.threads, plan.shared_d, plan.smem, stream));
   if (o.sim_event_end) SSA_RUN_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.sim_event_end), stream));
   SSA_RUN_TRY(launch_finalize(a.D1, a.D2, G, S, n_traj, dm.x0, d_mean, d_var, d_s1, d_s2, stream));
   if (stats) SSA_RUN_TRY(cudaEventRecord(ev1, stream));
@@ -534,6 +537,7 @@ bool model_image_view(const ssa_model* m, ModelImageView* v) {
   v->off_x0 = m->off_x0;
   v->off_dep_ptr = m->off_dep_ptr;
   v->off_dep_idx = m->off_dep_idx;
+  v->small = m->has_small ? &m->small : nullptr;
   return true;
 }
 

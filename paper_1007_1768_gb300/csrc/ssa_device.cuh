@@ -10,28 +10,29 @@
 #include <cstdint>
 
 #include "ssa_logtab.h"
+#include "ssa_softfloat.cuh"
 
 namespace ssa_dev {
 
-// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
-// easy as 1, 2, 3", SC'11): 10 rounds of two 64x64->128 multiplies and a
-// key-dependent xor, key bumped by two Weyl increments between rounds.
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies and a
+// key-dependent xor, the key bumped by two Weyl increments between rounds.
 struct Words4 {
-  uint64_t w0, w1, w2, w3;
+  uint32_t w0, w1, w2, w3;
 };
 
-__device__ __forceinline__ Words4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
-                                                uint64_t k0, uint64_t k1) {
-  constexpr uint64_t kM0 = 0xD2E7470EE14C6C93ULL;
-  constexpr uint64_t kM1 = 0xCA5A826395121157ULL;
-  constexpr uint64_t kW0 = 0x9E3779B97F4A7C15ULL;
-  constexpr uint64_t kW1 = 0xBB67AE8584CAA73BULL;
+__device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                                uint32_t k1) {
+  constexpr uint32_t kM0 = 0xD2511F53u;
+  constexpr uint32_t kM1 = 0xCD9E8D57u;
+  constexpr uint32_t kW0 = 0x9E3779B9u;
+  constexpr uint32_t kW1 = 0xBB67AE85u;
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint64_t hi0 = __umul64hi(kM0, c0), lo0 = kM0 * c0;
-    const uint64_t hi1 = __umul64hi(kM1, c2), lo1 = kM1 * c2;
-    const uint64_t n0 = hi1 ^ c1 ^ k0;
-    const uint64_t n2 = hi0 ^ c3 ^ k1;
+    const uint32_t hi0 = __umulhi(kM0, c0), lo0 = kM0 * c0;
+    const uint32_t hi1 = __umulhi(kM1, c2), lo1 = kM1 * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
     c0 = n0;
     c1 = lo1;
     c2 = n2;
@@ -42,52 +43,42 @@ __device__ __forceinline__ Words4 philox4x64_10(uint64_t c0, uint64_t c1, uint64
   return Words4{c0, c1, c2, c3};
 }
 
-// Odd 53-bit integer q = 2 (w >> 12) + 1; the uniform variate is q * 2^-53.
-__device__ __forceinline__ uint64_t odd53(uint64_t w) { return ((w >> 12) << 1) | 1ULL; }
-
-// Exact q * 2^-53 for q < 2^53.
-__device__ __forceinline__ double uniform_from_odd53(uint64_t q) {
-  return __dmul_rn(__ull2double_rn(q), 0x1p-53);
+// q = 2 ((a << 20) | (b >> 12)) + 1: an odd 53-bit integer; the uniform
+// variate is q * 2^-53, exactly representable and strictly inside (0, 1).
+__device__ __forceinline__ uint64_t odd53(uint32_t a, uint32_t b) {
+  return ((((uint64_t)a << 20) | (uint64_t)(b >> 12)) << 1) | 1ULL;
 }
 
 // floor(d * v / 2^64) for signed d and unsigned v.
 __device__ __forceinline__ int64_t mulhi_su(int64_t d, uint64_t v) {
-  uint64_t h = __umul64hi((uint64_t)d, v);
-  if (d < 0) h -= v;
-  return (int64_t)h;
+  return (int64_t)(__umul64hi((uint64_t)d, v) - ((d < 0) ? v : 0ULL));
 }
 
 // E = -ln(q * 2^-53) for odd q in [1, 2^53), formed in units of 2^-64 and
-// rounded once to double.  q = 2^e (1 + f); the top 7 bits of f pick the cell
-// centre c_i and F_i = 1 + c_i; r = (f - c_i) / F_i with |r| < 2^-8;
-// E = (53 - e) ln 2 - ln F_i - ln(1 + r), ln(1 + r) by its series to r^7.
-// inv / lnf are the cell tables (kLogInv, kLogLnF), staged in shared memory.
-__device__ __forceinline__ double neg_log_u(uint64_t q, const uint64_t* __restrict__ inv,
-                                            const uint64_t* __restrict__ lnf) {
+// rounded once to double; returned as the double's bit pattern.
+//   q = 2^e (1 + f); the top 9 bits of f pick the cell centre c_i, F_i = 1 + c_i;
+//   r = (f - c_i) / F_i with |r| < 2^-10 (floor(d * inv_i / 2^64));
+//   E = (53 - e) ln 2 - ln F_i - ln(1 + r),
+//   ln(1 + r) = r - r^2/2 + r^3 w, w = 1/3 - r/4 + r^2/5 kept in 32-bit Q1.31
+//   (w only needs ~2^-31 since |r^3| < 2^-30), r^2 and r^3 in Q.64.
+// inv / lnf are the 512-cell tables of ssa_logtab.h, staged in shared memory.
+__device__ __forceinline__ uint64_t neg_log_u_bits(uint64_t q, const uint64_t* __restrict__ inv,
+                                                   const uint64_t* __restrict__ lnf) {
   const int e = 63 - __clzll((long long)q);
   const uint64_t f = (q << (63 - e)) << 1;
-  const int i = (int)(f >> 57);
-  const uint64_t center = ((uint64_t)(2 * i + 1)) << 56;
+  const int i = (int)(f >> 55);
+  const uint64_t center = ((uint64_t)(2 * i + 1)) << 54;
   const int64_t d = (int64_t)(f - center);
   const int64_t r = mulhi_su(d, inv[i]);
-  constexpr int64_t K1 = ssa_logtab::kTables.horner[1];
-  constexpr int64_t K2 = ssa_logtab::kTables.horner[2];
-  constexpr int64_t K3 = ssa_logtab::kTables.horner[3];
-  constexpr int64_t K4 = ssa_logtab::kTables.horner[4];
-  constexpr int64_t K5 = ssa_logtab::kTables.horner[5];
-  constexpr int64_t K6 = ssa_logtab::kTables.horner[6];
-  constexpr int64_t K7 = ssa_logtab::kTables.horner[7];
-  int64_t acc = K7;
-  acc = K6 + __mul64hi(acc, r);
-  acc = K5 + __mul64hi(acc, r);
-  acc = K4 + __mul64hi(acc, r);
-  acc = K3 + __mul64hi(acc, r);
-  acc = K2 + __mul64hi(acc, r);
-  acc = K1 + __mul64hi(acc, r);
-  // ln(1 + r) = (acc * r) >> 62 as a signed 128-bit product, fits in 64 bits
-  const uint64_t plo = (uint64_t)acc * (uint64_t)r;
-  const int64_t phi = __mul64hi(acc, r);
-  const int64_t ln1p = (int64_t)(((uint64_t)phi << 2) | (plo >> 62));
+  const int64_t r2 = __mul64hi(r, r);
+  const int64_t r3 = __mul64hi(r2, r);
+  constexpr int32_t K3 = ssa_logtab::kTables.k3;
+  constexpr int32_t K5 = ssa_logtab::kTables.k5;
+  const int32_t rq = (int32_t)(r >> 33);
+  const int32_t r2q = (int32_t)(r2 >> 33);
+  const int32_t w = K3 - (rq >> 2) + (int32_t)(((long long)r2q * K5) >> 31);
+  const int64_t t3 = ((r3 >> 4) * (int64_t)w) >> 27;
+  const int64_t ln1p = r - (r2 >> 1) + t3;
   // E = n ln2 - lnF_i - ln1p in 128 bits
   constexpr uint64_t LN2 = ssa_logtab::kTables.ln2;
   const uint64_t n = (uint64_t)(53 - e);
@@ -99,8 +90,11 @@ __device__ __forceinline__ double neg_log_u(uint64_t q, const uint64_t* __restri
   const uint64_t l1 = (uint64_t)ln1p;
   hi = hi - ((lo < l1) ? 1ULL : 0ULL) + ((ln1p < 0) ? 1ULL : 0ULL);
   lo -= l1;
-  if (hi == 0) return __dmul_rn(__ull2double_rn(lo), 0x1p-64);
-  return __dmul_rn(__ull2double_rn((hi << 58) | (lo >> 6)), 0x1p-58);
+  // the integer is >= 2^11 and its double >= 2^11, so scaling by 2^-64 or
+  // 2^-58 keeps it normal: subtract from the exponent field
+  const bool small = hi == 0;
+  const uint64_t v = small ? lo : ((hi << 58) | (lo >> 6));
+  return ssa_sf::u64_to_f64(v) - ((small ? 64ULL : 58ULL) << 52);
 }
 
 // Bit pattern of a double as a signed integer; for non-negative doubles (and

@@ -45,8 +45,21 @@ struct DevModel {
 // Slots of the per-run device totals.
 enum { kStatEvents = 0, kStatTruncated = 1, kStatOverflowed = 2, kStatMaxX = 3, kStatCount = 8 };
 
+// Small-network tables passed by value to the thread kernel (M <= 16,
+// S <= 16): reads with a per-reaction constant index come straight from the
+// kernel's parameter space.
+constexpr int kSmallMax = 16;
+struct SmallModel {
+  int32_t rinfo[kSmallMax];
+  unsigned long long cbits[kSmallMax];   // rates as double bit patterns
+  int32_t x0[kSmallMax];
+  uint32_t depmask[kSmallMax];           // reactions to recompute after j fires
+  int32_t nu[kSmallMax * kSmallMax];     // dense net change [j][s]
+};
+
 // Arguments of the simulation kernels.
 struct RunArgs {
+  SmallModel sm;
   DevModel m;
   int32_t G;
   int64_t N;
@@ -64,27 +77,28 @@ struct RunArgs {
   uint64_t* traj_hash;                // [N] or null
   int32_t* traj_flags;                // [N] or null
   unsigned long long* device_totals;  // [4] or null (caller's running totals)
+  int32_t grid_uniform;               // grid is g_k = k t_end / (G - 1): index found by estimate + exact fix
+  float grid_scale;                   // (G - 1) / t_end, for the estimate only
+  float grid_margin;                  // estimates closer than this to an integer are checked against the grid
 };
 
-// Shared-memory layout of the thread-per-trajectory kernel (bytes).
+// Shared-memory layout of the thread-per-trajectory kernel (bytes): log
+// cells, the dense net-change rows and dependency masks (read with the fired
+// reaction's index), and the difference sums when they fit.
+constexpr int kLogCells = 512;
 struct ThreadSmem {
-  size_t log_inv, log_lnf, c, rinfo, nu_ptr, nu_idx, nu_val, x, d1, d2, total;
+  size_t log_inv, log_lnf, nu, depmask, d1, d2, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline ThreadSmem thread_smem_layout(int S, int M, int nnz, int G, int threads,
-                                                         bool shared_d) {
+__host__ __device__ inline ThreadSmem thread_smem_layout(int maxm, int maxs, int S, int G, bool shared_d) {
   ThreadSmem L;
   size_t o = 0;
-  L.log_inv = o; o += 128 * 8;
-  L.log_lnf = o; o += 128 * 8;
-  L.c = o; o += align_up((size_t)M * 8, 16);
-  L.rinfo = o; o += align_up((size_t)M * 4, 16);
-  L.nu_ptr = o; o += align_up((size_t)(M + 1) * 4, 16);
-  L.nu_idx = o; o += align_up((size_t)nnz * 4, 16);
-  L.nu_val = o; o += align_up((size_t)nnz * 4, 16);
-  L.x = o; o += align_up((size_t)S * threads * 4, 16);
+  L.log_inv = o; o += kLogCells * 8;
+  L.log_lnf = o; o += kLogCells * 8;
+  L.nu = o; o += align_up((size_t)maxm * maxs * 4, 16);
+  L.depmask = o; o += align_up((size_t)maxm * 4, 16);
   if (shared_d) {
     L.d1 = o; o += (size_t)G * S * 8;
     L.d2 = o; o += (size_t)G * S * 8;
@@ -95,16 +109,28 @@ __host__ __device__ inline ThreadSmem thread_smem_layout(int S, int M, int nnz, 
   return L;
 }
 
+// Template buckets of the thread kernel: M rounded up to an even number, S to 4, 8 or 16.
+__host__ __device__ inline int bucket_m(int M) { return (M + 1) / 2 * 2; }
+__host__ __device__ inline int bucket_s(int S) { return S <= 4 ? 4 : (S <= 8 ? 8 : 16); }
+
 // Launch helpers (ssa_kernels.cu).  Return cudaSuccess or the launch error.
 cudaError_t launch_thread_kernel(const RunArgs& a, int blocks, int threads, bool shared_d,
                                  size_t smem_bytes, cudaStream_t stream);
+// per-S-bucket launchers (ssa_thread_s4.cu, ssa_thread_s8.cu, ssa_thread_s16.cu)
+cudaError_t launch_thread_s4(const RunArgs& a, int blocks, int threads, bool shared_d, size_t smem, cudaStream_t st);
+cudaError_t launch_thread_s8(const RunArgs& a, int blocks, int threads, bool shared_d, size_t smem, cudaStream_t st);
+cudaError_t launch_thread_s16(const RunArgs& a, int blocks, int threads, bool shared_d, size_t smem, cudaStream_t st);
+cudaError_t set_smem_s4(int M, bool shared_d, size_t smem);
+cudaError_t set_smem_s8(int M, bool shared_d, size_t smem);
+cudaError_t set_smem_s16(int M, bool shared_d, size_t smem);
 cudaError_t launch_finalize(const unsigned long long* D1, const unsigned long long* D2, int G, int S,
                             int64_t N, const int32_t* x0, double* mean, double* var, int64_t* sum1,
                             int64_t* sum2, cudaStream_t stream);
 cudaError_t launch_uniform_grid(double* grid, int G, double t_end, cudaStream_t stream);
-// Largest M the thread kernel is instantiated for.
+// Largest M and S the thread kernel is instantiated for.
 constexpr int kThreadMaxM = 16;
-cudaError_t thread_kernel_set_smem(int M, bool shared_d, size_t smem_bytes);
+constexpr int kThreadMaxS = 16;
+cudaError_t thread_kernel_set_smem(int M, int S, bool shared_d, size_t smem_bytes);
 
 // Host image of a model's device tables (see DevModel for the layout), for
 // entry points that place the tables themselves.
@@ -113,7 +139,59 @@ struct ModelImageView {
   const unsigned char* image;
   size_t bytes;
   size_t off_c, off_rinfo, off_nu_ptr, off_nu_idx, off_nu_val, off_x0, off_dep_ptr, off_dep_idx;
+  const SmallModel* small;  // filled when M <= 16 and S <= 16
 };
+
+// Launch shape of the thread kernel.
+struct LaunchPlan {
+  int blocks, threads;
+  bool shared_d;
+  size_t smem;
+};
+
+// Chooses the launch shape: threads per CTA from the trajectories per SM
+// (64..512, multiples of 32) unless given.  The difference sums go to global
+// memory by default (fire-and-forget reductions that never stall a warp,
+// measured faster than shared-memory atomics here); SSA_REDUCE_SHARED stages
+// them per CTA in shared memory instead.
+// Returns nullptr or an error message.
+inline const char* plan_thread_launch(int S, int M, int G, int64_t N, int sms, size_t smem_optin, int reduce,
+                                      int block_threads, int grid_blocks, LaunchPlan* p) {
+  int threads = block_threads;
+  if (threads == 0) {
+    const int64_t per_sm = (N + sms - 1) / sms;
+    const int64_t t = (per_sm + 31) / 32 * 32;
+    threads = (int)(t < 64 ? 64 : (t > 512 ? 512 : t));
+  }
+  const int mb = bucket_m(M), sb = bucket_s(S);
+  const ThreadSmem sh = thread_smem_layout(mb, sb, S, G, true);
+  bool shared_d;
+  if (reduce == 1) {  // SSA_REDUCE_SHARED
+    if (sh.total > smem_optin) return "the difference sums do not fit in shared memory";
+    shared_d = true;
+  } else if (reduce == 2) {  // SSA_REDUCE_GLOBAL
+    shared_d = false;
+  } else {
+    shared_d = false;
+  }
+  const ThreadSmem lay = shared_d ? sh : thread_smem_layout(mb, sb, S, G, false);
+  int blocks = grid_blocks;
+  if (blocks == 0) {
+    const int64_t want = (N + threads - 1) / threads;
+    int per_sm = 1;
+    if (!shared_d) {
+      per_sm = (int)(smem_optin / (lay.total > 0 ? lay.total : 1));
+      per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+    }
+    const int64_t cap = (int64_t)sms * per_sm;
+    blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+  }
+  p->blocks = blocks;
+  p->threads = threads;
+  p->shared_d = shared_d;
+  p->smem = lay.total;
+  return nullptr;
+}
 
 }  // namespace ssa_impl
 

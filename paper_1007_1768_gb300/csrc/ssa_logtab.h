@@ -3,13 +3,12 @@
 // Method: Tang's table-driven logarithm (P. T. P. Tang, "Table-driven
 // implementation of the logarithm function in IEEE floating-point arithmetic",
 // ACM TOMS 16(4), 1990), carried out in 64-bit fixed point:
-//   F_i = 1 + (2i + 1) / 256, i = 0..127  (centres of 128 cells of [1, 2))
-//   kLogInv[i] = round(2^64 / F_i)
-//   kLogLnF[i] = round(2^64 ln F_i)
-//   kLogLn2    = round(2^64 ln 2)
-//   kLogHorner[m] = round((-1)^(m+1) 2^62 / m), m = 1..7 (Taylor coefficients
-//   of ln(1 + r) in Q1.62).
-// ln F = 2 atanh(a / b) with a = 2i + 1, b = 513 + 2i (and ln 2 = 2 atanh(1/3))
+//   F_i = 1 + (2i + 1) / 1024, i = 0..511  (centres of 512 cells of [1, 2))
+//   inv[i] = round(2^64 / F_i)
+//   lnf[i] = round(2^64 ln F_i)
+//   ln2    = round(2^64 ln 2)
+//   k3, k5 = round(2^31 / 3), round(2^31 / 5)  (series coefficients in Q1.31)
+// ln F = 2 atanh(a / b) with a = 2i + 1, b = 2049 + 2i (and ln 2 = 2 atanh(1/3))
 // is summed here in Q.100 fixed point with unsigned 128-bit integers: the
 // powers (a/b)^(2k+1) follow p_{k+1} = floor(p_k a^2 / b^2), each term is
 // floor(p_k / (2k + 1)); the accumulated floor error stays below 2^-92, far
@@ -42,28 +41,26 @@ constexpr uint64_t to_q64(u128 v) {
   return (uint64_t)((v + ((u128)1 << (kFracBits - 65))) >> (kFracBits - 64));
 }
 
+constexpr int kCells = 512;
+
 struct Tables {
-  uint64_t inv[128];
-  uint64_t lnf[128];
+  uint64_t inv[kCells];
+  uint64_t lnf[kCells];
   uint64_t ln2;
-  int64_t horner[8];
+  int32_t k3, k5;
 };
 
 constexpr Tables make_tables() {
   Tables t{};
-  for (int i = 0; i < 128; ++i) {
-    const uint64_t den = 257 + 2 * (uint64_t)i;            // 256 F_i
-    const u128 q = ((u128)1 << 73) / den;                  // 2 * 2^72 / den, floored
-    t.inv[i] = (uint64_t)((q + 1) >> 1);                   // round(2^72 / den)
-    t.lnf[i] = to_q64(two_atanh_q100(2 * (uint64_t)i + 1, 513 + 2 * (uint64_t)i));
+  for (int i = 0; i < kCells; ++i) {
+    const uint64_t den = 1025 + 2 * (uint64_t)i;           // 1024 F_i
+    const u128 q = ((u128)1 << 75) / den;                  // 2 * 2^74 / den, floored
+    t.inv[i] = (uint64_t)((q + 1) >> 1);                   // round(2^74 / den)
+    t.lnf[i] = to_q64(two_atanh_q100(2 * (uint64_t)i + 1, 2049 + 2 * (uint64_t)i));
   }
   t.ln2 = to_q64(two_atanh_q100(1, 3));
-  t.horner[0] = 0;
-  for (int m = 1; m <= 7; ++m) {
-    const uint64_t num = (uint64_t)1 << 62;
-    const uint64_t mag = (num + (uint64_t)m / 2) / (uint64_t)m;  // round(2^62 / m)
-    t.horner[m] = (m % 2 == 1) ? (int64_t)mag : -(int64_t)mag;
-  }
+  t.k3 = (int32_t)((((uint64_t)1 << 32) / 3 + 1) >> 1);   // round(2^31 / 3)
+  t.k5 = (int32_t)((((uint64_t)1 << 32) / 5 + 1) >> 1);   // round(2^31 / 5)
   return t;
 }
 

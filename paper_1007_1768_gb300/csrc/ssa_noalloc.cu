@@ -30,7 +30,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/ssa.h"
+#include "ssa.h"
 #include "ssa_internal.h"
 
 namespace ssa_impl {
@@ -95,11 +95,13 @@ extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n
   if (o.memory != SSA_MEM_DEVICE)
     return record_error(SSA_EINVAL, "ssa_ensemble_run_noalloc takes device buffers only (memory = SSA_MEM_DEVICE)");
   if (o.precision != SSA_PREC_FP64) return record_error(SSA_EUNSUPPORTED, "only SSA_PREC_FP64 is built");
-  if (o.schedule == SSA_SCHED_WARP || mv.M > kThreadMaxM)
-    return record_error(SSA_EUNSUPPORTED, "networks with more than 16 reactions are not supported here");
+  if (o.schedule == SSA_SCHED_WARP || !mv.small)
+    return record_error(SSA_EUNSUPPORTED, "networks with more than 16 reactions or species are not supported here");
   if (o.block_threads < 0 || o.block_threads > 512 || (o.block_threads % 32) != 0)
     return record_error(SSA_EINVAL, "block_threads must be 0 or a multiple of 32 up to 512");
   if (o.grid_blocks < 0) return record_error(SSA_EINVAL, "grid_blocks must be >= 0");
+  if (o.max_events > (int64_t)0xFFFFFFFFLL) return record_error(SSA_EINVAL, "max_events must be below 2^32");
+  if (o.stream_id > 0xFFFFFFFFULL) return record_error(SSA_EINVAL, "stream_id must be below 2^32");
 
   // scratch layout inside the fixed array
   const size_t gs = (size_t)n_grid * (size_t)mv.S;
@@ -130,35 +132,17 @@ extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n
   cudaStream_t stream = static_cast<cudaStream_t>(o.cuda_stream);
 
   // launch shape (same rule as ssa_ensemble_run)
-  int threads = o.block_threads;
-  if (threads == 0) {
-    const int64_t per_sm = (n_traj + sms - 1) / sms;
-    threads = (int)std::min<int64_t>(512, std::max<int64_t>(64, (per_sm + 31) / 32 * 32));
-  }
-  ThreadSmem lay_sh = thread_smem_layout(mv.S, mv.M, mv.nnz, n_grid, threads, true);
-  bool shared_d;
-  if (o.reduce == SSA_REDUCE_SHARED) {
-    if (lay_sh.total > smem_optin) return record_error(SSA_EINVAL, "shared reduction does not fit");
-    shared_d = true;
-  } else if (o.reduce == SSA_REDUCE_GLOBAL) {
-    shared_d = false;
-  } else {
-    shared_d = lay_sh.total <= smem_optin;
-  }
-  const ThreadSmem lay = shared_d ? lay_sh : thread_smem_layout(mv.S, mv.M, mv.nnz, n_grid, threads, false);
-  int blocks = o.grid_blocks;
-  if (blocks == 0) {
-    const int64_t want = (n_traj + threads - 1) / threads;
-    const int per_sm = shared_d ? 1 : std::max(1, std::min(8, (int)(smem_optin / std::max<size_t>(lay.total, 1))));
-    blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per_sm));
-  }
+  LaunchPlan plan;
+  if (const char* msg = plan_thread_launch(mv.S, mv.M, n_grid, n_traj, sms, smem_optin, o.reduce, o.block_threads,
+                                           o.grid_blocks, &plan))
+    return record_error(SSA_EINVAL, msg);
 
   auto cuda_fail = [](cudaError_t e, const char* what) {
     char msg[256];
     snprintf(msg, sizeof msg, "%s: %s", what, cudaGetErrorString(e));
     return record_error(SSA_ECUDA, msg);
   };
-  cudaError_t e = thread_kernel_set_smem(mv.M, shared_d, lay.total);
+  cudaError_t e = thread_kernel_set_smem(mv.M, mv.S, plan.shared_d, plan.smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   // counter, totals and difference sums start at zero on every call
   e = cudaMemsetAsync(scratch, 0, off_grid, stream);
@@ -175,6 +159,7 @@ extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n
 
   const unsigned char* b = scratch + off_model;
   RunArgs a;
+  a.sm = *mv.small;
   a.m.S = mv.S;
   a.m.M = mv.M;
   a.m.nnz = mv.nnz;
@@ -203,8 +188,11 @@ extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n
   a.traj_hash = o.traj_hash;
   a.traj_flags = o.traj_flags;
   a.device_totals = reinterpret_cast<unsigned long long*>(o.device_totals);
+  a.grid_uniform = (!grid && n_grid >= 2 && n_grid <= (1 << 20) && t_end < 1e30) ? 1 : 0;
+  a.grid_scale = (float)((double)(n_grid - 1) / t_end);
+  a.grid_margin = (float)((double)n_grid * 0x1p-21);
 
-  e = launch_thread_kernel(a, blocks, threads, shared_d, lay.total, stream);
+  e = launch_thread_kernel(a, plan.blocks, plan.threads, plan.shared_d, plan.smem, stream);
   if (e != cudaSuccess) return cuda_fail(e, "simulation kernel");
   e = launch_finalize(a.D1, a.D2, n_grid, mv.S, n_traj, a.m.x0, mean, var, sum1, sum2, stream);
   if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");

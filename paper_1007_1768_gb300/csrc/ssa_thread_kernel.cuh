@@ -1,0 +1,646 @@
+// The simulation kernel for small networks (at most 16 reactions and 16
+// species).  Included by ssa_thread_s{4,8,16}.cu, each of which instantiates
+// it for one species bucket so the builds run in parallel.
+//
+// Gillespie's direct method (Sec. 2), one trajectory per lane; lanes take
+// trajectory ids from a global work counter.
+//   * The state x, the propensities a_j (double bit patterns) and the
+//     left-to-right prefix sums are registers (MAXS / MAXM are template
+//     bounds).  Per-reaction tables read with a constant index come from the
+//     kernel parameters; those read with the fired reaction's index (net
+//     change rows, dependency masks) from shared memory.
+//   * After an event only the propensities it touched are recomputed (mask
+//     from the dependency graph).
+//   * a0 and the prefix sums are left-to-right FP64 sums; comparisons run on
+//     double bit patterns.
+//   * The loop is software-pipelined by one event: the event drawn in one
+//     iteration is applied to x at once, and kept or undone in the next
+//     iteration, once its time (E / a0 resolves meanwhile) is compared with
+//     t_end.  The kept sequence is exactly the plain loop's.
+//   * Selective memory (Sec. 3.2.1): a kept event at time t adds v and
+//     (2 x_old + v) v to the difference sums D1 / D2 at the first grid index
+//     with g_k >= t, for every species it changes by v; the finalize kernel
+//     scans them along the grid.
+//
+// Three per-warp regimes give the same bits:
+//   * full warp (more than 8 trajectories): the products c_j h_j and the
+//     quotient E / a0 run as exact integer arithmetic (ssa_softfloat.cuh),
+//     since the SM's FP64 unit, shared by all its warps, is the bottleneck;
+//   * sparse warp: the hardware products and quotient (fewer instructions,
+//     latency hidden behind the prefix chain);
+//   * cooperative (at most 4 trajectories left and no new work): the warp
+//     splits into groups of 8 lanes, one trajectory per group.  The lanes of
+//     a group share the propensity products and precompute the random numbers
+//     of the next 8 events at once; the prefix chain, selection and update
+//     run replicated in every lane of the group.  This cuts the instructions
+//     per event of the long trajectories that end the run.
+#ifndef SSA_THREAD_KERNEL_CUH_
+#define SSA_THREAD_KERNEL_CUH_
+
+#include <cstdint>
+
+#include "ssa_device.cuh"
+#include "ssa_internal.h"
+#include "ssa_logtab.h"
+#include "ssa_softfloat.cuh"
+
+namespace ssa_impl {
+namespace {
+
+using ssa_dev::obits;
+
+__device__ const ssa_logtab::Tables d_log_tables = ssa_logtab::kTables;
+
+constexpr unsigned long long kFnvOffset = 0xcbf29ce484222325ULL;
+constexpr unsigned long long kFnvPrime = 0x100000001b3ULL;
+constexpr long long kStateMax = 2147483647LL;
+constexpr unsigned kFullMask = 0xFFFFFFFFu;
+constexpr int kCoopGroup = 8;      // lanes per trajectory in cooperative mode
+constexpr int kCoopMaxTraj = 4;    // trajectories per warp in cooperative mode
+constexpr int kDenseLanes = 8;     // a warp with more trajectories runs the integer forms
+
+// x[s] for a runtime species index s < MAXS (select chain over registers).
+template <int MAXS>
+__device__ __forceinline__ int xget(const int (&x)[MAXS], int s) {
+  int v = x[0];
+#pragma unroll
+  for (int i = 1; i < MAXS; ++i) v = (s == i) ? x[i] : v;
+  return v;
+}
+
+// h_j(x) for a packed reaction word (branch-free: every form is formed and
+// the reaction's kind selects one).
+template <int MAXS>
+__device__ __forceinline__ long long mass_action_h(int32_t w, const int (&x)[MAXS]) {
+  const int kind = rinfo_kind(w);
+  const long long xa = xget<MAXS>(x, rinfo_a(w));
+  const long long xb = xget<MAXS>(x, rinfo_b(w));
+  const long long bi = xa * ((kind == kBi) ? xb : (xa - 1));  // x_a x_b, or x_a (x_a - 1)
+  const long long two = (kind == kBi) ? bi : (bi >> 1);
+  return (kind == kOrder0) ? 1LL : ((kind == kUni) ? xa : two);
+}
+
+// Exact (double)v for 0 <= v < 2^53, integer ops only.
+__device__ __forceinline__ unsigned long long small_int_to_f64_bits(unsigned long long v) {
+  const int lz = __clzll((long long)(v | 1ULL));
+  const unsigned long long r = ((unsigned long long)(1086 - lz) << 52) + ((v << lz) >> 11) - (1ULL << 52);
+  return (v == 0ULL) ? 0ULL : r;
+}
+
+// a_j = RN(c_j * h) as bits, exact integer product.  Returns false when the
+// product needs the hardware path (h >= 2^53, subnormal or overflowing cases).
+__device__ __forceinline__ bool propensity_int(unsigned long long cbits, long long h, unsigned long long& out) {
+  bool ok;
+  const unsigned long long r = ssa_sf::mul_u53(cbits, (unsigned long long)h & ((1ULL << 53) - 1), ok);
+  out = r;
+  return ok && (unsigned long long)h < (1ULL << 53);
+}
+
+// a_j = RN(c_j * h) as bits with the hardware multiply.
+__device__ __forceinline__ unsigned long long propensity_fp64(unsigned long long cbits, long long h) {
+  const double hd = ((unsigned long long)h < (1ULL << 53))
+                        ? __longlong_as_double((long long)small_int_to_f64_bits((unsigned long long)h))
+                        : __ll2double_rn(h);
+  return (unsigned long long)obits(__dmul_rn(__longlong_as_double((long long)cbits), hd));
+}
+
+// A float at or below the non-negative double with bits `b`, within 2^-23
+// relative (integer ops only; 0 below float's normal range).  Only used for
+// the grid index estimate, which is checked against the grid when close to
+// a cell boundary.
+__device__ __forceinline__ float approx_float_rz(long long b) {
+  const int e = (int)(b >> 52) - 1023 + 127;
+  const int f = (e << 23) | (int)((b >> 29) & 0x7FFFFF);
+  return __int_as_float(e <= 0 ? 0 : (e >= 255 ? 0x7F800000 : f));
+}
+
+// First index k' >= k with g_{k'} >= t (t given by its bits tb <= t_end), or G.
+__device__ __forceinline__ int grid_index(const RunArgs& a, long long tb, int k) {
+  const int G = a.G;
+  if (a.grid_uniform) {
+    // x = t (G - 1) / t_end; the estimate is within (G - 1) 2^-22 of x and
+    // the grid points within G 2^-50 (in index units) of k t_end / (G - 1):
+    // away from integers by more than grid_margin, ceil(estimate) is exact.
+    const float est = approx_float_rz(tb) * a.grid_scale;
+    const float fl = floorf(est);
+    const float fr = est - fl;
+    int ke = min(max((int)fl + 1, k), G);
+    if (fr > a.grid_margin && fr < 1.0f - a.grid_margin) return ke;
+    if (ke > k && obits(__ldg(a.grid + ke - 1)) >= tb) --ke;
+    if (ke > k && obits(__ldg(a.grid + ke - 1)) >= tb) --ke;
+    if (ke < G && obits(__ldg(a.grid + ke)) < tb) ++ke;
+    return ke;
+  }
+  while (k < G && obits(__ldg(a.grid + k)) < tb) ++k;
+  return k;
+}
+
+// Random numbers of event n of a trajectory: E = -ln(r1) and r2 = q2 2^-53,
+// both as double bit patterns.
+struct EventRandom {
+  unsigned long long E;
+  unsigned long long u2;
+};
+
+__device__ __forceinline__ EventRandom event_random(uint32_t n, unsigned long long traj_id, uint32_t stream,
+                                                    uint32_t k0, uint32_t k1, const uint64_t* s_inv,
+                                                    const uint64_t* s_lnf) {
+  const ssa_dev::Words4 w =
+      ssa_dev::philox4x32_10(n, (uint32_t)traj_id, (uint32_t)(traj_id >> 32), stream, k0, k1);
+  EventRandom r;
+  r.E = ssa_dev::neg_log_u_bits(ssa_dev::odd53(w.w0, w.w1), s_inv, s_lnf);
+  r.u2 = small_int_to_f64_bits(ssa_dev::odd53(w.w2, w.w3)) - (53ULL << 52);
+  return r;
+}
+
+// Everything one trajectory carries between iterations.
+template <int MAXM, int MAXS>
+struct Traj {
+  int x[MAXS];
+  int pv[MAXS];                 // state change of the pending event
+  unsigned long long av[MAXM];  // propensities (bits)
+  double pre[MAXM];             // prefix sums
+  uint32_t dirty;               // propensities to recompute
+  bool have;
+  long long li;                 // index in this launch
+  unsigned long long traj_id;   // global id (Philox counter)
+  double t;
+  uint32_t n;                   // events kept so far
+  int k;                        // grid index of the last kept event
+  unsigned long long hash;
+  int maxx;
+  int flags;
+  EventRandom rnd;              // random numbers of the event to draw next (thread mode)
+  bool pend;                    // an event was drawn and applied, not yet settled
+  bool pend_over;               // it would leave the int32 range: not applied
+  int pend_j;
+  double pend_t;
+};
+
+// Per-launch constants of the step.
+struct StepEnv {
+  int M, S, G;
+  long long t_end_bits;
+  uint32_t key0, key1, sid;
+  const uint64_t* s_inv;
+  const uint64_t* s_lnf;
+  const int32_t* s_nu;
+  const uint32_t* s_depmask;
+  unsigned long long* d1;
+  unsigned long long* d2;
+};
+
+template <int MAXM, int MAXS>
+__device__ __forceinline__ void start_trajectory(const RunArgs& a, const StepEnv& e, Traj<MAXM, MAXS>& q,
+                                                 unsigned long long next) {
+  q.have = true;
+  q.li = (long long)next;
+  q.traj_id = a.traj_offset + next;
+  q.maxx = 0;
+#pragma unroll
+  for (int s = 0; s < MAXS; ++s) {
+    q.x[s] = (s < e.S) ? a.sm.x0[s] : 0;
+    q.maxx = max(q.maxx, q.x[s]);
+  }
+  q.t = 0.0;
+  q.n = 0;
+  q.k = 0;
+  q.hash = kFnvOffset;
+  q.flags = 0;
+  q.dirty = (1u << MAXM) - 1u;
+  q.pend = false;
+  q.pend_over = false;
+  q.pend_j = 0;
+  q.pend_t = 0.0;
+}
+
+// Prefix sums and a0 from the propensities, left to right.
+template <int MAXM, int MAXS>
+__device__ __forceinline__ double prefix_sums(int M, Traj<MAXM, MAXS>& q) {
+  q.pre[0] = __longlong_as_double((long long)q.av[0]);
+#pragma unroll
+  for (int j = 1; j < MAXM; ++j) {
+    if (j < M) q.pre[j] = __dadd_rn(q.pre[j - 1], __longlong_as_double((long long)q.av[j]));
+    else q.pre[j] = q.pre[j - 1];
+  }
+  return q.pre[MAXM - 1];
+}
+
+// Settle the pending event: keep it (grid index, difference sums when
+// `emit`, time, count, hash) or, past t_end, undo it.  Returns true when the
+// trajectory ends (flags set).
+template <int MAXM, int MAXS>
+__device__ __forceinline__ bool settle(const RunArgs& a, const StepEnv& e, Traj<MAXM, MAXS>& q, bool emit) {
+  const long long tb = obits(q.pend_t);
+  const bool beyond = q.pend && tb > e.t_end_bits;  // not fired: undo
+  const bool keep = q.pend && !beyond && !q.pend_over;
+  const bool undo = beyond && !q.pend_over;
+#pragma unroll
+  for (int s = 0; s < MAXS; ++s) q.x[s] -= undo ? q.pv[s] : 0;
+  if (keep) q.k = grid_index(a, tb, q.k);
+  const bool in_grid = emit && keep && q.k < e.G;
+#pragma unroll
+  for (int s = 0; s < MAXS; ++s) {
+    const bool ch = keep && q.pv[s] != 0;
+    q.maxx = ch ? max(q.maxx, q.x[s]) : q.maxx;
+    if (in_grid && q.pv[s] != 0) {
+      const long long xo = (long long)q.x[s] - q.pv[s];
+      atomicAdd(e.d1 + (size_t)q.k * e.S + s, (unsigned long long)(long long)q.pv[s]);
+      atomicAdd(e.d2 + (size_t)q.k * e.S + s, (unsigned long long)((2 * xo + q.pv[s]) * (long long)q.pv[s]));
+    }
+  }
+  q.t = keep ? q.pend_t : q.t;
+  q.n += keep ? 1u : 0u;
+  const unsigned long long h1 = (q.hash ^ (unsigned long long)q.pend_j) * kFnvPrime;
+  const unsigned long long h2 = (h1 ^ (unsigned long long)tb) * kFnvPrime;
+  q.hash = keep ? h2 : q.hash;
+  const bool trunc = keep && (long long)q.n == a.max_events;
+  const bool over_end = q.pend && !beyond && q.pend_over;
+  q.flags = (trunc ? 1 : 0) | (over_end ? 2 : 0);
+  q.pend = false;
+  return beyond || over_end || trunc;
+}
+
+// Draw the next event with random numbers r: time t + E / a0, target r2 a0,
+// selection, and the state update applied at once (it settles next round).
+template <bool DENSE, int MAXM, int MAXS>
+__device__ __forceinline__ void draw(const StepEnv& e, Traj<MAXM, MAXS>& q, double a0, const EventRandom& r,
+                                     bool done) {
+  double tau;
+  if (DENSE) {
+    bool okd;
+    const unsigned long long tau_b = ssa_sf::div_pos(r.E, (unsigned long long)obits(a0), okd);
+    tau = okd ? __longlong_as_double((long long)tau_b) : __ddiv_rn(__longlong_as_double((long long)r.E), a0);
+  } else {
+    tau = __ddiv_rn(__longlong_as_double((long long)r.E), a0);  // a0 == 0 gives +inf: absorbing
+  }
+  const double t_next = __dadd_rn(q.t, tau);
+  const long long gb = obits(__dmul_rn(__longlong_as_double((long long)r.u2), a0));
+  // first j with prefix_j > target (prefixes are non-decreasing)
+  int cnt = 0;
+#pragma unroll
+  for (int j = 0; j < MAXM; ++j) {
+    if (j < e.M) cnt += (obits(q.pre[j]) <= gb) ? 1 : 0;
+  }
+  int jsel = cnt;
+  if (cnt >= e.M) {  // rounding left no j (or a0 == 0): the last reaction with a_j > 0
+    jsel = 0;
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) {
+      if (j < e.M && q.av[j] != 0ULL) jsel = j;
+    }
+  }
+  const int* row = e.s_nu + jsel * MAXS;
+  bool over = false;
+#pragma unroll
+  for (int s = 0; s < MAXS; ++s) {
+    q.pv[s] = row[s];
+    over |= (long long)q.x[s] + (long long)q.pv[s] > kStateMax;
+  }
+  const bool apply = !done && !over;
+#pragma unroll
+  for (int s = 0; s < MAXS; ++s) q.x[s] += apply ? q.pv[s] : 0;
+  q.pend = !done;
+  q.pend_over = over;
+  q.pend_j = jsel;
+  q.pend_t = t_next;
+  q.dirty = apply ? e.s_depmask[jsel] : 0u;
+}
+
+// One thread-mode iteration.  Returns true when the trajectory has ended.
+template <bool DENSE, int MAXM, int MAXS>
+__device__ __forceinline__ bool thread_step(const RunArgs& a, const StepEnv& e, Traj<MAXM, MAXS>& q) {
+  // propensities the last event touched
+  if (DENSE) {
+    bool all_ok = true;
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) {
+      if (j < e.M) {
+        unsigned long long r;
+        const bool ok = propensity_int(a.sm.cbits[j], mass_action_h<MAXS>(a.sm.rinfo[j], q.x), r);
+        const bool d = (q.dirty >> j) & 1u;
+        all_ok &= ok | !d;
+        q.av[j] = (d && ok) ? r : q.av[j];
+      }
+    }
+    if (!all_ok) {  // rare: redo the failed ones on the FP64 unit
+#pragma unroll
+      for (int j = 0; j < MAXM; ++j) {
+        if (j < e.M && ((q.dirty >> j) & 1u))
+          q.av[j] = propensity_fp64(a.sm.cbits[j], mass_action_h<MAXS>(a.sm.rinfo[j], q.x));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) {
+      if (j < e.M && ((q.dirty >> j) & 1u))
+        q.av[j] = propensity_fp64(a.sm.cbits[j], mass_action_h<MAXS>(a.sm.rinfo[j], q.x));
+    }
+  }
+  const double a0 = prefix_sums(e.M, q);
+  const bool done = settle(a, e, q, true);
+  const EventRandom r = q.rnd;
+  q.rnd = event_random(q.n + 1u, q.traj_id, e.sid, e.key0, e.key1, e.s_inv, e.s_lnf);
+  draw<DENSE>(e, q, a0, r, done);
+  return done;
+}
+
+template <int MAXM, int MAXS>
+__device__ __forceinline__ void finish_trajectory(const RunArgs& a, const Traj<MAXM, MAXS>& q,
+                                                  unsigned long long* blk) {
+  if (a.traj_events) a.traj_events[q.li] = (long long)q.n;
+  if (a.traj_hash) a.traj_hash[q.li] = q.hash;
+  if (a.traj_flags) a.traj_flags[q.li] = q.flags;
+  atomicAdd(&blk[0], (unsigned long long)q.n);
+  if (q.flags & 1) atomicAdd(&blk[1], 1ULL);
+  if (q.flags & 2) atomicAdd(&blk[2], 1ULL);
+  atomicMax(&blk[3], (unsigned long long)q.maxx);
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_all(T v, int src, int width = 32) {
+  return __shfl_sync(kFullMask, v, src, width);
+}
+
+// Cooperative mode for the (at most 4) trajectories left in a warp when no
+// new work remains.  All 32 lanes enter together.  Group g (lanes 8g..8g+7)
+// takes the g-th remaining trajectory: its state is copied to every lane of
+// the group, which then runs it event by event with the work split as
+// described at the top of this file.
+template <int MAXM, int MAXS>
+__device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Traj<MAXM, MAXS>& q, unsigned act,
+                                         unsigned long long* blk) {
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / kCoopGroup;
+  const int gl = lane % kCoopGroup;
+  // owner lane of this group's trajectory: the grp-th set bit of act
+  unsigned m = act;
+  int owner = -1;
+#pragma unroll
+  for (int r = 0; r < kCoopMaxTraj; ++r) {
+    const int b = __ffs(m) - 1;
+    if (r == grp) owner = b;
+    if (b >= 0) m &= m - 1;
+  }
+  const bool gactive = owner >= 0;
+  const int src = gactive ? owner : lane;
+  // replicate the owner's state in the group
+#pragma unroll
+  for (int s = 0; s < MAXS; ++s) {
+    q.x[s] = shfl_all(q.x[s], src);
+    q.pv[s] = shfl_all(q.pv[s], src);
+  }
+  q.li = shfl_all(q.li, src);
+  q.traj_id = shfl_all(q.traj_id, src);
+  q.t = shfl_all(q.t, src);
+  q.n = shfl_all(q.n, src);
+  q.k = shfl_all(q.k, src);
+  q.hash = shfl_all(q.hash, src);
+  q.maxx = shfl_all(q.maxx, src);
+  // a group without a trajectory carries no pending event (its lanes may
+  // hold the stale state of a trajectory now run by another group)
+  q.pend = (shfl_all((int)q.pend, src) != 0) && gactive;
+  q.pend_over = shfl_all((int)q.pend_over, src) != 0;
+  q.pend_j = shfl_all(q.pend_j, src);
+  q.pend_t = shfl_all(q.pend_t, src);
+  q.have = gactive;
+  q.dirty = (1u << MAXM) - 1u;  // recompute every propensity from the copied state
+  // this lane's propensity slots: j = gl + 8 i
+  constexpr int kSlots = (MAXM + kCoopGroup - 1) / kCoopGroup;
+  unsigned long long mine[kSlots];
+  int32_t mine_w[kSlots];
+  unsigned long long mine_c[kSlots];
+#pragma unroll
+  for (int i = 0; i < kSlots; ++i) {
+    mine[i] = 0ULL;
+    // the reaction index depends on the lane: pick its tables with selects
+    // over the constant indices (no dynamic indexing of the parameters)
+    mine_w[i] = 0;
+    mine_c[i] = 0ULL;
+#pragma unroll
+    for (int jj = 0; jj < MAXM; ++jj) {
+      if (jj / kCoopGroup == i) {
+        mine_w[i] = (jj % kCoopGroup == gl) ? a.sm.rinfo[jj] : mine_w[i];
+        mine_c[i] = (jj % kCoopGroup == gl) ? a.sm.cbits[jj] : mine_c[i];
+      }
+    }
+  }
+  // random numbers of events base .. base + 7, one per lane of the group
+  uint32_t base = 0;
+  EventRandom cache = {0ULL, 0ULL};
+  bool filled = false;
+
+  while (__any_sync(kFullMask, q.have)) {
+    // refresh every group's cache at once when any group may draw past its
+    // 8 (the groups advance in step, so they run out together); the next
+    // draw index is n or n + 1
+    const bool want = q.have && (!filled || q.n + 1u >= base + (uint32_t)kCoopGroup);
+    if (__any_sync(kFullMask, want)) {
+      base = q.n;
+      cache = event_random(base + (uint32_t)gl, q.traj_id, e.sid, e.key0, e.key1, e.s_inv, e.s_lnf);
+      filled = true;
+    }
+    // propensities: lane gl computes j = gl + 8 i when dirty
+#pragma unroll
+    for (int i = 0; i < kSlots; ++i) {
+      const int j = gl + kCoopGroup * i;
+      if (j < e.M && ((q.dirty >> j) & 1u)) mine[i] = propensity_fp64(mine_c[i], mass_action_h<MAXS>(mine_w[i], q.x));
+    }
+    // every propensity into every lane of the group
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) {
+      if (j < e.M) q.av[j] = shfl_all(mine[j / kCoopGroup], j % kCoopGroup, kCoopGroup);
+    }
+    const double a0 = prefix_sums(e.M, q);
+    const bool done = settle(a, e, q, gl == 0) && q.have;
+    // this event's random numbers, from the lane that holds them
+    const int slot = (int)(q.n - base) & (kCoopGroup - 1);
+    EventRandom r;
+    r.E = shfl_all(cache.E, slot, kCoopGroup);
+    r.u2 = shfl_all(cache.u2, slot, kCoopGroup);
+    draw<false>(e, q, a0, r, done || !q.have);
+    if (done) {
+      if (gl == 0) finish_trajectory(a, q, blk);
+      q.have = false;
+      q.pend = false;
+    }
+  }
+}
+
+template <int MAXM, int MAXS, bool SHARED_D>
+__global__ void __launch_bounds__(512) k_ssa_thread(const RunArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long blk[4];  // events, truncated, overflowed, max x
+  const int S = a.m.S, M = a.m.M, G = a.G, T = blockDim.x, tid = threadIdx.x;
+  const ThreadSmem L = thread_smem_layout(MAXM, MAXS, S, G, SHARED_D);
+  uint64_t* s_inv = reinterpret_cast<uint64_t*>(smem + L.log_inv);
+  uint64_t* s_lnf = reinterpret_cast<uint64_t*>(smem + L.log_lnf);
+  int32_t* s_nu = reinterpret_cast<int32_t*>(smem + L.nu);
+  uint32_t* s_depmask = reinterpret_cast<uint32_t*>(smem + L.depmask);
+  unsigned long long* d1 = SHARED_D ? reinterpret_cast<unsigned long long*>(smem + L.d1) : a.D1;
+  unsigned long long* d2 = SHARED_D ? reinterpret_cast<unsigned long long*>(smem + L.d2) : a.D2;
+
+  for (int i = tid; i < kLogCells; i += T) {
+    s_inv[i] = d_log_tables.inv[i];
+    s_lnf[i] = d_log_tables.lnf[i];
+  }
+  for (int i = tid; i < MAXM * MAXS; i += T) {
+    const int j = i / MAXS, s = i % MAXS;
+    s_nu[i] = (j < M && s < S) ? a.sm.nu[j * kSmallMax + s] : 0;
+  }
+  for (int j = tid; j < MAXM; j += T) s_depmask[j] = (j < M) ? a.sm.depmask[j] : 0u;
+  if (SHARED_D) {
+    for (int i = tid; i < G * S; i += T) {
+      d1[i] = 0ULL;
+      d2[i] = 0ULL;
+    }
+  }
+  if (tid < 4) blk[tid] = 0ULL;
+  __syncthreads();
+
+  StepEnv e;
+  e.M = M;
+  e.S = S;
+  e.G = G;
+  e.t_end_bits = obits(a.t_end);
+  e.key0 = (uint32_t)a.seed;
+  e.key1 = (uint32_t)(a.seed >> 32);
+  e.sid = (uint32_t)a.stream_id;
+  e.s_inv = s_inv;
+  e.s_lnf = s_lnf;
+  e.s_nu = s_nu;
+  e.s_depmask = s_depmask;
+  e.d1 = d1;
+  e.d2 = d2;
+
+  Traj<MAXM, MAXS> q;
+#pragma unroll
+  for (int s = 0; s < MAXS; ++s) {
+    q.x[s] = 0;
+    q.pv[s] = 0;
+  }
+#pragma unroll
+  for (int j = 0; j < MAXM; ++j) {
+    q.av[j] = 0ULL;
+    q.pre[j] = 0.0;
+  }
+  q.have = false;
+  q.pend = false;
+  q.pend_over = false;
+  q.dirty = 0;
+  q.li = 0;
+  q.traj_id = 0;
+  q.t = 0.0;
+  q.n = 0;
+  q.k = 0;
+  q.hash = kFnvOffset;
+  q.maxx = 0;
+  q.flags = 0;
+  q.pend_j = 0;
+  q.pend_t = 0.0;
+  q.rnd = EventRandom{0ULL, 0ULL};
+  bool exhausted = false;  // this lane saw the work counter run out
+
+  // Every lane of the warp stays in this loop until the warp has no work, so
+  // warp-wide votes see all 32 lanes.
+  for (;;) {
+    if (!q.have && !exhausted) {
+      const unsigned long long next = atomicAdd(a.counter, 1ULL);
+      if (next < (unsigned long long)a.N) {
+        start_trajectory(a, e, q, next);
+        q.rnd = event_random(0u, q.traj_id, e.sid, e.key0, e.key1, e.s_inv, e.s_lnf);
+      } else {
+        exhausted = true;
+      }
+    }
+    const unsigned act = __ballot_sync(kFullMask, q.have);
+    if (act == 0u) break;
+    const int nact = __popc(act);
+    if (nact <= kCoopMaxTraj && __any_sync(kFullMask, exhausted)) {
+      coop_run(a, e, q, act, blk);
+      break;
+    }
+    if (q.have) {
+      const bool done = (nact > kDenseLanes) ? thread_step<true>(a, e, q) : thread_step<false>(a, e, q);
+      if (done) {
+        finish_trajectory(a, q, blk);
+        q.have = false;
+      }
+    }
+  }
+
+  __syncthreads();
+  if (SHARED_D) {
+    for (int i = tid; i < G * S; i += T) {
+      const unsigned long long v1 = d1[i], v2 = d2[i];
+      if (v1) atomicAdd(a.D1 + i, v1);
+      if (v2) atomicAdd(a.D2 + i, v2);
+    }
+  }
+  if (tid == 0) {
+    atomicAdd(a.stats + kStatEvents, blk[0]);
+    atomicAdd(a.stats + kStatTruncated, blk[1]);
+    atomicAdd(a.stats + kStatOverflowed, blk[2]);
+    atomicMax(a.stats + kStatMaxX, blk[3]);
+    if (a.device_totals) {
+      atomicAdd(a.device_totals + 0, blk[0]);
+      atomicAdd(a.device_totals + 1, blk[1]);
+      atomicAdd(a.device_totals + 2, blk[2]);
+      atomicMax(a.device_totals + 3, blk[3]);
+    }
+  }
+}
+
+template <int MAXM, int MAXS>
+cudaError_t launch_bucket(const RunArgs& a, int blocks, int threads, bool shared_d, size_t smem, cudaStream_t st) {
+  if (shared_d)
+    k_ssa_thread<MAXM, MAXS, true><<<blocks, threads, smem, st>>>(a);
+  else
+    k_ssa_thread<MAXM, MAXS, false><<<blocks, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MAXM, int MAXS>
+cudaError_t set_smem_bucket(bool shared_d, size_t smem) {
+  if (shared_d)
+    return cudaFuncSetAttribute(k_ssa_thread<MAXM, MAXS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  return cudaFuncSetAttribute(k_ssa_thread<MAXM, MAXS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+
+// Dispatch on the M bucket for one S bucket.
+template <int MAXS>
+cudaError_t launch_for_s(const RunArgs& a, int blocks, int threads, bool shared_d, size_t smem, cudaStream_t st) {
+  switch (bucket_m(a.m.M)) {
+    case 2: return launch_bucket<2, MAXS>(a, blocks, threads, shared_d, smem, st);
+    case 4: return launch_bucket<4, MAXS>(a, blocks, threads, shared_d, smem, st);
+    case 6: return launch_bucket<6, MAXS>(a, blocks, threads, shared_d, smem, st);
+    case 8: return launch_bucket<8, MAXS>(a, blocks, threads, shared_d, smem, st);
+    case 10: return launch_bucket<10, MAXS>(a, blocks, threads, shared_d, smem, st);
+    case 12: return launch_bucket<12, MAXS>(a, blocks, threads, shared_d, smem, st);
+    case 14: return launch_bucket<14, MAXS>(a, blocks, threads, shared_d, smem, st);
+    case 16: return launch_bucket<16, MAXS>(a, blocks, threads, shared_d, smem, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int MAXS>
+cudaError_t set_smem_for_s(int M, bool shared_d, size_t smem) {
+  switch (bucket_m(M)) {
+    case 2: return set_smem_bucket<2, MAXS>(shared_d, smem);
+    case 4: return set_smem_bucket<4, MAXS>(shared_d, smem);
+    case 6: return set_smem_bucket<6, MAXS>(shared_d, smem);
+    case 8: return set_smem_bucket<8, MAXS>(shared_d, smem);
+    case 10: return set_smem_bucket<10, MAXS>(shared_d, smem);
+    case 12: return set_smem_bucket<12, MAXS>(shared_d, smem);
+    case 14: return set_smem_bucket<14, MAXS>(shared_d, smem);
+    case 16: return set_smem_bucket<16, MAXS>(shared_d, smem);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+}  // namespace ssa_impl
+
+#endif  // SSA_THREAD_KERNEL_CUH_

@@ -1,0 +1,12 @@
+// Thread-per-trajectory kernels for networks with at most 16 species.
+#include "ssa_thread_kernel.cuh"
+
+namespace ssa_impl {
+
+cudaError_t launch_thread_s16(const RunArgs& a, int blocks, int threads, bool shared_d, size_t smem, cudaStream_t st) {
+  return launch_for_s<16>(a, blocks, threads, shared_d, smem, st);
+}
+
+cudaError_t set_smem_s16(int M, bool shared_d, size_t smem) { return set_smem_for_s<16>(M, shared_d, smem); }
+
+}  // namespace ssa_impl
