@@ -36,6 +36,10 @@ if ROOT not in sys.path:
 METRIC = "SSA reaction events/s incl. grid align+mean/var reduce, 1 GB300, vs plain FP64"
 UNIT = "events/s"
 SMS_GB300 = 152
+# DRAM read + write bytes of one k_ssa_thread launch (ncu capture summarised in
+# profiles/k_ssa_thread_hiv_shaped.md: tables, grid and parameters; the
+# difference sums stay in L2), independent of the number of trajectories.
+SIM_KERNEL_DRAM_BYTES = 841728
 FP64_OPS_PER_SM_CLK = 2.0  # 1.25 TFLOP/s dense FP64 (FMA = 2 flops) / (152 SMs * 2.07 GHz)
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -55,6 +59,11 @@ def parse_args():
     p.add_argument("--profile-small", action="store_true",
                    help="one small step for an ncu capture (--profile-n trajectories); prints no bench line")
     p.add_argument("--profile-n", type=int, default=16384)
+    p.add_argument("--scan", action="store_true",
+                   help="time one ensemble per trajectory count (32 .. 1,048,576) and print, per count, the "
+                        "cycles per event of its longest trajectory (the serial floor of the step)")
+    p.add_argument("--probe", choices=["pipes", "latency", "step"],
+                   help="build and run one of the pipe / latency / step-part probes in csrc/probes")
     return p.parse_args()
 
 
@@ -293,7 +302,7 @@ def run_ours(args):
             "events_per_step": events_all / K,
             "wall_s_timed_region": wall,
             "roofline": {"bound": "alu", "kernel": "k_ssa_thread", "achieved": achieved, "peak": peak,
-                         "unit": "GFLOP/s (FP64 ops)", "frac": achieved / peak, "traffic": None,
+                         "unit": "GFLOP/s (FP64 ops)", "frac": achieved / peak, "traffic": SIM_KERNEL_DRAM_BYTES,
                          "kernel_ms": kern_avg, "ops_per_event": fp64_ops_per_event(M),
                          "peak_basis": "2 FP64 ops/clk/SM x 152 SMs x median SM clock (nominal 1.25 TFLOP/s dense)"},
             "cpu_baseline": cpu,
@@ -308,8 +317,45 @@ def run_ours(args):
     return 0
 
 
+def run_scan():
+    """Kernel time per trajectory count for the HIV-shaped model; for counts
+    up to 65,536 also the longest trajectory's events, whose serial chain sets
+    the floor of the kernel time."""
+    import paper_1007_1768_gb300 as ssa
+    import workloads as W
+    net = W.hiv_shaped()
+    model = ssa.Model.from_network(net)
+    for n in [32, 128, 1024, 16384, 65536, 262144, 1048576]:
+        best = None
+        for rep in range(3):
+            r = ssa.ensemble_run(model, n, 30.0, 3001, 1000 + rep, per_traj=n <= 65536, want_sums=False)
+            if best is None or r.kernel_ms < best.kernel_ms:
+                best = r
+        mx = int(best.traj_events.max()) if best.traj_events is not None else None
+        line = {"n_traj": n, "kernel_ms": round(best.kernel_ms, 3), "events": best.events,
+                "events_per_s": best.events / best.kernel_ms * 1e3, "max_traj_events": mx,
+                "cycles_per_event_of_longest_at_2070MHz": round(best.kernel_ms * 2.07e6 / mx, 1) if mx else None}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_probe(name: str):
+    """Builds csrc/probes/probe_<name>.cu with nvcc for sm_103a and runs it."""
+    from paper_1007_1768_gb300 import build as libbuild
+    src = os.path.join(ROOT, "paper_1007_1768_gb300", "csrc", "probes", f"probe_{name}.cu")
+    exe = os.path.join(libbuild.BUILD, f"probe_{name}")
+    os.makedirs(libbuild.BUILD, exist_ok=True)
+    subprocess.run([libbuild.nvcc(), "-O3", "-std=c++17", "-fmad=false", "-I", libbuild.INCLUDE, *libbuild.ARCH,
+                    "-o", exe, src], check=True)
+    return subprocess.run([exe]).returncode
+
+
 def main():
     args = parse_args()
+    if args.scan:
+        return run_scan()
+    if args.probe:
+        return run_probe(args.probe)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -174,7 +174,8 @@ struct Traj {
   bool pend;                    // an event was drawn and applied, not yet settled
   bool pend_over;               // it would leave the int32 range: not applied
   int pend_j;
-  double pend_t;
+  unsigned long long pend_E;    // its -ln(r1) (bits); its time is t + pend_E / pend_a0
+  double pend_a0;
 };
 
 // Per-launch constants of the step.
@@ -211,7 +212,18 @@ __device__ __forceinline__ void start_trajectory(const RunArgs& a, const StepEnv
   q.pend = false;
   q.pend_over = false;
   q.pend_j = 0;
-  q.pend_t = 0.0;
+  q.pend_E = 0ULL;
+  q.pend_a0 = 0.0;
+}
+
+// tau = RN(E / a0) as a double: the exact integer quotient (branch-free, so
+// its instructions fill the stalls of the prefix chain it is issued with);
+// the hardware division for the rare operands it does not cover (a0 == 0
+// gives +inf: the state is absorbing).
+__device__ __forceinline__ double quotient(unsigned long long Eb, double a0) {
+  bool ok;
+  const unsigned long long qb = ssa_sf::div_pos(Eb, (unsigned long long)obits(a0), ok);
+  return ok ? __longlong_as_double((long long)qb) : __ddiv_rn(__longlong_as_double((long long)Eb), a0);
 }
 
 // Prefix sums and a0 from the propensities, left to right.
@@ -226,12 +238,14 @@ __device__ __forceinline__ double prefix_sums(int M, Traj<MAXM, MAXS>& q) {
   return q.pre[MAXM - 1];
 }
 
-// Settle the pending event: keep it (grid index, difference sums when
-// `emit`, time, count, hash) or, past t_end, undo it.  Returns true when the
-// trajectory ends (flags set).
+// Settle the pending event, whose waiting time is tau: keep it (grid index,
+// difference sums when `emit`, time, count, hash) or, past t_end, undo it.
+// Returns true when the trajectory ends (flags set).
 template <int MAXM, int MAXS>
-__device__ __forceinline__ bool settle(const RunArgs& a, const StepEnv& e, Traj<MAXM, MAXS>& q, bool emit) {
-  const long long tb = obits(q.pend_t);
+__device__ __forceinline__ bool settle(const RunArgs& a, const StepEnv& e, Traj<MAXM, MAXS>& q, double tau,
+                                       bool emit) {
+  const double t_next = __dadd_rn(q.t, tau);
+  const long long tb = obits(t_next);
   const bool beyond = q.pend && tb > e.t_end_bits;  // not fired: undo
   const bool keep = q.pend && !beyond && !q.pend_over;
   const bool undo = beyond && !q.pend_over;
@@ -249,7 +263,7 @@ __device__ __forceinline__ bool settle(const RunArgs& a, const StepEnv& e, Traj<
       atomicAdd(e.d2 + (size_t)q.k * e.S + s, (unsigned long long)((2 * xo + q.pv[s]) * (long long)q.pv[s]));
     }
   }
-  q.t = keep ? q.pend_t : q.t;
+  q.t = keep ? t_next : q.t;
   q.n += keep ? 1u : 0u;
   const unsigned long long h1 = (q.hash ^ (unsigned long long)q.pend_j) * kFnvPrime;
   const unsigned long long h2 = (h1 ^ (unsigned long long)tb) * kFnvPrime;
@@ -261,20 +275,12 @@ __device__ __forceinline__ bool settle(const RunArgs& a, const StepEnv& e, Traj<
   return beyond || over_end || trunc;
 }
 
-// Draw the next event with random numbers r: time t + E / a0, target r2 a0,
-// selection, and the state update applied at once (it settles next round).
-template <bool DENSE, int MAXM, int MAXS>
+// Draw the next event with random numbers r: target r2 a0, selection, and
+// the state update applied at once.  Its time t + E / a0 is formed and
+// checked against t_end in the next iteration.
+template <int MAXM, int MAXS>
 __device__ __forceinline__ void draw(const StepEnv& e, Traj<MAXM, MAXS>& q, double a0, const EventRandom& r,
                                      bool done) {
-  double tau;
-  if (DENSE) {
-    bool okd;
-    const unsigned long long tau_b = ssa_sf::div_pos(r.E, (unsigned long long)obits(a0), okd);
-    tau = okd ? __longlong_as_double((long long)tau_b) : __ddiv_rn(__longlong_as_double((long long)r.E), a0);
-  } else {
-    tau = __ddiv_rn(__longlong_as_double((long long)r.E), a0);  // a0 == 0 gives +inf: absorbing
-  }
-  const double t_next = __dadd_rn(q.t, tau);
   const long long gb = obits(__dmul_rn(__longlong_as_double((long long)r.u2), a0));
   // first j with prefix_j > target (prefixes are non-decreasing)
   int cnt = 0;
@@ -303,7 +309,8 @@ __device__ __forceinline__ void draw(const StepEnv& e, Traj<MAXM, MAXS>& q, doub
   q.pend = !done;
   q.pend_over = over;
   q.pend_j = jsel;
-  q.pend_t = t_next;
+  q.pend_E = r.E;
+  q.pend_a0 = a0;
   q.dirty = apply ? e.s_depmask[jsel] : 0u;
 }
 
@@ -337,11 +344,18 @@ __device__ __forceinline__ bool thread_step(const RunArgs& a, const StepEnv& e, 
         q.av[j] = propensity_fp64(a.sm.cbits[j], mass_action_h<MAXS>(a.sm.rinfo[j], q.x));
     }
   }
+  // one straight-line block of independent chains: the pending event's
+  // quotient, the prefix sums of the new state, and the random numbers of
+  // the event after the one drawn below (index n + 2 once the pending event
+  // is kept; n + 1 when there is none)
+  const double tau = quotient(q.pend_E, q.pend_a0);
   const double a0 = prefix_sums(e.M, q);
-  const bool done = settle(a, e, q, true);
+  const EventRandom r_after = event_random(q.n + (q.pend ? 2u : 1u), q.traj_id, e.sid, e.key0, e.key1, e.s_inv,
+                                           e.s_lnf);
+  const bool done = settle(a, e, q, tau, true);
   const EventRandom r = q.rnd;
-  q.rnd = event_random(q.n + 1u, q.traj_id, e.sid, e.key0, e.key1, e.s_inv, e.s_lnf);
-  draw<DENSE>(e, q, a0, r, done);
+  q.rnd = r_after;
+  draw(e, q, a0, r, done);
   return done;
 }
 
@@ -402,7 +416,8 @@ __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Tra
   q.pend = (shfl_all((int)q.pend, src) != 0) && gactive;
   q.pend_over = shfl_all((int)q.pend_over, src) != 0;
   q.pend_j = shfl_all(q.pend_j, src);
-  q.pend_t = shfl_all(q.pend_t, src);
+  q.pend_E = shfl_all(q.pend_E, src);
+  q.pend_a0 = shfl_all(q.pend_a0, src);
   q.have = gactive;
   q.dirty = (1u << MAXM) - 1u;  // recompute every propensity from the copied state
   // this lane's propensity slots: j = gl + 8 i
@@ -451,14 +466,15 @@ __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Tra
     for (int j = 0; j < MAXM; ++j) {
       if (j < e.M) q.av[j] = shfl_all(mine[j / kCoopGroup], j % kCoopGroup, kCoopGroup);
     }
+    const double tau = quotient(q.pend_E, q.pend_a0);
     const double a0 = prefix_sums(e.M, q);
-    const bool done = settle(a, e, q, gl == 0) && q.have;
+    const bool done = settle(a, e, q, tau, gl == 0) && q.have;
     // this event's random numbers, from the lane that holds them
     const int slot = (int)(q.n - base) & (kCoopGroup - 1);
     EventRandom r;
     r.E = shfl_all(cache.E, slot, kCoopGroup);
     r.u2 = shfl_all(cache.u2, slot, kCoopGroup);
-    draw<false>(e, q, a0, r, done || !q.have);
+    draw(e, q, a0, r, done || !q.have);
     if (done) {
       if (gl == 0) finish_trajectory(a, q, blk);
       q.have = false;
@@ -537,7 +553,8 @@ __global__ void __launch_bounds__(512) k_ssa_thread(const RunArgs a) {
   q.maxx = 0;
   q.flags = 0;
   q.pend_j = 0;
-  q.pend_t = 0.0;
+  q.pend_E = 0ULL;
+  q.pend_a0 = 0.0;
   q.rnd = EventRandom{0ULL, 0ULL};
   bool exhausted = false;  // this lane saw the work counter run out
 
