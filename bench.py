@@ -10,6 +10,10 @@ sums, mean, variance).  Inputs are resident on the device; each step uses a
 new seed.  L2 is flushed (256 MiB write) between timed steps, outside the
 timed events.
 
+--workload random runs the random 32-species / 128-reaction network instead
+(262,144 trajectories, t_end = 10, 1001-point grid), which the library runs
+one trajectory per warp with the W32 summation schedule.
+
 --impl reference times the oracle (plain single-threaded C++ per trajectory,
 run on all host cores over trajectory-id ranges) on a bounded sample of the
 same workload.
@@ -40,6 +44,16 @@ SMS_GB300 = 152
 # profiles/k_ssa_thread_hiv_shaped.md: tables, grid and parameters; the
 # difference sums stay in L2), independent of the number of trajectories.
 SIM_KERNEL_DRAM_BYTES = 841728
+# Bench workloads: the HIV-shaped model (the headline line) and the random
+# 32-species / 128-reaction network (one trajectory per warp).
+WORKLOADS = {
+    "hiv_shaped": {"factory": "workload_hiv_shaped", "name": "hiv_shaped_S4_M10_G3001_T30", "n_traj": 65536,
+                   "steps": 100, "e2e_steps": 20, "cpu_sample": 16384, "ref_sample": 4096,
+                   "kernel": "k_ssa_thread", "dram_bytes": SIM_KERNEL_DRAM_BYTES},
+    "random": {"factory": "workload_random", "name": "random_S32_M128_G1001_T10_netseed3", "n_traj": 262144,
+               "steps": 10, "e2e_steps": 3, "cpu_sample": 2048, "ref_sample": 512,
+               "kernel": "k_ssa_warp", "dram_bytes": None},
+}
 FP64_OPS_PER_SM_CLK = 2.0  # 1.25 TFLOP/s dense FP64 (FMA = 2 flops) / (152 SMs * 2.07 GHz)
 
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -50,11 +64,14 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 def parse_args():
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--steps", type=int, default=None, help="timed steps (default per workload)")
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--n-traj", type=int, default=65536, help="trajectories per GPU")
-    p.add_argument("--e2e-steps", type=int, default=20)
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="hiv_shaped",
+                   help="hiv_shaped: 4 species / 10 reactions, 65,536 trajectories, thread kernel; random: "
+                        "32 species / 128 reactions, 262,144 trajectories, warp kernel")
+    p.add_argument("--n-traj", type=int, default=None, help="trajectories per GPU (default per workload)")
+    p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--profile-small", action="store_true",
                    help="one small step for an ncu capture (--profile-n trajectories); prints no bench line")
@@ -64,7 +81,18 @@ def parse_args():
                         "cycles per event of its longest trajectory (the serial floor of the step)")
     p.add_argument("--probe", choices=["pipes", "latency", "step"],
                    help="build and run one of the pipe / latency / step-part probes in csrc/probes")
-    return p.parse_args()
+    args = p.parse_args()
+    spec = WORKLOADS[args.workload]
+    args.steps = spec["steps"] if args.steps is None else args.steps
+    args.n_traj = spec["n_traj"] if args.n_traj is None else args.n_traj
+    args.e2e_steps = spec["e2e_steps"] if args.e2e_steps is None else args.e2e_steps
+    return args
+
+
+def make_workload(args, n):
+    import workloads as W
+    spec = WORKLOADS[args.workload]
+    return getattr(W, spec["factory"])(n)
 
 
 def dist_env():
@@ -147,11 +175,11 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    import workloads as W
-    w = W.workload_hiv_shaped(args.n_traj)
+    spec = WORKLOADS[args.workload]
+    w = make_workload(args, args.n_traj)
     oracle.lib()
     cores = os.cpu_count() or 1
-    sample = min(args.n_traj, 4096)
+    sample = min(args.n_traj, spec["ref_sample"])
     for i in range(args.warmup):
         oracle.run(w.net, sample, w.t_end, w.n_grid, 1 + i, threads=cores)
     events = 0
@@ -165,7 +193,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "hiv_shaped_S4_M10_G3001_T30", "n_traj": args.n_traj, "n_grid": w.n_grid,
+        "config": {"workload": spec["name"], "n_traj": args.n_traj, "n_grid": w.n_grid,
                    "t_end": w.t_end, "precision": "fp64", "sample_per_step": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{sample} trajectories per step (seeds 1000..), {cores} threads"},
@@ -179,8 +207,8 @@ def run_ours(args):
     import torch
 
     import paper_1007_1768_gb300 as ssa
-    import workloads as W
 
+    spec = WORKLOADS[args.workload]
     rank, world, local = dist_env()
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
@@ -193,7 +221,7 @@ def run_ours(args):
         pg = dist
 
     n = args.n_traj if not args.profile_small else args.profile_n
-    w = W.workload_hiv_shaped(n)
+    w = make_workload(args, n)
     model = ssa.Model.from_network(w.net)
     G, S, M = w.n_grid, w.net.n_species, w.net.n_reactions
     stream = torch.cuda.current_stream(dev)
@@ -289,20 +317,20 @@ def run_ours(args):
         e_dt = time.perf_counter() - t0
         e2e = {"value": e_ev / e_dt, "unit": UNIT, "h2d_bytes_per_step": int(grid_h.nbytes),
                "d2h_bytes_per_step": int(2 * G * S * 8 + 8 * 8), "steps": args.e2e_steps}
-        cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(w, min(n, 16384))
+        cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(w, min(n, spec["cpu_sample"]))
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "hiv_shaped_S4_M10_G3001_T30", "n_traj_per_gpu": n, "n_grid": G,
+            "config": {"workload": spec["name"], "n_traj_per_gpu": n, "n_grid": G,
                        "t_end": w.t_end, "precision": "fp64-exact", "seeds": "1000+step",
                        "l2": "flushed between timed steps (256 MiB write outside the step events)",
                        "parallelism": f"replicas x{world} (trajectory-id shards)"},
             "traj_per_s": world * n / (total_ms * 1e-3 / K) if K else None,
             "events_per_step": events_all / K,
             "wall_s_timed_region": wall,
-            "roofline": {"bound": "alu", "kernel": "k_ssa_thread", "achieved": achieved, "peak": peak,
-                         "unit": "GFLOP/s (FP64 ops)", "frac": achieved / peak, "traffic": SIM_KERNEL_DRAM_BYTES,
+            "roofline": {"bound": "alu", "kernel": spec["kernel"], "achieved": achieved, "peak": peak,
+                         "unit": "GFLOP/s (FP64 ops)", "frac": achieved / peak, "traffic": spec["dram_bytes"],
                          "kernel_ms": kern_avg, "ops_per_event": fp64_ops_per_event(M),
                          "peak_basis": "2 FP64 ops/clk/SM x 152 SMs x median SM clock (nominal 1.25 TFLOP/s dense)"},
             "cpu_baseline": cpu,

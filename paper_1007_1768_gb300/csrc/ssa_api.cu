@@ -370,9 +370,14 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
     if (st != SSA_OK) return st;
   }
   if (o.precision != SSA_PREC_FP64) return fail(SSA_EUNSUPPORTED, "only SSA_PREC_FP64 is built");
-  if (o.schedule == SSA_SCHED_WARP || !m->has_small)
-    return fail(SSA_EUNSUPPORTED, "networks with more than %d reactions or species need the warp schedule",
-                kThreadMaxM);
+  // AUTO: one trajectory per thread when the network fits its registers,
+  // else one per warp
+  const bool use_warp = o.schedule == SSA_SCHED_WARP || (o.schedule == SSA_SCHED_AUTO && !m->has_small);
+  if (!use_warp && !m->has_small)
+    return fail(SSA_EUNSUPPORTED, "the thread schedule takes at most %d reactions and %d species", kThreadMaxM,
+                kThreadMaxS);
+  if (use_warp && warp_max_chunk(m->M) == 0)
+    return fail(SSA_EUNSUPPORTED, "the warp schedule takes at most %d reactions", kWarpMaxM);
   const int64_t max_events = (o.max_events > 0) ? o.max_events : SSA_DEFAULT_MAX_EVENTS;
 
   int dev = 0;
@@ -388,10 +393,26 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
   // launch shape
   const int S = m->S, G = n_grid;
   LaunchPlan plan;
-  if (const char* msg = plan_thread_launch(S, m->M, G, n_traj, di.sms, di.smem_optin, o.reduce, o.block_threads,
-                                           o.grid_blocks, &plan))
-    return fail(SSA_EINVAL, "%s", msg);
-  SSA_CUDA_TRY(thread_kernel_set_smem(m->M, S, plan.shared_d, plan.smem));
+  if (use_warp) {
+    if (o.block_threads > 256) return fail(SSA_EINVAL, "the warp schedule takes at most 256 threads per CTA");
+    plan.threads = o.block_threads ? o.block_threads : 256;
+    plan.shared_d = false;
+    plan.smem = warp_kernel_smem(m->M, S, (int)m->nu_idx.size(), plan.threads);
+    if (plan.smem > di.smem_optin)
+      return fail(SSA_EUNSUPPORTED, "the warp kernel needs %zu bytes of shared memory per CTA (%zu available)",
+                  plan.smem, di.smem_optin);
+    int per_sm = 0;
+    SSA_CUDA_TRY(warp_kernel_prepare(m->M, plan.smem, plan.threads, &per_sm));
+    if (per_sm < 1) return fail(SSA_EUNSUPPORTED, "the warp kernel cannot be resident with this shape");
+    const int64_t want = (n_traj + plan.threads / 32 - 1) / (plan.threads / 32);
+    const int64_t cap = (int64_t)di.sms * per_sm;
+    plan.blocks = o.grid_blocks ? o.grid_blocks : (int)(want < cap ? want : cap);
+  } else {
+    if (const char* msg = plan_thread_launch(S, m->M, G, n_traj, di.sms, di.smem_optin, o.reduce, o.block_threads,
+                                             o.grid_blocks, &plan))
+      return fail(SSA_EINVAL, "%s", msg);
+    SSA_CUDA_TRY(thread_kernel_set_smem(m->M, S, plan.shared_d, plan.smem));
+  }
 
   // workspace
   const Workspace wl = workspace_layout(S, G, n_traj, o);
@@ -465,7 +486,10 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
     SSA_RUN_TRY(cudaEventRecord(ev0, stream));
   }
   if (o.sim_event_begin) SSA_RUN_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.sim_event_begin), stream));
-  SSA_RUN_TRY(launch_thread_kernel(a, plan.blocks, plan.threads, plan.shared_d, plan.smem, stream));
+  if (use_warp)
+    SSA_RUN_TRY(launch_warp_kernel(a, plan.blocks, plan.threads, plan.smem, stream));
+  else
+    SSA_RUN_TRY(launch_thread_kernel(a, plan.blocks, plan.threads, plan.shared_d, plan.smem, stream));
   if (o.sim_event_end) SSA_RUN_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.sim_event_end), stream));
   SSA_RUN_TRY(launch_finalize(a.D1, a.D2, G, S, n_traj, dm.x0, d_mean, d_var, d_s1, d_s2, stream));
   if (stats) SSA_RUN_TRY(cudaEventRecord(ev1, stream));

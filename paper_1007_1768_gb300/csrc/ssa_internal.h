@@ -132,6 +132,16 @@ constexpr int kThreadMaxM = 16;
 constexpr int kThreadMaxS = 16;
 cudaError_t thread_kernel_set_smem(int M, int S, bool shared_d, size_t smem_bytes);
 
+// Warp-per-trajectory kernel (ssa_warp_kernel.cu), schedule W32.  Chunk
+// bound of the instantiation serving M reactions (0 when M > 512).
+int warp_max_chunk(int M);
+constexpr int kWarpMaxM = 512;
+// Dynamic shared memory of one CTA of `threads` threads.
+size_t warp_kernel_smem(int M, int S, int nnz, int threads);
+// Sets the kernel's shared-memory limit and reports resident CTAs per SM.
+cudaError_t warp_kernel_prepare(int M, size_t smem, int threads, int* blocks_per_sm);
+cudaError_t launch_warp_kernel(const RunArgs& a, int blocks, int threads, size_t smem, cudaStream_t stream);
+
 // Host image of a model's device tables (see DevModel for the layout), for
 // entry points that place the tables themselves.
 struct ModelImageView {

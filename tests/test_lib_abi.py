@@ -126,3 +126,18 @@ def test_host_run_rejects_bad_arguments_before_touching_the_gpu():
     with pytest.raises(ssa.SSAError):
         ssa.ensemble_run(model, 10, 10.0, 11, seed=1, block_threads=48)
     model.close()
+
+
+def test_schedule_limits_are_refused_before_touching_the_gpu():
+    import workloads as W
+    big = ssa.Model.from_network(W.random_network(3))  # 32 species, 128 reactions
+    with pytest.raises(ssa.SSAError) as e:
+        ssa.ensemble_run(big, 10, 1.0, 11, seed=1, schedule="thread")
+    assert e.value.status == binding.SSA_EUNSUPPORTED and "thread schedule" in str(e.value)
+    big.close()
+    huge = ssa.Model.from_network(W.random_network(4, n_species=8, n_reactions=513))
+    for sched in ("auto", "warp"):
+        with pytest.raises(ssa.SSAError) as e:
+            ssa.ensemble_run(huge, 10, 1.0, 11, seed=1, schedule=sched)
+        assert e.value.status == binding.SSA_EUNSUPPORTED and "512" in str(e.value)
+    huge.close()
