@@ -37,6 +37,8 @@ _lib = None
 
 SCHEDULE_L = 0     # left-to-right a0 / prefix sums
 SCHEDULE_W32 = 1   # 32-lane chunked sums + Kogge-Stone scan
+PRECISION_FP64 = 0  # FP64 propensities (exact mode)
+PRECISION_FP32 = 1  # binary32 propensities and selection sums, FP64 a0 and time
 FLAG_TRUNCATED = 1
 FLAG_OVERFLOW = 2
 MAX_EVENTS = (1 << 32) - 1  # the event index is a 32-bit Philox counter word
@@ -136,10 +138,10 @@ def lib():
         L.oracle_uniform_grid.argtypes = [ctypes.c_int, f64, vp]
         L.oracle_uniform_grid.restype = None
         L.oracle_run.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, i64, i64, f64, ctypes.c_int, vp,
-                                 u64, u64, i64, ctypes.c_int, vp, vp, vp, vp, vp, vp]
+                                 u64, u64, i64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp]
         L.oracle_run.restype = ctypes.c_int
         L.oracle_trace.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, i64, f64, ctypes.c_int, vp, u64,
-                                   u64, i64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
+                                   u64, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
         L.oracle_trace.restype = ctypes.c_int
         L.oracle_prefix.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, vp]
         L.oracle_prefix.restype = None
@@ -188,15 +190,17 @@ def _model_arrays(net):
 
 
 class OracleResult:
-    def __init__(self, S1, S2, totals, traj_events=None, traj_hash=None, traj_flags=None):
+    def __init__(self, S1, S2, totals, traj_events=None, traj_hash=None, traj_flags=None, S3=None, S4=None):
         self.S1, self.S2 = S1, S2
+        self.S3, self.S4 = S3, S4
         self.events, self.truncated, self.overflowed, self.max_x = (int(v) for v in totals)
         self.traj_events, self.traj_hash, self.traj_flags = traj_events, traj_hash, traj_flags
 
 
 def run(net, n_traj: int, t_end: float, n_grid: int, seed: int, grid=None, traj_begin: int = 0,
         stream: int = 0, max_events: int = MAX_EVENTS, schedule: int = SCHEDULE_L,
-        per_traj: bool = False, threads: int = 1, ids=None) -> OracleResult:
+        per_traj: bool = False, threads: int = 1, ids=None, precision: int = PRECISION_FP64,
+        moments: bool = False) -> OracleResult:
     """Runs trajectory ids [traj_begin, traj_begin + n_traj) (or the explicit
     list ``ids``) and returns the exact int64 grid sums S1 = sum x,
     S2 = sum x^2 (shape [G, S]) plus totals.  ``threads`` > 1 splits the ids
@@ -216,6 +220,8 @@ def run(net, n_traj: int, t_end: float, n_grid: int, seed: int, grid=None, traj_
     def work(span_list):
         s1 = np.zeros((G, S), dtype=np.int64)
         s2 = np.zeros((G, S), dtype=np.int64)
+        s3 = np.zeros((G, S), dtype=np.float64) if moments else None
+        s4 = np.zeros((G, S), dtype=np.float64) if moments else None
         tot = np.zeros(4, dtype=np.int64)
         cnt = sum(e - b for b, e in span_list)
         ev = np.zeros(cnt, dtype=np.int64) if per_traj else None
@@ -226,14 +232,15 @@ def run(net, n_traj: int, t_end: float, n_grid: int, seed: int, grid=None, traj_
             n = e - b
             rc = L.oracle_run(S, M, R.ctypes.data, P.ctypes.data, c.ctypes.data, x0.ctypes.data, b, e,
                               float(t_end), G, g.ctypes.data, int(seed), int(stream), int(max_events),
-                              int(schedule), s1.ctypes.data, s2.ctypes.data,
+                              int(schedule), int(precision), s1.ctypes.data, s2.ctypes.data,
+                              s3.ctypes.data if moments else None, s4.ctypes.data if moments else None,
                               ev[off:].ctypes.data if per_traj else None,
                               hs[off:].ctypes.data if per_traj else None,
                               fl[off:].ctypes.data if per_traj else None, tot.ctypes.data)
             if rc != 0:
                 raise ValueError("oracle_run rejected its arguments")
             off += n
-        return s1, s2, tot, ev, hs, fl
+        return s1, s2, tot, ev, hs, fl, s3, s4
 
     if threads <= 1 or n_total < 2:
         parts = [work(spans)]
@@ -254,8 +261,10 @@ def run(net, n_traj: int, t_end: float, n_grid: int, seed: int, grid=None, traj_
     S1 = np.zeros((G, S), dtype=np.int64)
     S2 = np.zeros((G, S), dtype=np.int64)
     tot = np.zeros(4, dtype=np.int64)
+    S3 = sum(p[6] for p in parts) if moments else None
+    S4 = sum(p[7] for p in parts) if moments else None
     with np.errstate(over="ignore"):
-        for s1, s2, t, _, _, _ in parts:
+        for s1, s2, t, *_ in parts:
             S1 = (S1.view(np.uint64) + s1.view(np.uint64)).view(np.int64)
             S2 = (S2.view(np.uint64) + s2.view(np.uint64)).view(np.int64)
             tot[:3] += t[:3]
@@ -264,12 +273,13 @@ def run(net, n_traj: int, t_end: float, n_grid: int, seed: int, grid=None, traj_
         ev = np.concatenate([p[3] for p in parts])
         hs = np.concatenate([p[4] for p in parts])
         fl = np.concatenate([p[5] for p in parts])
-        return OracleResult(S1, S2, tot, ev, hs, fl)
-    return OracleResult(S1, S2, tot)
+        return OracleResult(S1, S2, tot, ev, hs, fl, S3, S4)
+    return OracleResult(S1, S2, tot, S3=S3, S4=S4)
 
 
 def trace(net, traj_id: int, t_end: float, n_grid: int, seed: int, grid=None, stream: int = 0,
-          max_events: int = MAX_EVENTS, schedule: int = SCHEDULE_L, record_max: int = 100000):
+          max_events: int = MAX_EVENTS, schedule: int = SCHEDULE_L, record_max: int = 100000,
+          precision: int = PRECISION_FP64):
     """One trajectory: (event times, reaction indices, per-grid states [G, S], flags)."""
     L = lib()
     R, P, c, x0 = _model_arrays(net)
@@ -281,7 +291,8 @@ def trace(net, traj_id: int, t_end: float, n_grid: int, seed: int, grid=None, st
     ne = np.zeros(1, dtype=np.int64)
     flags = L.oracle_trace(net.n_species, net.n_reactions, R.ctypes.data, P.ctypes.data, c.ctypes.data,
                            x0.ctypes.data, int(traj_id), float(t_end), G, g.ctypes.data, int(seed), int(stream),
-                           int(max_events), int(schedule), record_max, rt.ctypes.data, rj.ctypes.data,
+                           int(max_events), int(schedule), int(precision), record_max, rt.ctypes.data,
+                           rj.ctypes.data,
                            xs.ctypes.data, ne.ctypes.data)
     n = int(min(ne[0], record_max))
     return rt[:n], rj[:n], xs, int(flags), int(ne[0])

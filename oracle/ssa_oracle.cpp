@@ -38,6 +38,19 @@
 //     (right-continuous); an event whose time exceeds t_end is not fired;
 //   * a0 == 0 makes the state absorbing (t_next = +inf).
 //
+// FP32-propensity mode (the precision variant; time stays FP64):
+//   * a_j = (float)c_j * (float)h_j in binary32, each step rounded to nearest;
+//   * the selection prefix sums are binary32 sums of these a_j in the
+//     run's schedule (L or W32), with total A32 (the last prefix or the
+//     scan's lane-31 value);
+//   * a0 is an FP64 sum of the (exactly widened) binary32 a_j in the same
+//     schedule, formed again at every event (no incremental drift), and
+//     t_next = t + (-ln r1) / a0 in FP64;
+//   * selection: smallest j with (double)prefix_j > r2 * (double)A32 (FP64
+//     product); if none, the last j with a_j > 0.
+// When every product and sum is exact in binary32, this mode reproduces the
+// FP64 mode's trajectories bit for bit.
+//
 // Build: g++ -O2 -ffp-contract=off (no FMA contraction), no -ffast-math.
 #include <cstdint>
 #include <cstring>
@@ -158,27 +171,28 @@ int64_t mass_action_h(const Model& m, int j, const std::vector<int64_t>& x) {
 // previous step's values).  The prefix of reaction j is (scan of lanes before
 // j's lane) + (left-to-right sum inside j's chunk up to j), formed as
 // excl + inner with excl = 0 for lane 0.  a0 is lane 31's inclusive value.
-void w32_prefix(const std::vector<double>& a, int M, std::vector<double>& prefix, double* a0) {
+template <typename T>
+void w32_prefix(const std::vector<T>& a, int M, std::vector<T>& prefix, T* a0) {
   const int chunk = (M + 31) / 32;
-  double part[32];
+  T part[32];
   for (int l = 0; l < 32; ++l) {
-    double s = 0.0;
+    T s = 0;
     for (int q = 0; q < chunk; ++q) {
       int j = l * chunk + q;
       if (j < M) s = (q == 0) ? a[j] : s + a[j];
     }
     part[l] = s;
   }
-  double scan[32];
+  T scan[32];
   for (int l = 0; l < 32; ++l) scan[l] = part[l];
   for (int off = 1; off < 32; off <<= 1) {
-    double prev[32];
+    T prev[32];
     for (int l = 0; l < 32; ++l) prev[l] = scan[l];
     for (int l = off; l < 32; ++l) scan[l] = prev[l] + prev[l - off];
   }
   for (int l = 0; l < 32; ++l) {
-    double excl = (l == 0) ? 0.0 : scan[l - 1];
-    double inner = 0.0;
+    T excl = (l == 0) ? 0 : scan[l - 1];
+    T inner = 0;
     for (int q = 0; q < chunk; ++q) {
       int j = l * chunk + q;
       if (j >= M) break;
@@ -207,13 +221,14 @@ struct TrajResult {
 // One trajectory of the direct method with grid alignment (emission into
 // S1 / S2 of x and x^2 at every grid point, right-continuous).
 TrajResult run_one(const Model& m, uint64_t traj_id, double t_end, int G, const double* grid,
-                   uint64_t seed, uint64_t stream, int64_t max_events, int schedule,
-                   uint64_t* S1, uint64_t* S2,
+                   uint64_t seed, uint64_t stream, int64_t max_events, int schedule, int precision,
+                   uint64_t* S1, uint64_t* S2, double* S3, double* S4,
                    int record_max, double* rec_t, int32_t* rec_j) {
   TrajResult res;
   std::vector<int64_t> x(m.S);
   for (int s = 0; s < m.S; ++s) { x[s] = m.x0[s]; if (x[s] > res.max_x) res.max_x = x[s]; }
-  std::vector<double> a(m.M), prefix(m.M);
+  std::vector<double> a(m.M), prefix(m.M), a_wide(m.M), scratch(m.M);
+  std::vector<float> a32(m.M), prefix32(m.M);
   const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   uint32_t words[4] = {0, 0, 0, 0};
   double t = 0.0;
@@ -224,18 +239,43 @@ TrajResult run_one(const Model& m, uint64_t traj_id, double t_end, int G, const 
       for (int s = 0; s < m.S; ++s) {
         S1[(size_t)k * m.S + s] += (uint64_t)x[s];
         S2[(size_t)k * m.S + s] += (uint64_t)(x[s] * x[s]);
+        if (S3) {
+          const double xd = (double)x[s];
+          S3[(size_t)k * m.S + s] += xd * xd * xd;
+          S4[(size_t)k * m.S + s] += (xd * xd) * (xd * xd);
+        }
       }
       ++k;
     }
   };
   for (;;) {
     // propensities (Sec. 3.2: mass action), a0 and selection prefix sums
-    for (int j = 0; j < m.M; ++j) a[j] = m.c[j] * (double)mass_action_h(m, j, x);
     double a0 = 0.0;
-    if (schedule == 0) {
-      for (int j = 0; j < m.M; ++j) { a0 = (j == 0) ? a[0] : a0 + a[j]; prefix[j] = a0; }
+    float a0_32 = 0.0f;
+    if (precision == 0) {
+      for (int j = 0; j < m.M; ++j) a[j] = m.c[j] * (double)mass_action_h(m, j, x);
+      if (schedule == 0) {
+        for (int j = 0; j < m.M; ++j) { a0 = (j == 0) ? a[0] : a0 + a[j]; prefix[j] = a0; }
+      } else {
+        w32_prefix(a, m.M, prefix, &a0);
+      }
     } else {
-      w32_prefix(a, m.M, prefix, &a0);
+      for (int j = 0; j < m.M; ++j) {
+        a32[j] = (float)m.c[j] * (float)mass_action_h(m, j, x);
+        a_wide[j] = (double)a32[j];
+        a[j] = a_wide[j];
+      }
+      if (schedule == 0) {
+        for (int j = 0; j < m.M; ++j) {
+          a0_32 = (j == 0) ? a32[0] : a0_32 + a32[j];
+          prefix32[j] = a0_32;
+          a0 = (j == 0) ? a_wide[0] : a0 + a_wide[j];
+        }
+      } else {
+        w32_prefix(a32, m.M, prefix32, &a0_32);
+        w32_prefix(a_wide, m.M, scratch, &a0);
+      }
+      for (int j = 0; j < m.M; ++j) prefix[j] = (double)prefix32[j];
     }
     // random numbers for event n
     const uint32_t ctr[4] = {(uint32_t)n, (uint32_t)traj_id, (uint32_t)(traj_id >> 32), (uint32_t)stream};
@@ -250,8 +290,10 @@ TrajResult run_one(const Model& m, uint64_t traj_id, double t_end, int G, const 
     }
     emit_until(t_next);
     if (t_next > t_end) break;
-    // select the transition: smallest j with prefix_j > r2 * a0
-    const double target = ((double)odd53(words[2], words[3]) * 0x1p-53) * a0;
+    // select the transition: smallest j with prefix_j > r2 * a0 (FP32
+    // mode: r2 times the binary32 total of the prefix sums)
+    const double sel_total = (precision == 0) ? a0 : (double)a0_32;
+    const double target = ((double)odd53(words[2], words[3]) * 0x1p-53) * sel_total;
     int jsel = -1;
     for (int j = 0; j < m.M; ++j) {
       if (prefix[j] > target) { jsel = j; break; }
@@ -326,21 +368,25 @@ void oracle_uniform_grid(int G, double t_end, double* grid) {
 }
 
 // Runs trajectories [traj_begin, traj_end) and ADDS their x and x^2 grid sums
-// into S1 / S2 (int64, wrapping, G x S row-major).  Per-trajectory outputs are
-// indexed by id - traj_begin and may be null.  totals[0..3] receive (added):
+// into S1 / S2 (int64, wrapping, G x S row-major), and, when S3 / S4 are
+// given, x^3 and x^4 as FP64 sums (for standard errors of the variance).
+// schedule: 0 = L, 1 = W32; precision: 0 = FP64, 1 = FP32 propensities.
+// Per-trajectory outputs are indexed by id - traj_begin and may be null.  totals[0..3] receive (added):
 // events, truncated trajectories, overflowed trajectories, max state seen.
 // Returns 0, or -1 on bad arguments / uninitialised tables.
 int oracle_run(int S, int M, const int32_t* R, const int32_t* P, const double* c, const int32_t* x0,
                int64_t traj_begin, int64_t traj_end, double t_end, int G, const double* grid,
-               uint64_t seed, uint64_t stream, int64_t max_events, int schedule,
-               int64_t* S1, int64_t* S2,
+               uint64_t seed, uint64_t stream, int64_t max_events, int schedule, int precision,
+               int64_t* S1, int64_t* S2, double* S3, double* S4,
                int64_t* traj_events, uint64_t* traj_hash, int32_t* traj_flags, int64_t* totals) {
-  if (!g_log.ready || traj_end < traj_begin || G < 1 || (schedule != 0 && schedule != 1)) return -1;
+  if (!g_log.ready || traj_end < traj_begin || G < 1 || (schedule != 0 && schedule != 1) ||
+      (precision != 0 && precision != 1) || ((S3 == nullptr) != (S4 == nullptr)))
+    return -1;
   Model m;
   if (!build_model(S, M, R, P, c, x0, &m)) return -1;
   for (int64_t id = traj_begin; id < traj_end; ++id) {
-    TrajResult r = run_one(m, (uint64_t)id, t_end, G, grid, seed, stream, max_events, schedule,
-                           (uint64_t*)S1, (uint64_t*)S2, 0, nullptr, nullptr);
+    TrajResult r = run_one(m, (uint64_t)id, t_end, G, grid, seed, stream, max_events, schedule, precision,
+                           (uint64_t*)S1, (uint64_t*)S2, S3, S4, 0, nullptr, nullptr);
     const int64_t o = id - traj_begin;
     if (traj_events) traj_events[o] = r.events;
     if (traj_hash) traj_hash[o] = r.hash;
@@ -359,14 +405,15 @@ int oracle_run(int S, int M, const int32_t* R, const int32_t* P, const double* c
 // record_max events) and its per-grid states into xs (G x S).
 int oracle_trace(int S, int M, const int32_t* R, const int32_t* P, const double* c, const int32_t* x0,
                  int64_t traj_id, double t_end, int G, const double* grid, uint64_t seed,
-                 uint64_t stream, int64_t max_events, int schedule, int record_max,
+                 uint64_t stream, int64_t max_events, int schedule, int precision, int record_max,
                  double* rec_t, int32_t* rec_j, int64_t* xs, int64_t* n_events) {
   if (!g_log.ready) return -1;
   Model m;
   if (!build_model(S, M, R, P, c, x0, &m)) return -1;
   std::vector<uint64_t> s1((size_t)G * S, 0), s2((size_t)G * S, 0);
-  TrajResult r = run_one(m, (uint64_t)traj_id, t_end, G, grid, seed, stream, max_events, schedule,
-                         s1.data(), s2.data(), record_max, rec_t, rec_j);
+  if ((schedule != 0 && schedule != 1) || (precision != 0 && precision != 1)) return -1;
+  TrajResult r = run_one(m, (uint64_t)traj_id, t_end, G, grid, seed, stream, max_events, schedule, precision,
+                         s1.data(), s2.data(), nullptr, nullptr, record_max, rec_t, rec_j);
   for (size_t q = 0; q < (size_t)G * S; ++q) xs[q] = (int64_t)s1[q];
   *n_events = r.events;
   return r.flags;
