@@ -143,6 +143,8 @@ def lib():
         L.oracle_trace.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, i64, f64, ctypes.c_int, vp, u64,
                                    u64, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
         L.oracle_trace.restype = ctypes.c_int
+        L.oracle_select.argtypes = [ctypes.c_int, vp, ctypes.c_int, f64]
+        L.oracle_select.restype = ctypes.c_int
         L.oracle_prefix.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, vp]
         L.oracle_prefix.restype = None
         L.oracle_finalize.argtypes = [i64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
@@ -296,6 +298,13 @@ def trace(net, traj_id: int, t_end: float, n_grid: int, seed: int, grid=None, st
                            xs.ctypes.data, ne.ctypes.data)
     n = int(min(ne[0], record_max))
     return rt[:n], rj[:n], xs, int(flags), int(ne[0])
+
+
+def select(a, target: float, schedule: int = SCHEDULE_L) -> int:
+    """The reaction index the direct method picks for propensities ``a`` and
+    the target r2 * total (-1 when every a_j is zero)."""
+    av = np.ascontiguousarray(a, dtype=np.float64)
+    return int(lib().oracle_select(av.shape[0], av.ctypes.data, int(schedule), float(target)))
 
 
 def prefix_sums(a, schedule: int = SCHEDULE_L):

@@ -32,8 +32,9 @@
 //   * h_j = prod_s C(x_s, R_js); a_j = c_j * (double)h_j;
 //     a0 and the selection prefix sums are left-to-right FP64 sums (schedule
 //     L) or the 32-lane chunked scan described at w32_prefix() (schedule W32);
-//   * selection: smallest j with prefix_j > r2 * a0; if rounding leaves none,
-//     the last j with a_j > 0;
+//   * selection: smallest j with a_j > 0 and prefix_j > r2 * a0; if rounding
+//     leaves none, the last j with a_j > 0 (zero-propensity transitions are
+//     never chosen);
 //   * grid value at g_k is the state after all events with time <= g_k
 //     (right-continuous); an event whose time exceeds t_end is not fired;
 //   * a0 == 0 makes the state absorbing (t_next = +inf).
@@ -46,8 +47,8 @@
 //   * a0 is an FP64 sum of the (exactly widened) binary32 a_j in the same
 //     schedule, formed again at every event (no incremental drift), and
 //     t_next = t + (-ln r1) / a0 in FP64;
-//   * selection: smallest j with (double)prefix_j > r2 * (double)A32 (FP64
-//     product); if none, the last j with a_j > 0.
+//   * selection: smallest j with a_j > 0 and (double)prefix_j > r2 *
+//     (double)A32 (FP64 product); if none, the last j with a_j > 0.
 // When every product and sum is exact in binary32, this mode reproduces the
 // FP64 mode's trajectories bit for bit.
 //
@@ -203,6 +204,22 @@ void w32_prefix(const std::vector<T>& a, int M, std::vector<T>& prefix, T* a0) {
   *a0 = scan[31];
 }
 
+// Selection (Sec. 2: one of the possible transitions is chosen): the
+// smallest j with a_j > 0 and prefix_j > target; if rounding leaves none,
+// the last j with a_j > 0.  A transition whose propensity is zero is not
+// possible and is never chosen.  Under schedule L the prefixes never
+// decrease, so a_j = 0 already rules j out; under W32 a lane's exclusive
+// scan value can exceed the previous lane's last prefix by rounding, and
+// without the a_j > 0 condition a zero-propensity reaction at the start of a
+// lane could be chosen.
+int select_reaction(const std::vector<double>& a, const std::vector<double>& prefix, int M, double target) {
+  for (int j = 0; j < M; ++j)
+    if (a[j] > 0.0 && prefix[j] > target) return j;
+  for (int j = M - 1; j >= 0; --j)
+    if (a[j] > 0.0) return j;
+  return -1;
+}
+
 const int kFlagTruncated = 1;
 const int kFlagOverflow = 2;
 const int64_t kStateLimit = 2147483647LL;  // int32 state
@@ -290,17 +307,11 @@ TrajResult run_one(const Model& m, uint64_t traj_id, double t_end, int G, const 
     }
     emit_until(t_next);
     if (t_next > t_end) break;
-    // select the transition: smallest j with prefix_j > r2 * a0 (FP32
-    // mode: r2 times the binary32 total of the prefix sums)
+    // select the transition: smallest j with a_j > 0 and prefix_j > r2 * a0
+    // (FP32 mode: r2 times the binary32 total of the prefix sums)
     const double sel_total = (precision == 0) ? a0 : (double)a0_32;
     const double target = ((double)odd53(words[2], words[3]) * 0x1p-53) * sel_total;
-    int jsel = -1;
-    for (int j = 0; j < m.M; ++j) {
-      if (prefix[j] > target) { jsel = j; break; }
-    }
-    if (jsel < 0) {
-      for (int j = m.M - 1; j >= 0; --j) if (a[j] > 0.0) { jsel = j; break; }
-    }
+    const int jsel = select_reaction(a, prefix, m.M, target);
     // state update, refusing to leave the int32 range
     bool over = false;
     for (int s = 0; s < m.S; ++s) {
@@ -430,6 +441,20 @@ void oracle_prefix(int M, const double* a, int schedule, double* prefix, double*
     w32_prefix(av, M, pv, a0);
   }
   for (int j = 0; j < M; ++j) prefix[j] = pv[j];
+}
+
+// The reaction the direct method picks for propensities a[0..M) (FP64
+// values; FP32-mode callers pass the widened binary32 values and prefixes)
+// and a target r2 * total; prefixes in the given schedule.  For tests.
+int oracle_select(int M, const double* a, int schedule, double target) {
+  std::vector<double> av(a, a + M), pv(M);
+  double a0 = 0.0;
+  if (schedule == 0) {
+    for (int j = 0; j < M; ++j) { a0 = (j == 0) ? av[0] : a0 + av[j]; pv[j] = a0; }
+  } else {
+    w32_prefix(av, M, pv, &a0);
+  }
+  return select_reaction(av, pv, M, target);
 }
 
 // mean = S1 / N; var = (N S2 - S1^2) / (N (N - 1)), numerator exact in int128

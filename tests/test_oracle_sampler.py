@@ -308,3 +308,35 @@ def test_w32_rounding_within_bound():
         exact = np.cumsum([Fraction(float(v)) for v in a])
         for j in range(M):
             assert abs(Fraction(float(pre[j])) - exact[j]) <= exact[j] * Fraction(64, 2 ** 53)
+
+
+def test_w32_selection_never_picks_a_zero_propensity_reaction():
+    """Under W32 a lane's exclusive scan value can exceed the previous lane's
+    last prefix by rounding, so the prefixes are not monotone at lane
+    boundaries.  A zero-propensity reaction opening a lane must still never
+    be chosen (Sec. 2: only possible transitions fire), for any target."""
+    rng = np.random.default_rng(5)
+    M = 64  # two reactions per lane
+    found = 0
+    for _ in range(200):
+        a = rng.uniform(0.1, 1.0, size=M) * 10.0 ** rng.integers(-3, 4, size=M)
+        for lane in range(1, 32):
+            j0 = 2 * lane
+            b = a.copy()
+            b[j0] = 0.0
+            pre, a0 = oracle.prefix_sums(b, oracle.SCHEDULE_W32)
+            if not pre[j0] > pre[j0 - 1]:
+                continue
+            found += 1
+            lo = pre[j0 - 1]
+            for target in (lo, np.nextafter(lo, np.inf), np.nextafter(pre[j0], -np.inf)):
+                j = oracle.select(b, target, oracle.SCHEDULE_W32)
+                assert j != j0 and b[j] > 0.0
+                assert j > j0 - 1  # prefix_{j0-1} <= target: nothing at or before j0 - 1 qualifies
+            j = oracle.select(b, np.nextafter(lo, -np.inf), oracle.SCHEDULE_W32)
+            assert j <= j0 - 1 and b[j] > 0.0
+        if found >= 5:
+            break
+    assert found >= 5
+    # all-zero propensities: nothing to choose
+    assert oracle.select(np.zeros(40), 0.0, oracle.SCHEDULE_W32) == -1
