@@ -71,6 +71,10 @@ def parse_args():
                    help="hiv_shaped: 4 species / 10 reactions, 65,536 trajectories, thread kernel; random: "
                         "32 species / 128 reactions, 262,144 trajectories, warp kernel")
     p.add_argument("--n-traj", type=int, default=None, help="trajectories per GPU (default per workload)")
+    p.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
+                   help="fp32: binary32 propensities and selection sums, FP64 a0 and time (one trajectory "
+                        "per warp); the line then adds the FP64 kernel's rate on the same GPU and the "
+                        "FP32-vs-FP64 standard-error report")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--profile-small", action="store_true",
@@ -234,8 +238,9 @@ def run_ours(args):
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     L = ssa.lib()
 
-    def run_step(seed, ev_begin=None, ev_end=None):
+    def run_step(seed, ev_begin=None, ev_end=None, precision=args.precision):
         o = ssa.make_opts(memory=ssa.binding.MEM_DEVICE, cuda_stream=stream.cuda_stream, traj_offset=rank * n,
+                          precision=precision,
                           workspace=ws.data_ptr(), workspace_bytes=ws_bytes, device_totals=totals.data_ptr(),
                           sim_event_begin=ev_begin, sim_event_end=ev_end)
         st = L.ssa_ensemble_run(model.handle, n, w.t_end, G, None, seed, o, mean.data_ptr(), var.data_ptr(),
@@ -301,6 +306,11 @@ def run_ours(args):
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
     peak = FP64_OPS_PER_SM_CLK * SMS_GB300 * sm_mhz * 1e6 * 1e-9
 
+    fp64_same_gpu = fp32_vs_fp64 = None
+    if args.precision == "fp32" and rank == 0:
+        fp64_same_gpu, fp32_vs_fp64 = compare_with_fp64(args, ssa, torch, model, w, n, run_step, totals, stream,
+                                                        flush)
+
     result = None
     if rank == 0:
         # end to end through the C ABI with host buffers: grid in, mean/var out
@@ -323,7 +333,9 @@ def run_ours(args):
             "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": spec["name"], "n_traj_per_gpu": n, "n_grid": G,
-                       "t_end": w.t_end, "precision": "fp64-exact", "seeds": "1000+step",
+                       "t_end": w.t_end,
+                       "precision": "fp64-exact" if args.precision == "fp64" else "fp32-propensities",
+                       "seeds": "1000+step",
                        "l2": "flushed between timed steps (256 MiB write outside the step events)",
                        "parallelism": f"replicas x{world} (trajectory-id shards)"},
             "traj_per_s": world * n / (total_ms * 1e-3 / K) if K else None,
@@ -334,6 +346,8 @@ def run_ours(args):
                          "kernel_ms": kern_avg, "ops_per_event": fp64_ops_per_event(M),
                          "peak_basis": "2 FP64 ops/clk/SM x 152 SMs x median SM clock (nominal 1.25 TFLOP/s dense)"},
             "cpu_baseline": cpu,
+            "fp64_same_gpu": fp64_same_gpu,
+            "fp32_vs_fp64": fp32_vs_fp64,
             "e2e": e2e,
             "gpu_launches": 3 * K,
             "clocks": clk,
@@ -343,6 +357,65 @@ def run_ours(args):
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def compare_with_fp64(args, ssa, torch, model, w, n, run_step, totals, stream, flush):
+    """For an FP32-propensity run: the FP64 kernel's events/s on the same
+    workload and GPU (same timing rules), and the standard-error report of
+    the FP32 grid mean / variance against FP64 with the same seed."""
+    import numpy as np
+    K2 = max(1, min(3, args.steps))
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(K2)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(K2)]
+    run_step(1, precision="fp64")
+    torch.cuda.synchronize()
+    totals.zero_()
+    for i in range(K2):
+        flush.fill_(i & 0xFF)
+        ev_s[i].record(stream)
+        run_step(1000 + i, precision="fp64")
+        ev_e[i].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(ev_s[i].elapsed_time(ev_e[i]) for i in range(K2))
+    ev64 = int(totals[0].item())
+    same_gpu = {"value": ev64 / (ms * 1e-3), "unit": UNIT, "steps": K2, "ms_per_step": ms / K2,
+                "events_per_step": ev64 / K2}
+    # standard errors by batch means: B shards of N / B trajectories (shards add up
+    # exactly to the full run), per precision; no distributional assumption
+    dev = torch.device("cuda", torch.cuda.current_device())
+    B = 32
+    nb = n // B
+    out = {}
+    for prec in ("fp32", "fp64"):
+        s1 = s2 = 0
+        sh_mean, sh_var, ev = [], [], 0
+        for b in range(B):
+            r = ssa.ensemble_run(model, nb, w.t_end, w.n_grid, 4242, device=dev, precision=prec,
+                                 traj_offset=b * nb)
+            a1, a2 = r.sum1.cpu().numpy(), r.sum2.cpu().numpy()
+            s1, s2 = s1 + a1, s2 + a2
+            sh_mean.append(r.mean.cpu().numpy())
+            sh_var.append(r.var.cpu().numpy())
+            ev += r.events
+        N = nb * B
+        mean = s1 / N
+        var = (N * s2.astype(np.float64) - s1.astype(np.float64) ** 2) / (N * (N - 1.0))
+        se_m = np.std(np.stack(sh_mean), axis=0, ddof=1) / np.sqrt(B)
+        se_v = np.std(np.stack(sh_var), axis=0, ddof=1) / np.sqrt(B)
+        out[prec] = (mean, var, se_m, se_v, ev)
+    m32, v32, sm32, sv32, e32 = out["fp32"]
+    m64, v64, sm64, sv64, e64 = out["fp64"]
+    se_m = np.sqrt(sm32 ** 2 + sm64 ** 2)
+    se_v = np.sqrt(sv32 ** 2 + sv64 ** 2)
+    zm = np.abs(m32 - m64) / np.where(se_m > 0, se_m, 1.0)
+    zv = np.abs(v32 - v64) / np.where(se_v > 0, se_v, 1.0)
+    zero_ok = bool(np.array_equal(m32[se_m == 0], m64[se_m == 0]) and np.array_equal(v32[se_v == 0], v64[se_v == 0]))
+    report = {"cells": int(m32.size), "max_z_mean": float(zm.max()), "max_z_var": float(zv.max()),
+              "cells_above_4se": int((zm > 4).sum() + (zv > 4).sum()), "zero_se_cells_equal": zero_ok,
+              "events_fp32": e32, "events_fp64": e64, "seed": 4242, "n_traj": nb * B,
+              "se": f"batch means over {B} shards of {nb} trajectories, per precision; "
+                    "z = |x32 - x64| / sqrt(se32^2 + se64^2)"}
+    return same_gpu, report
 
 
 def run_scan():

@@ -51,9 +51,26 @@ typedef enum ssa_status {
   SSA_EUNSUPPORTED = 7  /* valid request this build does not implement */
 } ssa_status;
 
-/* Precision of the propensity arithmetic.  Time is FP64 in every mode. */
+/* Precision of the propensity arithmetic.  Time is FP64 in every mode.
+ *   SSA_PREC_FP64: a_j = c_j * (double)h_j; a0 and the selection prefix sums
+ *     are FP64 sums in the schedule's order.
+ *   SSA_PREC_FP32: a_j = (float)c_j * (float)h_j in binary32; the selection
+ *     prefix sums are binary32 sums (schedule W32) with total A32; a0 is the
+ *     FP64 sum (schedule W32) of the exactly widened a_j, formed anew at
+ *     every event; tau = -ln(r1) / a0 and t in FP64; the reaction is the
+ *     first j with a_j > 0 and (double)prefix_j > r2 * (double)A32.  Runs
+ *     one trajectory per warp; rates must lie in the binary32 range. */
 enum { SSA_PREC_FP64 = 0, SSA_PREC_FP32 = 1 };
-/* Kernel shape: one trajectory per thread, or one per warp. */
+/* Kernel shape and summation order:
+ *   SSA_SCHED_THREAD: one trajectory per thread, sums left to right
+ *     (schedule L); networks of at most 16 reactions and 16 species.
+ *   SSA_SCHED_WARP: one trajectory per warp, schedule W32: lane l owns the
+ *     reactions l*c .. l*c + c - 1 (c = ceil(M / 32)) and sums them left to
+ *     right; the 32 lane sums are combined by an inclusive Kogge-Stone scan
+ *     (offsets 1, 2, 4, 8, 16); prefix_j = (scan of the lanes before j's
+ *     lane) + (running sum inside j's chunk); a0 = the scan's last value.
+ *     Networks of at most 512 reactions.
+ *   SSA_SCHED_AUTO: THREAD for FP64 networks that fit it, else WARP. */
 enum { SSA_SCHED_AUTO = 0, SSA_SCHED_THREAD = 1, SSA_SCHED_WARP = 2 };
 /* Where grid / outputs live. */
 enum { SSA_MEM_HOST = 0, SSA_MEM_DEVICE = 1 };
@@ -155,6 +172,9 @@ ssa_status ssa_ensemble_workspace_size(const ssa_model* model, int64_t n_traj, i
  *   sum1[k][s] = sum_i X_i,s(g_k),  sum2[k][s] = sum_i X_i,s(g_k)^2   (int64)
  *   mean = sum1 / N,  var = (N sum2 - sum1^2) / (N (N - 1))           (FP64)
  * where X_i(g) is trajectory i's state after every event with time <= g.
+ * At each event the reaction fired is the first j with a_j > 0 and
+ * prefix_j > r2 * a0 (the last j with a_j > 0 if rounding leaves none), and
+ * the time step is -ln(r1) / a0 (Sec. 2, direct method).
  * Event n of trajectory id = traj_offset + i draws one Philox4x32-10 block
  * with key (seed low word, seed high word) and counter (n, id low word, id
  * high word, opts->stream_id), so any trajectory can be reproduced alone and
@@ -164,8 +184,9 @@ ssa_status ssa_ensemble_workspace_size(const ssa_model* model, int64_t n_traj, i
  *     or NULL for g_k = (k * t_end) / (n_grid - 1) (g_0 = t_end if n_grid == 1).
  *   mean, var [G x S] doubles; sum1, sum2 [G x S] int64 or NULL.
  *   stats: host struct or NULL.
- * In SSA_PREC_FP64 the results are bit-identical to the plain CPU statement
- * of the same arithmetic (the oracle shipped with the tests).
+ * The results are bit-identical to the plain CPU statement of the same
+ * arithmetic (the oracle shipped with the tests) for the precision and
+ * summation schedule the run uses.
  * Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA, SSA_EUNSUPPORTED,
  * SSA_EOVERFLOW (only detectable when the call waits: host memory or stats).
  */

@@ -369,10 +369,18 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
     st = check_host_grid(grid, n_grid, t_end);
     if (st != SSA_OK) return st;
   }
-  if (o.precision != SSA_PREC_FP64) return fail(SSA_EUNSUPPORTED, "only SSA_PREC_FP64 is built");
-  // AUTO: one trajectory per thread when the network fits its registers,
-  // else one per warp
-  const bool use_warp = o.schedule == SSA_SCHED_WARP || (o.schedule == SSA_SCHED_AUTO && !m->has_small);
+  const bool fp32 = o.precision == SSA_PREC_FP32;
+  if (fp32) {
+    if (o.schedule == SSA_SCHED_THREAD)
+      return fail(SSA_EUNSUPPORTED, "the FP32-propensity mode runs on the warp schedule");
+    for (int32_t j = 0; j < m->M; ++j)
+      if (m->c[j] > 3.4028234663852886e38)
+        return fail(SSA_EINVAL, "rates[%d] exceeds the binary32 range of the FP32-propensity mode", j);
+  }
+  // AUTO: one trajectory per thread when the network fits its registers
+  // (FP64 mode), else one per warp
+  const bool use_warp =
+      o.schedule == SSA_SCHED_WARP || (o.schedule == SSA_SCHED_AUTO && (!m->has_small || fp32));
   if (!use_warp && !m->has_small)
     return fail(SSA_EUNSUPPORTED, "the thread schedule takes at most %d reactions and %d species", kThreadMaxM,
                 kThreadMaxS);
@@ -402,7 +410,7 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
       return fail(SSA_EUNSUPPORTED, "the warp kernel needs %zu bytes of shared memory per CTA (%zu available)",
                   plan.smem, di.smem_optin);
     int per_sm = 0;
-    SSA_CUDA_TRY(warp_kernel_prepare(m->M, plan.smem, plan.threads, &per_sm));
+    SSA_CUDA_TRY(warp_kernel_prepare(m->M, fp32, plan.smem, plan.threads, &per_sm));
     if (per_sm < 1) return fail(SSA_EUNSUPPORTED, "the warp kernel cannot be resident with this shape");
     const int64_t want = (n_traj + plan.threads / 32 - 1) / (plan.threads / 32);
     const int64_t cap = (int64_t)di.sms * per_sm;
@@ -487,7 +495,7 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
   }
   if (o.sim_event_begin) SSA_RUN_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.sim_event_begin), stream));
   if (use_warp)
-    SSA_RUN_TRY(launch_warp_kernel(a, plan.blocks, plan.threads, plan.smem, stream));
+    SSA_RUN_TRY(launch_warp_kernel(a, fp32, plan.blocks, plan.threads, plan.smem, stream));
   else
     SSA_RUN_TRY(launch_thread_kernel(a, plan.blocks, plan.threads, plan.shared_d, plan.smem, stream));
   if (o.sim_event_end) SSA_RUN_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o.sim_event_end), stream));

@@ -139,8 +139,10 @@ constexpr int kWarpMaxM = 512;
 // Dynamic shared memory of one CTA of `threads` threads.
 size_t warp_kernel_smem(int M, int S, int nnz, int threads);
 // Sets the kernel's shared-memory limit and reports resident CTAs per SM.
-cudaError_t warp_kernel_prepare(int M, size_t smem, int threads, int* blocks_per_sm);
-cudaError_t launch_warp_kernel(const RunArgs& a, int blocks, int threads, size_t smem, cudaStream_t stream);
+// fp32 selects the FP32-propensity instantiation.
+cudaError_t warp_kernel_prepare(int M, bool fp32, size_t smem, int threads, int* blocks_per_sm);
+cudaError_t launch_warp_kernel(const RunArgs& a, bool fp32, int blocks, int threads, size_t smem,
+                               cudaStream_t stream);
 
 // Host image of a model's device tables (see DevModel for the layout), for
 // entry points that place the tables themselves.

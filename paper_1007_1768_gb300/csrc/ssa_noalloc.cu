@@ -94,7 +94,7 @@ extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n
   if (!mean || !var) return record_error(SSA_EINVAL, "mean and var must not be NULL");
   if (o.memory != SSA_MEM_DEVICE)
     return record_error(SSA_EINVAL, "ssa_ensemble_run_noalloc takes device buffers only (memory = SSA_MEM_DEVICE)");
-  if (o.precision != SSA_PREC_FP64) return record_error(SSA_EUNSUPPORTED, "only SSA_PREC_FP64 is built");
+  if (o.precision != SSA_PREC_FP64) return record_error(SSA_EUNSUPPORTED, "this entry point runs SSA_PREC_FP64 only");
   if (o.schedule == SSA_SCHED_WARP || !mv.small)
     return record_error(SSA_EUNSUPPORTED, "networks with more than 16 reactions or species are not supported here");
   if (o.block_threads < 0 || o.block_threads > 512 || (o.block_threads % 32) != 0)

@@ -178,6 +178,22 @@ SF_HD uint64_t div_pos(uint64_t nb, uint64_t db, bool& ok) {
   return r;
 }
 
+// Exact widening of a non-negative binary32 value (zero, subnormal, normal
+// or +inf, given by its bits) to binary64, returned as bits.  Normal values
+// rebias the exponent (127 -> 1023) and move the significand up 29 bits;
+// subnormal ones m 2^-149 are normalised by the leading-zero count of m.
+SF_HD uint64_t f32_to_f64(uint32_t fb) {
+  const uint32_t e = fb >> 23;
+  const uint64_t m = fb & 0x7FFFFFu;
+  const uint64_t normal = ((uint64_t)(e + 896u) << 52) | (m << 29);
+  const uint64_t inf = 0x7FF0000000000000ULL | (m << 29);
+  // subnormal: leading one of m at bit 22 - (lz - 41) with lz = clz64(m)
+  const int lz = clz64(m | 1ULL);
+  const int sh = lz - 40;                                  // moves the leading one to bit 23
+  const uint64_t sub = ((uint64_t)(897 - sh) << 52) | (((m << sh) & 0x7FFFFFULL) << 29);
+  return (e == 255u) ? inf : (e != 0u ? normal : (m != 0 ? sub : 0ULL));
+}
+
 }  // namespace ssa_sf
 
 #endif  // SSA_SOFTFLOAT_CUH_

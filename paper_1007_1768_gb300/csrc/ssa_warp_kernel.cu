@@ -10,8 +10,8 @@
 //     previous step's values);
 //   prefix_j = inner_j for lane 0, v_{l-1} + inner_j otherwise, with
 //     inner_j the running sum inside the chunk up to j; a0 = v_31.
-// Selection: each lane finds its first reaction with prefix_j > r2 a0; a
-// ballot picks the lowest such lane (the first j overall).  After an event,
+// Selection: each lane finds its first reaction with a_j > 0 and
+// prefix_j > r2 a0; a ballot picks the lowest such lane (the first j overall).  After an event,
 // every lane reads its bits of the fired reaction's dependency mask (a
 // per-reaction, per-lane table in shared memory) and recomputes only those
 // propensities.  The state x lives in shared memory (S counts per warp); the
@@ -28,9 +28,14 @@ namespace {
 constexpr int kWarpFlagTruncated = 1;  // per-trajectory flag bits
 constexpr int kWarpFlagOverflow = 2;
 
+// Exact binary32 -> binary64 widening of a non-negative value on the integer pipe.
+__device__ __forceinline__ double widen(float f) {
+  return __longlong_as_double((long long)ssa_sf::f32_to_f64(__float_as_uint(f)));
+}
+
 // Shared-memory layout of the warp kernel (bytes).
 struct WarpSmem {
-  size_t log_inv, log_lnf, cbits, rinfo, nu_ptr, nu_idx, nu_val, x0, depw, x, total;
+  size_t log_inv, log_lnf, cbits, c32, rinfo, nu_ptr, nu_idx, nu_val, x0, depw, x, total;
 };
 
 __host__ __device__ inline WarpSmem warp_smem_layout(int M, int S, int nnz, int warps) {
@@ -39,6 +44,7 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int M, int S, int nnz, int 
   L.log_inv = o; o += kLogCells * 8;
   L.log_lnf = o; o += kLogCells * 8;
   L.cbits = o; o += align_up((size_t)M * 8, 16);
+  L.c32 = o; o += align_up((size_t)M * 4, 16);
   L.rinfo = o; o += align_up((size_t)M * 4, 16);
   L.nu_ptr = o; o += align_up((size_t)(M + 1) * 4, 16);
   L.nu_idx = o; o += align_up((size_t)nnz * 4, 16);
@@ -51,8 +57,9 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int M, int S, int nnz, int 
 }
 
 // MAXCH bounds the chunk ceil(M / 32) (registers only; the chunk itself is
-// the runtime value, as the schedule defines it).
-template <int MAXCH>
+// the runtime value, as the schedule defines it).  F32 selects the
+// FP32-propensity mode.
+template <int MAXCH, bool F32>
 __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long blk[4];
@@ -63,6 +70,7 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a) {
   uint64_t* s_inv = reinterpret_cast<uint64_t*>(smem + L.log_inv);
   uint64_t* s_lnf = reinterpret_cast<uint64_t*>(smem + L.log_lnf);
   unsigned long long* s_cbits = reinterpret_cast<unsigned long long*>(smem + L.cbits);
+  float* s_c32 = reinterpret_cast<float*>(smem + L.c32);
   int32_t* s_rinfo = reinterpret_cast<int32_t*>(smem + L.rinfo);
   int32_t* s_nuptr = reinterpret_cast<int32_t*>(smem + L.nu_ptr);
   int32_t* s_nuidx = reinterpret_cast<int32_t*>(smem + L.nu_idx);
@@ -77,6 +85,7 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a) {
   }
   for (int j = tid; j < M; j += T) {
     s_cbits[j] = (unsigned long long)obits(a.m.c[j]);
+    s_c32[j] = __double2float_rn(a.m.c[j]);
     s_rinfo[j] = a.m.rinfo[j];
   }
   for (int j = tid; j <= M; j += T) s_nuptr[j] = a.m.nu_ptr[j];
@@ -116,9 +125,13 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a) {
       maxx = max(maxx, s_x0[s]);
     }
     __syncwarp();
-    double av[MAXCH];
+    double av[MAXCH];  // FP64 mode: a_j
+    float af[MAXCH];   // FP32 mode: a_j in binary32
 #pragma unroll
-    for (int q = 0; q < MAXCH; ++q) av[q] = 0.0;
+    for (int q = 0; q < MAXCH; ++q) {
+      av[q] = 0.0;
+      af[q] = 0.0f;
+    }
     uint32_t dirty = (1u << mine) - 1u;
     double t = 0.0;
     uint32_t n = 0;
@@ -142,24 +155,55 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a) {
           const long long bi = xa * ((kind == kBi) ? xb : (xa - 1));
           const long long h =
               (kind == kOrder0) ? 1LL : ((kind == kUni) ? xa : ((kind == kBi) ? bi : (bi >> 1)));
-          av[q] = __longlong_as_double((long long)propensity_fp64(s_cbits[j], h));
+          if constexpr (F32)
+            af[q] = __fmul_rn(s_c32[j], __ll2float_rn(h));
+          else
+            av[q] = __longlong_as_double((long long)propensity_fp64(s_cbits[j], h));
         }
       }
       // schedule W32: running sums inside the chunk, Kogge-Stone scan of the
-      // chunk sums, prefixes excl + inner
-      double run[MAXCH];
+      // chunk sums, prefixes excl + inner.  A past-the-end a_j is +0 and
+      // x + (+0) = x, so the last running sum is the chunk sum (+0 for an
+      // empty lane).
+      double run[MAXCH];   // FP64 mode: running sums
+      float run32[MAXCH];  // FP32 mode: binary32 running sums
+      double a0, excl = 0.0, sel_total;
+      float excl32 = 0.0f;
+      if constexpr (F32) {
+        // binary32 selection sums
 #pragma unroll
-      for (int q = 0; q < MAXCH; ++q) run[q] = (q == 0) ? av[0] : __dadd_rn(run[q - 1], av[q]);
-      // av[q] = +0 past the lane's own reactions, and x + (+0) = x, so the
-      // last running sum is the chunk sum (+0 for an empty lane)
-      double v = run[MAXCH - 1];
+        for (int q = 0; q < MAXCH; ++q) run32[q] = (q == 0) ? af[0] : __fadd_rn(run32[q - 1], af[q]);
+        float v32 = run32[MAXCH - 1];
 #pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const double u = __shfl_up_sync(kFullMask, v, off);
-        if (lane >= off) v = __dadd_rn(v, u);
+        for (int off = 1; off < 32; off <<= 1) {
+          const float u = __shfl_up_sync(kFullMask, v32, off);
+          if (lane >= off) v32 = __fadd_rn(v32, u);
+        }
+        excl32 = __shfl_up_sync(kFullMask, v32, 1);
+        sel_total = widen(__shfl_sync(kFullMask, v32, 31));
+        // a0: FP64 sum of the widened a_j in the same schedule, formed anew each event
+        double r64 = widen(af[0]);
+#pragma unroll
+        for (int q = 1; q < MAXCH; ++q) r64 = __dadd_rn(r64, widen(af[q]));
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const double u = __shfl_up_sync(kFullMask, r64, off);
+          if (lane >= off) r64 = __dadd_rn(r64, u);
+        }
+        a0 = __shfl_sync(kFullMask, r64, 31);
+      } else {
+#pragma unroll
+        for (int q = 0; q < MAXCH; ++q) run[q] = (q == 0) ? av[0] : __dadd_rn(run[q - 1], av[q]);
+        double v = run[MAXCH - 1];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const double u = __shfl_up_sync(kFullMask, v, off);
+          if (lane >= off) v = __dadd_rn(v, u);
+        }
+        excl = __shfl_up_sync(kFullMask, v, 1);
+        a0 = __shfl_sync(kFullMask, v, 31);
+        sel_total = a0;
       }
-      const double excl = __shfl_up_sync(kFullMask, v, 1);
-      const double a0 = __shfl_sync(kFullMask, v, 31);
       // random numbers of event n: 32 consecutive events drawn at once, one per lane
       if (!filled || n >= base + 32u) {
         base = n;
@@ -175,14 +219,25 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a) {
       const long long tb = obits(t_next);
       if (tb > t_end_bits) break;
       k = grid_index(a, tb, k);
-      // selection: first j with prefix_j > r2 a0
-      const long long gb = obits(__dmul_rn(__longlong_as_double((long long)Ub), a0));
+      // selection: first j with a_j > 0 and prefix_j > r2 * total (FP64
+      // product; FP32 mode compares the widened binary32 prefixes).  The
+      // a_j > 0 test matters at lane boundaries, where the scan's exclusive
+      // value can exceed the previous lane's last prefix by rounding.
+      const long long gb = obits(__dmul_rn(__longlong_as_double((long long)Ub), sel_total));
       int myfirst = -1;
 #pragma unroll
       for (int q = MAXCH - 1; q >= 0; --q) {
         if (q < mine) {
-          const double pre = (lane == 0) ? run[q] : __dadd_rn(excl, run[q]);
-          if (obits(pre) > gb) myfirst = my0 + q;
+          long long pb;
+          bool pos;
+          if constexpr (F32) {
+            pb = obits(widen((lane == 0) ? run32[q] : __fadd_rn(excl32, run32[q])));
+            pos = __float_as_uint(af[q]) != 0u;
+          } else {
+            pb = obits((lane == 0) ? run[q] : __dadd_rn(excl, run[q]));
+            pos = obits(av[q]) > 0;
+          }
+          if (pos && pb > gb) myfirst = my0 + q;
         }
       }
       const unsigned hit = __ballot_sync(kFullMask, myfirst >= 0);
@@ -193,7 +248,8 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a) {
         int mylast = -1;
 #pragma unroll
         for (int q = 0; q < MAXCH; ++q) {
-          if (q < mine && obits(av[q]) > 0) mylast = my0 + q;
+          const bool pos = F32 ? (__float_as_uint(af[q]) != 0u) : (obits(av[q]) > 0);
+          if (q < mine && pos) mylast = my0 + q;
         }
         const unsigned pos = __ballot_sync(kFullMask, mylast >= 0);
         jsel = __shfl_sync(kFullMask, mylast, 31 - __clz(pos));
@@ -261,17 +317,42 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a) {
   }
 }
 
-template <int MAXCH>
+template <int MAXCH, bool F32>
 cudaError_t launch_ch(const RunArgs& a, int blocks, int threads, size_t smem, cudaStream_t st) {
-  k_ssa_warp<MAXCH><<<blocks, threads, smem, st>>>(a);
+  k_ssa_warp<MAXCH, F32><<<blocks, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-template <int MAXCH>
+template <int MAXCH, bool F32>
 cudaError_t prepare_ch(size_t smem, int threads, int* per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_ssa_warp<MAXCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_ssa_warp<MAXCH, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_ssa_warp<MAXCH>, threads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_ssa_warp<MAXCH, F32>, threads, smem);
+}
+
+template <bool F32>
+cudaError_t prepare_prec(int M, size_t smem, int threads, int* per_sm) {
+  switch (warp_max_chunk(M)) {
+    case 1: return prepare_ch<1, F32>(smem, threads, per_sm);
+    case 2: return prepare_ch<2, F32>(smem, threads, per_sm);
+    case 4: return prepare_ch<4, F32>(smem, threads, per_sm);
+    case 8: return prepare_ch<8, F32>(smem, threads, per_sm);
+    case 16: return prepare_ch<16, F32>(smem, threads, per_sm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <bool F32>
+cudaError_t launch_prec(const RunArgs& a, int blocks, int threads, size_t smem, cudaStream_t stream) {
+  switch (warp_max_chunk(a.m.M)) {
+    case 1: return launch_ch<1, F32>(a, blocks, threads, smem, stream);
+    case 2: return launch_ch<2, F32>(a, blocks, threads, smem, stream);
+    case 4: return launch_ch<4, F32>(a, blocks, threads, smem, stream);
+    case 8: return launch_ch<8, F32>(a, blocks, threads, smem, stream);
+    case 16: return launch_ch<16, F32>(a, blocks, threads, smem, stream);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -285,26 +366,15 @@ size_t warp_kernel_smem(int M, int S, int nnz, int threads) {
   return warp_smem_layout(M, S, nnz, threads / 32).total;
 }
 
-cudaError_t warp_kernel_prepare(int M, size_t smem, int threads, int* blocks_per_sm) {
-  switch (warp_max_chunk(M)) {
-    case 1: return prepare_ch<1>(smem, threads, blocks_per_sm);
-    case 2: return prepare_ch<2>(smem, threads, blocks_per_sm);
-    case 4: return prepare_ch<4>(smem, threads, blocks_per_sm);
-    case 8: return prepare_ch<8>(smem, threads, blocks_per_sm);
-    case 16: return prepare_ch<16>(smem, threads, blocks_per_sm);
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t warp_kernel_prepare(int M, bool fp32, size_t smem, int threads, int* blocks_per_sm) {
+  return fp32 ? prepare_prec<true>(M, smem, threads, blocks_per_sm)
+              : prepare_prec<false>(M, smem, threads, blocks_per_sm);
 }
 
-cudaError_t launch_warp_kernel(const RunArgs& a, int blocks, int threads, size_t smem, cudaStream_t stream) {
-  switch (warp_max_chunk(a.m.M)) {
-    case 1: return launch_ch<1>(a, blocks, threads, smem, stream);
-    case 2: return launch_ch<2>(a, blocks, threads, smem, stream);
-    case 4: return launch_ch<4>(a, blocks, threads, smem, stream);
-    case 8: return launch_ch<8>(a, blocks, threads, smem, stream);
-    case 16: return launch_ch<16>(a, blocks, threads, smem, stream);
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t launch_warp_kernel(const RunArgs& a, bool fp32, int blocks, int threads, size_t smem,
+                               cudaStream_t stream) {
+  return fp32 ? launch_prec<true>(a, blocks, threads, smem, stream)
+              : launch_prec<false>(a, blocks, threads, smem, stream);
 }
 
 }  // namespace ssa_impl

@@ -75,9 +75,22 @@ int main(int argc, char** argv) {
     const uint64_t sg = ssa_sf::scale_down(sx, 53, ok);
     if (!ok || sg != bits(dbl(sx) * 0x1p-53)) ++bad_scale;
   }
+  // widening binary32 -> binary64: every non-negative finite value and +inf
+  long bad_widen = 0, widened = 0;
+  for (uint64_t fb = 0; fb <= 0x7F800000ULL; ++fb) {
+    float f;
+    const uint32_t fb32 = (uint32_t)fb;
+    std::memcpy(&f, &fb32, 4);
+    if (ssa_sf::f32_to_f64(fb32) != bits((double)f)) {
+      ++bad_widen;
+      if (bad_widen < 5) printf("WIDEN %08x\n", fb32);
+    }
+    ++widened;
+  }
+  printf("widen %ld %ld 0\n", widened, bad_widen);
   printf("mul %ld %ld %ld\n", cases, bad_mul, fb_mul);
   printf("div %ld %ld %ld\n", cases, bad_div, fb_div);
   printf("cvt %ld %ld 0\n", cases, bad_cvt);
   printf("scale %ld %ld 0\n", cases, bad_scale);
-  return (bad_mul || bad_div || bad_cvt || bad_scale) ? 1 : 0;
+  return (bad_mul || bad_div || bad_cvt || bad_scale || bad_widen) ? 1 : 0;
 }

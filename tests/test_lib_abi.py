@@ -141,3 +141,17 @@ def test_schedule_limits_are_refused_before_touching_the_gpu():
             ssa.ensemble_run(huge, 10, 1.0, 11, seed=1, schedule=sched)
         assert e.value.status == binding.SSA_EUNSUPPORTED and "512" in str(e.value)
     huge.close()
+
+
+def test_fp32_mode_limits_are_refused_before_touching_the_gpu():
+    net_R, net_P = [[0], [1]], [[1], [0]]
+    model = ssa.Model(net_R, net_P, [10.0, 0.1], [0])
+    with pytest.raises(ssa.SSAError) as e:
+        ssa.ensemble_run(model, 10, 1.0, 11, seed=1, precision="fp32", schedule="thread")
+    assert e.value.status == binding.SSA_EUNSUPPORTED and "warp schedule" in str(e.value)
+    model.close()
+    model = ssa.Model(net_R, net_P, [1e39, 0.1], [0])
+    with pytest.raises(ssa.SSAError) as e:
+        ssa.ensemble_run(model, 10, 1.0, 11, seed=1, precision="fp32")
+    assert e.value.status == binding.SSA_EINVAL and "binary32" in str(e.value)
+    model.close()
