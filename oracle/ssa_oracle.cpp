@@ -44,15 +44,18 @@
 //   * the selection prefix sums are binary32 sums of these a_j in the
 //     run's schedule (L or W32), with total A32 (the last prefix or the
 //     scan's lane-31 value);
-//   * a0 is an FP64 sum of the (exactly widened) binary32 a_j in the same
-//     schedule, formed again at every event (no incremental drift), and
-//     t_next = t + (-ln r1) / a0 in FP64;
+//   * a0 in FP64, formed again at every event (no incremental drift): under
+//     W32 each lane's chunk is summed left to right in binary32 with
+//     error compensation (compensated_sum), widened to FP64, and the 32
+//     lane values are combined by the W32 Kogge-Stone scan in FP64; under L
+//     the whole list is one compensated sum; t_next = t + (-ln r1) / a0;
 //   * selection: smallest j with a_j > 0 and (double)prefix_j > r2 *
 //     (double)A32 (FP64 product); if none, the last j with a_j > 0.
 // When every product and sum is exact in binary32, this mode reproduces the
 // FP64 mode's trajectories bit for bit.
 //
 // Build: g++ -O2 -ffp-contract=off (no FMA contraction), no -ffast-math.
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <limits>
@@ -204,6 +207,37 @@ void w32_prefix(const std::vector<T>& a, int M, std::vector<T>& prefix, T* a0) {
   *a0 = scan[31];
 }
 
+// Inclusive Kogge-Stone scan of 32 lane values (offsets 1, 2, 4, 8, 16,
+// every lane reading the previous step's values); total = lane 31's value.
+void w32_lanes(const std::vector<double>& v, std::vector<double>& scan, double* total) {
+  for (int l = 0; l < 32; ++l) scan[l] = v[l];
+  for (int off = 1; off < 32; off <<= 1) {
+    double prev[32];
+    for (int l = 0; l < 32; ++l) prev[l] = scan[l];
+    for (int l = off; l < 32; ++l) scan[l] = prev[l] + prev[l - off];
+  }
+  *total = scan[31];
+}
+
+// FP32 mode: a0's share of a[b..e) (binary32 values), summed left to right
+// with error compensation in binary32 -- the cascaded TwoSum of Ogita, Rump
+// and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 26(6),
+// 2005, Algorithm Sum2): s_j = s_{j-1} + a_j rounded, its exact rounding
+// error by Knuth's TwoSum, the errors added up in binary32 -- and the two
+// parts widened exactly and added once in FP64.
+double compensated_sum(const std::vector<float>& a, int b, int e) {
+  float s = a[b], err = 0.0f;
+  for (int j = b + 1; j < e; ++j) {
+    const float x = a[j];
+    const float t = s + x;
+    const float bp = t - s;
+    const float d = (s - (t - bp)) + (x - bp);  // TwoSum: s + x = t + d exactly
+    err = err + d;
+    s = t;
+  }
+  return (double)s + (double)err;
+}
+
 // Selection (Sec. 2: one of the possible transitions is chosen): the
 // smallest j with a_j > 0 and prefix_j > target; if rounding leaves none,
 // the last j with a_j > 0.  A transition whose propensity is zero is not
@@ -244,7 +278,7 @@ TrajResult run_one(const Model& m, uint64_t traj_id, double t_end, int G, const 
   TrajResult res;
   std::vector<int64_t> x(m.S);
   for (int s = 0; s < m.S; ++s) { x[s] = m.x0[s]; if (x[s] > res.max_x) res.max_x = x[s]; }
-  std::vector<double> a(m.M), prefix(m.M), a_wide(m.M), scratch(m.M);
+  std::vector<double> a(m.M), prefix(m.M), a_wide(m.M);
   std::vector<float> a32(m.M), prefix32(m.M);
   const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   uint32_t words[4] = {0, 0, 0, 0};
@@ -286,11 +320,19 @@ TrajResult run_one(const Model& m, uint64_t traj_id, double t_end, int G, const 
         for (int j = 0; j < m.M; ++j) {
           a0_32 = (j == 0) ? a32[0] : a0_32 + a32[j];
           prefix32[j] = a0_32;
-          a0 = (j == 0) ? a_wide[0] : a0 + a_wide[j];
         }
+        a0 = compensated_sum(a32, 0, m.M);
       } else {
         w32_prefix(a32, m.M, prefix32, &a0_32);
-        w32_prefix(a_wide, m.M, scratch, &a0);
+        // lane l's chunk summed with compensation, then the lanes' FP64 values
+        // in the W32 scan order
+        const int chunk = (m.M + 31) / 32;
+        std::vector<double> lane_sum(32, 0.0), lane_scan(32);
+        for (int l = 0; l < 32; ++l) {
+          const int b = l * chunk, e = std::min(m.M, b + chunk);
+          lane_sum[l] = (b < e) ? compensated_sum(a32, b, e) : 0.0;
+        }
+        w32_lanes(lane_sum, lane_scan, &a0);
       }
       for (int j = 0; j < m.M; ++j) prefix[j] = (double)prefix32[j];
     }

@@ -8,7 +8,8 @@ outside the oracle:
     in both summation schedules;
   * hand-built cases whose binary32 and FP64 results differ, checked against
     numpy's IEEE binary32 / binary64 arithmetic: the first event time uses
-    the FP64 sum of the widened binary32 propensities, and each propensity is
+    a0 formed in FP64 from error-compensated binary32 chunk sums (so rounding
+    losses of the binary32 sums do not reach a0), and each propensity is
     (float)c * (float)h rounded in binary32;
   * the closed forms of the birth-death and isomerisation processes.
 """
@@ -78,6 +79,32 @@ def test_time_step_uses_the_fp64_sum_of_the_binary32_propensities():
             assert t == E / (2.0 ** 24 + 1.0)
             assert t != E / 2.0 ** 24
             assert j == 0  # reaction 1 is absorbed by the binary32 total's rounding
+
+
+def test_a0_sums_each_lane_chunk_with_compensation():
+    # 64 reactions (two per lane); reactions 0 and 1 share lane 0 with
+    # a = (2^24, 1): the binary32 running sum rounds to 2^24, its TwoSum error
+    # is 1, so a0 = 2^24 + 1 under W32; under L the whole list is one
+    # compensated sum and gives the same.  Zero rates elsewhere.
+    M = 64
+    R = np.zeros((M, 1), np.int32)
+    P = np.zeros((M, 1), np.int32)
+    rates = np.zeros(M)
+    rates[0], rates[1] = 2.0 ** 24, 1.0
+    net = W.Network("chunk_pair", ["X"], R, P, rates, np.array([0], np.int32))
+    for schedule in SCHEDULES:
+        for seed in (7, 8):
+            t, j, E = _first_event(net, seed, schedule=schedule)
+            assert t == E / (2.0 ** 24 + 1.0), schedule
+            assert j == 0
+    # three values whose binary32 sum loses 2^-24 twice over: the compensated
+    # FP64 value keeps both
+    rates = np.zeros(M)
+    rates[0], rates[1], rates[2] = 1.0, 2.0 ** -24, 2.0 ** -24
+    assert np.float32(np.float32(1.0) + np.float32(2.0 ** -24)) == np.float32(1.0)
+    net = W.Network("chunk_small", ["X"], R, P, rates, np.array([0], np.int32))
+    t, _, E = _first_event(net, 9, schedule=oracle.SCHEDULE_L)
+    assert t == E / (1.0 + 2.0 ** -23)
 
 
 def test_propensity_is_a_binary32_product_of_rounded_factors():
