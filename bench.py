@@ -53,6 +53,9 @@ WORKLOADS = {
     "random": {"factory": "workload_random", "name": "random_S32_M128_G1001_T10_netseed3", "n_traj": 262144,
                "steps": 10, "e2e_steps": 3, "cpu_sample": 2048, "ref_sample": 512,
                "kernel": "k_ssa_warp", "dram_bytes": None},
+    "batch": {"factory": None, "name": "batch256_S4-64_M8-512_N1024-65536_G501_T10_fp32", "n_traj": None,
+              "steps": 2, "e2e_steps": 1, "cpu_sample": 64, "ref_sample": 16,
+              "kernel": "k_ssa_batch", "dram_bytes": None},
 }
 FP64_OPS_PER_SM_CLK = 2.0  # 1.25 TFLOP/s dense FP64 (FMA = 2 flops) / (152 SMs * 2.07 GHz)
 
@@ -76,6 +79,8 @@ def parse_args():
                         "per warp); the line then adds the FP64 kernel's rate on the same GPU and the "
                         "FP32-vs-FP64 standard-error report")
     p.add_argument("--e2e-steps", type=int, default=None)
+    p.add_argument("--batch-div", type=int, default=1,
+                   help="batch workload: divide every network's trajectory count by this")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--profile-small", action="store_true",
                    help="one small step for an ncu capture (--profile-n trajectories); prints no bench line")
@@ -89,6 +94,8 @@ def parse_args():
     spec = WORKLOADS[args.workload]
     args.steps = spec["steps"] if args.steps is None else args.steps
     args.n_traj = spec["n_traj"] if args.n_traj is None else args.n_traj
+    if args.workload == "batch" and args.impl == "reference":
+        p.error("--impl reference times single-network workloads")
     args.e2e_steps = spec["e2e_steps"] if args.e2e_steps is None else args.e2e_steps
     return args
 
@@ -318,11 +325,12 @@ def run_ours(args):
         grid_h = (np.arange(G, dtype=np.float64) * w.t_end) / (G - 1)
         e_ev = 0
         for i in range(2):
-            ssa.ensemble_run(model, n, w.t_end, G, 1 + i, grid=grid_h, want_sums=False, traj_offset=rank * n)
+            ssa.ensemble_run(model, n, w.t_end, G, 1 + i, grid=grid_h, want_sums=False, traj_offset=rank * n,
+                             precision=args.precision)
         t0 = time.perf_counter()
         for i in range(args.e2e_steps):
             r = ssa.ensemble_run(model, n, w.t_end, G, 5000 + i, grid=grid_h, want_sums=False,
-                                 traj_offset=rank * n)
+                                 traj_offset=rank * n, precision=args.precision)
             e_ev += r.events
         e_dt = time.perf_counter() - t0
         e2e = {"value": e_ev / e_dt, "unit": UNIT, "h2d_bytes_per_step": int(grid_h.nbytes),
@@ -331,7 +339,7 @@ def run_ours(args):
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+            "dtype": "f64" if args.precision == "fp64" else "f32-propensities/f64-time", "data": "synthetic",
             "config": {"workload": spec["name"], "n_traj_per_gpu": n, "n_grid": G,
                        "t_end": w.t_end,
                        "precision": "fp64-exact" if args.precision == "fp64" else "fp32-propensities",
@@ -418,6 +426,157 @@ def compare_with_fp64(args, ssa, torch, model, w, n, run_step, totals, stream, f
     return same_gpu, report
 
 
+def run_batch(args):
+    """The uneven batch of 256 random networks in one graph replay per step
+    (FP32 propensities, FP64 time): persistent kernels per register bucket,
+    launch shape from the autotuner."""
+    import numpy as np
+    import torch
+
+    import paper_1007_1768_gb300 as ssa
+    import workloads as W
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    spec = WORKLOADS["batch"]
+    ws = W.batch_networks(traj_div=args.batch_div)
+    models = [ssa.Model.from_network(w.net) for w in ws]
+    n_traj = [w.n_traj for w in ws]
+    t_end = [w.t_end for w in ws]
+    n_grid = [w.n_grid for w in ws]
+    stream = torch.cuda.current_stream(dev)
+    batch = ssa.Batch(models, n_traj, t_end, n_grid, device=dev, precision="fp32", max_events=1000000,
+                      traj_offset=rank * 10 ** 9)
+    threads, split, tune_ms = batch.tune()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for i in range(args.warmup):
+        batch.launch(1 + i, stats=False)
+    torch.cuda.synchronize()
+    K = args.steps
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    events = 0
+    ops = 0.0
+    Ms = np.array([w.net.n_reactions for w in ws], dtype=np.float64)
+    for i in range(K):
+        flush.fill_(i & 0xFF)
+        ev_s[i].record(stream)
+        _, st = batch.launch(1000 + i, stats=True)
+        ev_e[i].record(stream)
+        events += st.events
+        per = np.array([batch.network_stats(b).events for b in range(len(ws))], dtype=np.float64)
+        ops += float((per * (Ms + 2.0)).sum())
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [ev_s[i].elapsed_time(ev_e[i]) for i in range(K)]
+    total_ms = sum(step_ms)
+    if pg:
+        t = torch.tensor([total_ms, float(events)], dtype=torch.float64)
+        mx = t.clone()
+        pg.all_reduce(mx, op=pg.ReduceOp.MAX)
+        sm = t.clone()
+        pg.all_reduce(sm, op=pg.ReduceOp.SUM)
+        total_ms, events_all = float(mx[0]), float(sm[1])
+    else:
+        events_all = float(events)
+    value = events_all / (total_ms * 1e-3)
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    peak = FP64_OPS_PER_SM_CLK * SMS_GB300 * sm_mhz * 1e6 * 1e-9
+    achieved = ops / (total_ms * 1e-3) * 1e-9
+    if rank == 0:
+        # end to end: one-shot host call (model tables, graph, launch, copies back)
+        host_means = [np.empty((g, m.n_species)) for g, m in zip(n_grid, models)]
+        host_vars = [np.empty((g, m.n_species)) for g, m in zip(n_grid, models)]
+        t0 = time.perf_counter()
+        e_events = 0
+        for i in range(args.e2e_steps):
+            hb = ssa.Batch(models, n_traj, t_end, n_grid, precision="fp32", max_events=1000000,
+                           block_threads=threads)
+            outs, st = hb.launch(7000 + i, stats=True)
+            e_events += st.events
+            hb.close()
+        e_dt = time.perf_counter() - t0
+        d2h = int(sum(2 * g * m.n_species * 8 for g, m in zip(n_grid, models)))
+        # descriptors, finalisation entries and work offsets the one-shot call copies in
+        h2d = int(len(ws) * (136 + 72 + 4 + 16) + 4 + 16)
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_baseline_batch(ws, spec["cpu_sample"])
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32-propensities/f64-time", "data": "synthetic",
+            "config": {"workload": spec["name"], "networks": len(ws), "n_traj_total": int(sum(n_traj)),
+                       "traj_div": args.batch_div, "n_grid": 501, "t_end": 10.0, "precision": "fp32-propensities",
+                       "launch": {"block_threads": threads, "split_by_bucket": split, "tune_sample_ms": tune_ms},
+                       "l2": "flushed between timed steps (256 MiB write outside the step events)",
+                       "parallelism": f"replicas x{world} (trajectory-id shards)"},
+            "traj_per_s": world * sum(n_traj) / (total_ms * 1e-3 / K),
+            "events_per_step": events_all / K,
+            "roofline": {"bound": "alu", "kernel": spec["kernel"], "achieved": achieved, "peak": peak,
+                         "unit": "GFLOP/s (FP64 ops)", "frac": achieved / peak, "traffic": None,
+                         "ops_per_event": "M_b + 2 (FP64 re-summation of a0, r2 * A32, quotient, t add)",
+                         "peak_basis": "2 FP64 ops/clk/SM x 152 SMs x median SM clock"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e_events / e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": args.e2e_steps, "note": "one-shot batches from host: create, tune-free launch, copy"},
+            "gpu_launches": K * (2 + n_groups(ws, split)),
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    batch.close()
+    for m in models:
+        m.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def n_groups(ws, split: bool) -> int:
+    """Simulation kernels per batch replay: one per register bucket (the
+    warp layout's chunk ceil(M / 32) rounded up to 1, 2, 4, 8, 16) when split."""
+    if not split:
+        return 1
+    buckets = set()
+    for w in ws:
+        ch = (w.net.n_reactions + 31) // 32
+        buckets.add(next(b for b in (1, 2, 4, 8, 16) if b >= ch))
+    return len(buckets)
+
+
+def cpu_baseline_batch(ws, per_network: int):
+    """The oracle on all host cores over the first `per_network` trajectories
+    of every network of the batch (FP32 propensities, W32)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    cores = os.cpu_count() or 1
+
+    def one(w):
+        r = oracle.run(w.net, min(per_network, w.n_traj), w.t_end, w.n_grid, w.seed, max_events=1000000,
+                       schedule=oracle.SCHEDULE_W32, precision=oracle.PRECISION_FP32)
+        return r.events
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        ev = sum(ex.map(one, ws))
+    dt = time.perf_counter() - t0
+    return {"value": ev / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {per_network} trajectories of each of the {len(ws)} networks, {ev} events in "
+                      f"{dt:.2f} s on {cores} threads"}
+
+
 def run_scan():
     """Kernel time per trajectory count for the HIV-shaped model; for counts
     up to 65,536 also the longest trajectory's events, whose serial chain sets
@@ -459,6 +618,8 @@ def main():
         return run_probe(args.probe)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

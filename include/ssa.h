@@ -55,11 +55,13 @@ typedef enum ssa_status {
  *   SSA_PREC_FP64: a_j = c_j * (double)h_j; a0 and the selection prefix sums
  *     are FP64 sums in the schedule's order.
  *   SSA_PREC_FP32: a_j = (float)c_j * (float)h_j in binary32; the selection
- *     prefix sums are binary32 sums (schedule W32) with total A32; a0 is the
- *     FP64 sum (schedule W32) of the exactly widened a_j, formed anew at
- *     every event; tau = -ln(r1) / a0 and t in FP64; the reaction is the
- *     first j with a_j > 0 and (double)prefix_j > r2 * (double)A32.  Runs
- *     one trajectory per warp; rates must lie in the binary32 range. */
+ *     prefix sums are binary32 sums (schedule W32) with total A32; a0 is
+ *     formed anew at every event in FP64: each lane's chunk is summed in
+ *     binary32 with its rounding errors carried (cascaded TwoSum), the two
+ *     parts widened and added in FP64, and the 32 lane values combined by
+ *     the W32 scan in FP64; tau = -ln(r1) / a0 and t in FP64; the reaction
+ *     is the first j with a_j > 0 and (double)prefix_j > r2 * (double)A32.
+ *     Runs one trajectory per warp; rates must lie in the binary32 range. */
 enum { SSA_PREC_FP64 = 0, SSA_PREC_FP32 = 1 };
 /* Kernel shape and summation order:
  *   SSA_SCHED_THREAD: one trajectory per thread, sums left to right
@@ -234,6 +236,88 @@ ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n_traj, doub
                                     const double* grid, uint64_t seed, const ssa_run_opts* opts,
                                     double* mean, double* var, int64_t* sum1, int64_t* sum2,
                                     ssa_run_stats* stats);
+
+/* ------------------------------------------------------------------ batches
+ * Many networks of uneven size and trajectory count -- the parametric copies
+ * and sweeps of Sec. 3.2 (StochRxn_ff) -- run together: one persistent
+ * kernel per register bucket of the warp layout, on parallel branches of one
+ * CUDA graph that also zeroes the sums and finalises every network.  The
+ * graph is captured at the first launch and replayed for every seed.
+ *
+ * Network b runs n_traj[b] trajectories with ids opts->traj_offset + i and
+ * Philox stream id (fourth counter word) opts->stream_id + b, one trajectory
+ * per warp (schedule W32) in opts->precision.  Its results are bit-identical
+ * to ssa_ensemble_run of that network alone with schedule SSA_SCHED_WARP and
+ * stream_id = opts->stream_id + b; they do not depend on the launch shape.
+ */
+typedef struct ssa_batch ssa_batch; /* opaque, owned by the library */
+
+/*
+ * Creates a batch of n_models >= 1 networks.  Per network b (host arrays):
+ *   models[b]: a model with at most 512 reactions (the batch keeps a
+ *     reference: models must outlive the batch);
+ *   n_traj[b] >= 1; t_end[b] > 0 and finite; n_grid[b] >= 1;
+ *   grids: NULL (every grid uniform, g_k = k t_end / (n_grid - 1)) or an
+ *     array of n_models host pointers, each NULL (uniform) or n_grid[b]
+ *     ascending values in [0, t_end[b]] (copied).
+ * opts (NULL for defaults): precision, max_events, traj_offset, stream_id
+ * (stream_id + n_models <= 2^32), cuda_stream (where launches run), memory
+ * (where ssa_batch_launch's output buffers live), block_threads (0 = 128
+ * until ssa_batch_tune picks; else 64, 128 or 256).  schedule must be AUTO or
+ * WARP.  Allocates one device slab for every network's grid, tables,
+ * difference sums and results; synchronous.
+ * Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA, SSA_EUNSUPPORTED.
+ */
+ssa_status ssa_batch_create(int32_t n_models, const ssa_model* const* models, const int64_t* n_traj,
+                            const double* t_end, const int32_t* n_grid, const double* const* grids,
+                            const ssa_run_opts* opts, ssa_batch** out);
+
+/*
+ * Autotuner: times every launch shape (block size 64, 128 or 256; one kernel
+ * per register bucket or one kernel for all) on a sample of the batch (the
+ * first ceil(n_traj[b] / 8) trajectories of every network), keeps the
+ * fastest and reports it (each output pointer may be NULL): block_threads,
+ * split (1 = one kernel per bucket), sample_ms (device time of the chosen
+ * shape on the sample).  Results of later launches are unchanged by it.
+ * Synchronous.
+ */
+ssa_status ssa_batch_tune(ssa_batch* batch, int32_t* block_threads, int32_t* split, double* sample_ms);
+
+/*
+ * Runs the batch for `seed` on opts->cuda_stream.  means, vars, sums1, sums2:
+ * NULL, or arrays of n_models pointers (each may be NULL) to G_b x S_b
+ * buffers in opts->memory's space that receive network b's results.  The
+ * results also stay in the batch's own device buffers (ssa_batch_result)
+ * until the next launch.  stats: host struct or NULL (totals over all
+ * networks; kernel_ms is the device time of the whole graph).  The call waits
+ * for the stream when stats is non-NULL or host outputs are requested;
+ * otherwise it only enqueues work.
+ * Errors: SSA_EINVAL, SSA_ECUDA, SSA_EOVERFLOW (only detectable when the call
+ * waits: a count reached SSA_STATE_MAX, or N * max_x^2 could leave int64).
+ */
+ssa_status ssa_batch_launch(ssa_batch* batch, uint64_t seed, double* const* means, double* const* vars,
+                            int64_t* const* sums1, int64_t* const* sums2, ssa_run_stats* stats);
+
+/* Device pointers to network `index`'s results of the last launch (each
+ * output may be NULL); valid until the next launch or ssa_batch_destroy. */
+ssa_status ssa_batch_result(const ssa_batch* batch, int32_t index, const double** mean, const double** var,
+                            const int64_t** sum1, const int64_t** sum2);
+
+/* Totals of network `index` (events, truncated, overflowed, max_x) from the
+ * last launch that waited for the stream; kernel_ms is 0. */
+ssa_status ssa_batch_network_stats(const ssa_batch* batch, int32_t index, ssa_run_stats* out);
+
+/* Releases a batch.  NULL is ignored.  No launch of it may be pending. */
+void ssa_batch_destroy(ssa_batch* batch);
+
+/*
+ * One-shot batch: ssa_batch_create, one ssa_batch_launch with `seed` and the
+ * given means / vars (arrays of n_models pointers, opts->memory's space), a
+ * wait for the stream, and ssa_batch_destroy.
+ */
+ssa_status ssa_batch_run(int32_t n_models, const ssa_model* const* models, const int64_t* n_traj,
+                         const double* t_end, const int32_t* n_grid, const double* const* grids, uint64_t seed,
+                         const ssa_run_opts* opts, double* const* means, double* const* vars);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,8 @@ TRAJ_TRUNCATED, TRAJ_OVERFLOW = 1, 2
 EXPORTS = [
     "ssa_status_string", "ssa_last_error", "ssa_run_opts_init", "ssa_model_create", "ssa_model_destroy",
     "ssa_model_info", "ssa_ensemble_workspace_size", "ssa_ensemble_run", "ssa_ensemble_run_noalloc",
+    "ssa_batch_create", "ssa_batch_tune", "ssa_batch_launch", "ssa_batch_result", "ssa_batch_network_stats",
+    "ssa_batch_destroy", "ssa_batch_run",
 ]
 
 
@@ -90,6 +92,21 @@ def lib():
         L.ssa_ensemble_run.restype = ctypes.c_int
         L.ssa_ensemble_run_noalloc.argtypes = L.ssa_ensemble_run.argtypes
         L.ssa_ensemble_run_noalloc.restype = ctypes.c_int
+        L.ssa_batch_create.argtypes = [i32, vp, vp, vp, vp, vp, ctypes.POINTER(RunOpts), ctypes.POINTER(vp)]
+        L.ssa_batch_create.restype = ctypes.c_int
+        L.ssa_batch_tune.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(f64)]
+        L.ssa_batch_tune.restype = ctypes.c_int
+        L.ssa_batch_launch.argtypes = [vp, u64, vp, vp, vp, vp, ctypes.POINTER(RunStats)]
+        L.ssa_batch_launch.restype = ctypes.c_int
+        L.ssa_batch_result.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                       ctypes.POINTER(vp)]
+        L.ssa_batch_result.restype = ctypes.c_int
+        L.ssa_batch_network_stats.argtypes = [vp, i32, ctypes.POINTER(RunStats)]
+        L.ssa_batch_network_stats.restype = ctypes.c_int
+        L.ssa_batch_destroy.argtypes = [vp]
+        L.ssa_batch_destroy.restype = None
+        L.ssa_batch_run.argtypes = [i32, vp, vp, vp, vp, vp, u64, ctypes.POINTER(RunOpts), vp, vp]
+        L.ssa_batch_run.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -232,3 +249,102 @@ def ensemble_run(model: Model, n_traj: int, t_end: float, n_grid: int, seed: int
                                       None if s2 is None else s2.data_ptr(), ctypes.byref(st) if stats else None))
     return EnsembleResult(mean, var, s1, s2, int(st.events), int(st.truncated), int(st.overflowed), int(st.max_x),
                           float(st.kernel_ms), tev, ths, tfl)
+
+
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        arr[i] = p
+    return arr
+
+
+class Batch:
+    """A batch of networks run together (ssa_batch_create / _tune / _launch).
+
+    ``device=None`` keeps outputs on the host (numpy, synchronous launches); a
+    torch device makes launch() return torch tensors on that device, filled on
+    torch's current stream."""
+
+    def __init__(self, models, n_traj, t_end, n_grid, grids=None, *, device=None, **opt_kw):
+        self.n = len(models)
+        self.models = list(models)  # the batch references the models: keep them alive
+        self.n_traj = np.ascontiguousarray(n_traj, dtype=np.int64)
+        self.t_end = np.ascontiguousarray(t_end, dtype=np.float64)
+        self.n_grid = np.ascontiguousarray(n_grid, dtype=np.int32)
+        if not (self.n_traj.shape == self.t_end.shape == self.n_grid.shape == (self.n,)):
+            raise ValueError("n_traj, t_end and n_grid need one entry per model")
+        self.device = device
+        if device is not None:
+            import torch
+            dev = torch.device(device)
+            self._stream = torch.cuda.current_stream(dev)
+            opt_kw.setdefault("cuda_stream", self._stream.cuda_stream)
+            self.opts = make_opts(memory=MEM_DEVICE, **opt_kw)
+        else:
+            self.opts = make_opts(memory=MEM_HOST, **opt_kw)
+        self._grids = None
+        gp = None
+        if grids is not None:
+            self._grids = [None if g is None else np.ascontiguousarray(g, dtype=np.float64) for g in grids]
+            gp = _ptr_array([None if g is None else g.ctypes.data for g in self._grids])
+        hp = _ptr_array([m.handle.value for m in self.models])
+        h = ctypes.c_void_p()
+        _check(lib().ssa_batch_create(self.n, hp, self.n_traj.ctypes.data, self.t_end.ctypes.data,
+                                      self.n_grid.ctypes.data, gp, ctypes.byref(self.opts), ctypes.byref(h)))
+        self._h = h
+        self.species = [m.n_species for m in self.models]
+
+    def tune(self):
+        """Autotunes the launch shape; returns (block_threads, split, sample_ms)."""
+        t, sp, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _check(lib().ssa_batch_tune(self._h, ctypes.byref(t), ctypes.byref(sp), ctypes.byref(ms)))
+        return int(t.value), bool(sp.value), float(ms.value)
+
+    def launch(self, seed: int, want_sums: bool = False, stats: bool = True):
+        """Runs the batch; returns (list of per-network dicts with mean, var
+        and, if asked, sum1 / sum2; RunStats or None)."""
+        outs = []
+        for b in range(self.n):
+            shape = (int(self.n_grid[b]), self.species[b])
+            if self.device is None:
+                o = {"mean": np.empty(shape), "var": np.empty(shape)}
+                if want_sums:
+                    o["sum1"] = np.empty(shape, dtype=np.int64)
+                    o["sum2"] = np.empty(shape, dtype=np.int64)
+            else:
+                import torch
+                o = {"mean": torch.empty(shape, dtype=torch.float64, device=self.device),
+                     "var": torch.empty(shape, dtype=torch.float64, device=self.device)}
+                if want_sums:
+                    o["sum1"] = torch.empty(shape, dtype=torch.int64, device=self.device)
+                    o["sum2"] = torch.empty(shape, dtype=torch.int64, device=self.device)
+            outs.append(o)
+
+        def ptr(a):
+            return a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr()
+
+        def arr(key):
+            if key not in outs[0]:
+                return None
+            return _ptr_array([ptr(o[key]) for o in outs])
+
+        st = RunStats()
+        _check(lib().ssa_batch_launch(self._h, int(seed), arr("mean"), arr("var"), arr("sum1"), arr("sum2"),
+                                      ctypes.byref(st) if stats else None))
+        return outs, (st if stats else None)
+
+    def network_stats(self, index: int) -> RunStats:
+        st = RunStats()
+        _check(lib().ssa_batch_network_stats(self._h, int(index), ctypes.byref(st)))
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ssa_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -551,6 +551,15 @@ namespace ssa_impl {
 
 ssa_status record_error(ssa_status st, const char* msg) { return fail(st, "%s", msg); }
 
+int set_error(int status, const char* msg) { return (int)fail((ssa_status)status, "%s", msg); }
+
+int model_device_tables(const ssa_model* m, int dev, DevModel* out) {
+  if (dev < 0 || dev >= kMaxDevices) return (int)fail(SSA_EUNSUPPORTED, "device index %d out of range", dev);
+  return (int)model_on_device(m, dev, out);
+}
+
+const double* model_rates(const ssa_model* m) { return m->c.data(); }
+
 void clear_error() { g_last_error.clear(); }
 
 bool model_image_view(const ssa_model* m, ModelImageView* v) {

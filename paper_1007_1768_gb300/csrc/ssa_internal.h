@@ -127,6 +127,22 @@ cudaError_t launch_finalize(const unsigned long long* D1, const unsigned long lo
                             int64_t N, const int32_t* x0, double* mean, double* var, int64_t* sum1,
                             int64_t* sum2, cudaStream_t stream);
 cudaError_t launch_uniform_grid(double* grid, int G, double t_end, cudaStream_t stream);
+// One network's finalisation inputs and outputs (device pointers).
+struct FinalizeNet {
+  const unsigned long long* D1;
+  const unsigned long long* D2;
+  const int32_t* x0;
+  double* mean;
+  double* var;
+  int64_t* sum1;  // may be null
+  int64_t* sum2;  // may be null
+  int32_t G, S;
+  int64_t N;
+};
+// Finalises n_nets networks in one launch: cta_begin[b] = sum of S over
+// networks before b (n_nets + 1 entries, device), total_ctas = sum of S.
+cudaError_t launch_finalize_batch(const FinalizeNet* nets, const int* cta_begin, int n_nets, int total_ctas,
+                                  int max_G, cudaStream_t stream);
 // Largest M and S the thread kernel is instantiated for.
 constexpr int kThreadMaxM = 16;
 constexpr int kThreadMaxS = 16;
@@ -212,6 +228,13 @@ struct ssa_model;
 namespace ssa_impl {
 // Accessors implemented in ssa_api.cu.
 bool model_image_view(const ssa_model* m, ModelImageView* v);
+// The model's device tables on `dev` (copied there on first use); returns
+// SSA_OK or an error status with the thread's message set.
+int model_device_tables(const ssa_model* m, int dev, DevModel* out);
+// Rates of the model (host copy, [M]).
+const double* model_rates(const ssa_model* m);
+// Sets the calling thread's error message and returns `status`.
+int set_error(int status, const char* msg);
 }  // namespace ssa_impl
 
 #endif  // SSA_INTERNAL_H_

@@ -11,7 +11,8 @@
 //   D1 / D2 sit in shared memory per CTA when 2 G S 8 bytes fit, else in
 //   global memory; either way they end up summed in global memory.
 //
-// k_finalize: one CTA per species scans D1 / D2 along the grid, adds N x0,
+// k_finalize (k_finalize_batch: for many networks at once): one CTA per
+//   species scans D1 / D2 along the grid, adds N x0,
 //   and writes sum1, sum2, mean = sum1 / N and
 //   var = (N sum2 - sum1^2) / (N (N - 1)) with an exact 128-bit numerator.
 #include <cstdint>
@@ -55,12 +56,12 @@ __device__ __forceinline__ unsigned long long block_scan_u64(unsigned long long 
   return v + excl;
 }
 
-__global__ void __launch_bounds__(1024) k_finalize(const unsigned long long* __restrict__ D1,
-                                                   const unsigned long long* __restrict__ D2, int G, int S,
-                                                   long long N, const int32_t* __restrict__ x0, double* mean,
-                                                   double* var, long long* sum1, long long* sum2) {
-  __shared__ unsigned long long tot1[32], tot2[32];
-  const int s = blockIdx.x;
+// Scans species column s of one network's difference sums (the calling CTA).
+__device__ __forceinline__ void finalize_column(const unsigned long long* __restrict__ D1,
+                                                const unsigned long long* __restrict__ D2, int G, int S,
+                                                long long N, const int32_t* __restrict__ x0, double* mean,
+                                                double* var, long long* sum1, long long* sum2, int s,
+                                                unsigned long long* tot1, unsigned long long* tot2) {
   const long long xv = x0[s];
   unsigned long long carry1 = (unsigned long long)N * (unsigned long long)xv;
   unsigned long long carry2 = (unsigned long long)N * (unsigned long long)(xv * xv);
@@ -98,6 +99,30 @@ __global__ void __launch_bounds__(1024) k_finalize(const unsigned long long* __r
   }
 }
 
+__global__ void __launch_bounds__(1024) k_finalize(const unsigned long long* __restrict__ D1,
+                                                   const unsigned long long* __restrict__ D2, int G, int S,
+                                                   long long N, const int32_t* __restrict__ x0, double* mean,
+                                                   double* var, long long* sum1, long long* sum2) {
+  __shared__ unsigned long long tot1[32], tot2[32];
+  finalize_column(D1, D2, G, S, N, x0, mean, var, sum1, sum2, blockIdx.x, tot1, tot2);
+}
+
+// Batched finalisation: CTA c serves species c - cta_begin[b] of network b,
+// where cta_begin[b] <= c < cta_begin[b + 1].
+__global__ void __launch_bounds__(1024) k_finalize_batch(const FinalizeNet* __restrict__ nets,
+                                                         const int* __restrict__ cta_begin, int n_nets) {
+  __shared__ unsigned long long tot1[32], tot2[32];
+  const int c = blockIdx.x;
+  int lo = 0, hi = n_nets;  // last b with cta_begin[b] <= c
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (cta_begin[mid] <= c) lo = mid; else hi = mid;
+  }
+  const FinalizeNet f = nets[lo];
+  finalize_column(f.D1, f.D2, f.G, f.S, f.N, f.x0, f.mean, f.var, reinterpret_cast<long long*>(f.sum1),
+                  reinterpret_cast<long long*>(f.sum2), c - cta_begin[lo], tot1, tot2);
+}
+
 __global__ void k_uniform_grid(double* grid, int G, double t_end) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= G) return;
@@ -130,6 +155,14 @@ cudaError_t launch_finalize(const unsigned long long* D1, const unsigned long lo
   if (G < 1024) threads = ((G + 31) / 32) * 32;
   k_finalize<<<S, threads, 0, stream>>>(D1, D2, G, S, (long long)N, x0, mean, var,
                                          reinterpret_cast<long long*>(sum1), reinterpret_cast<long long*>(sum2));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batch(const FinalizeNet* nets, const int* cta_begin, int n_nets, int total_ctas,
+                                  int max_G, cudaStream_t stream) {
+  int threads = 1024;
+  if (max_G < 1024) threads = ((max_G + 31) / 32) * 32;
+  k_finalize_batch<<<total_ctas, threads, 0, stream>>>(nets, cta_begin, n_nets);
   return cudaGetLastError();
 }
 

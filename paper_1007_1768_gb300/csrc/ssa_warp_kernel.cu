@@ -1,37 +1,14 @@
-// The simulation kernel for large networks: one trajectory per warp.
-//
-// Gillespie's direct method (Sec. 2) with the reactions spread over the 32
-// lanes: lane l owns the contiguous chunk of CH = ceil(M / 32) reactions
-// starting at l * CH and keeps their propensities in registers.  Summation
-// schedule W32 (the oracle implements the same order):
-//   part_l = left-to-right sum of lane l's chunk (0 for an empty lane);
-//   inclusive Kogge-Stone scan of the parts with offsets 1, 2, 4, 8, 16
-//     (v_l <- v_l + v_{l - off} for l >= off, all lanes reading the
-//     previous step's values);
-//   prefix_j = inner_j for lane 0, v_{l-1} + inner_j otherwise, with
-//     inner_j the running sum inside the chunk up to j; a0 = v_31.
-// Selection: each lane finds its first reaction with a_j > 0 and
-// prefix_j > r2 a0; a ballot picks the lowest such lane (the first j overall).  After an event,
-// every lane reads its bits of the fired reaction's dependency mask (a
-// per-reaction, per-lane table in shared memory) and recomputes only those
-// propensities.  The state x lives in shared memory (S counts per warp); the
-// changes of the fired reaction are applied one per lane.  The random numbers
-// of 32 consecutive events are drawn at once, one per lane.  Selective memory
-// (Sec. 3.2.1) is the same difference-sum scheme as the thread kernel.
+// The single-network simulation kernel for large networks: one trajectory
+// per warp (schedule W32; the step itself is in ssa_warp_step.cuh).  Every
+// CTA stages the network's tables in shared memory once: rates, packed
+// reactant words, the net-change CSR, x0, the per-lane dependency bits and
+// the log tables; each warp then takes trajectory ids from a global counter.
 #include <cstdint>
 
-#include "ssa_thread_kernel.cuh"  // shared helpers: products, grid index, tables
+#include "ssa_warp_step.cuh"
 
 namespace ssa_impl {
 namespace {
-
-constexpr int kWarpFlagTruncated = 1;  // per-trajectory flag bits
-constexpr int kWarpFlagOverflow = 2;
-
-// Exact binary32 -> binary64 widening of a non-negative value on the integer pipe.
-__device__ __forceinline__ double widen(float f) {
-  return __longlong_as_double((long long)ssa_sf::f32_to_f64(__float_as_uint(f)));
-}
 
 // Shared-memory layout of the warp kernel (bytes).
 struct WarpSmem {
@@ -56,14 +33,12 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int M, int S, int nnz, int 
   return L;
 }
 
-// MAXCH bounds the chunk ceil(M / 32) (registers only; the chunk itself is
-// the runtime value, as the schedule defines it).  F32 selects the
-// FP32-propensity mode.
+// MAXCH bounds the chunk ceil(M / 32); F32 selects the FP32-propensity mode.
 template <int MAXCH, bool F32>
 __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long blk[4];
-  const int S = a.m.S, M = a.m.M, G = a.G, T = blockDim.x, tid = threadIdx.x;
+  const int S = a.m.S, M = a.m.M, T = blockDim.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
   const int ch = (M + 31) / 32;
   const WarpSmem L = warp_smem_layout(M, S, a.m.nnz, nwarps);
@@ -94,23 +69,31 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a) {
     s_nuval[i] = a.m.nu_val[i];
   }
   for (int s = tid; s < S; s += T) s_x0[s] = a.m.x0[s];
-  // entry (j, l): bit q set when reaction l * ch + q reads a species j changes
-  for (int i = tid; i < M * 32; i += T) {
-    const int j = i >> 5, l = i & 31;
-    uint32_t bits = 0;
-    for (int q = a.m.dep_ptr[j]; q < a.m.dep_ptr[j + 1]; ++q) {
-      const int kk = a.m.dep_idx[q];
-      if (kk / ch == l) bits |= 1u << (kk - l * ch);
-    }
-    s_depw[i] = (uint16_t)bits;
-  }
+  for (int i = tid; i < M * 32; i += T) s_depw[i] = depw_entry(a.m.dep_ptr, a.m.dep_idx, ch, i >> 5, i & 31);
   if (tid < 4) blk[tid] = 0ULL;
   __syncthreads();
 
-  const long long t_end_bits = obits(a.t_end);
-  const uint32_t key0 = (uint32_t)a.seed, key1 = (uint32_t)(a.seed >> 32), sid = (uint32_t)a.stream_id;
-  const int my0 = lane * ch;                          // first reaction of this lane
-  const int mine = max(0, min(ch, M - my0));          // reactions this lane owns
+  WarpNet net;
+  net.rinfo = s_rinfo;
+  net.cbits = s_cbits;
+  net.c32 = s_c32;
+  net.nu_ptr = s_nuptr;
+  net.nu_idx = s_nuidx;
+  net.nu_val = s_nuval;
+  net.depw = s_depw;
+  net.x0 = s_x0;
+  net.grid = a.grid;
+  net.D1 = a.D1;
+  net.D2 = a.D2;
+  net.t_end_bits = obits(a.t_end);
+  net.S = S;
+  net.M = M;
+  net.G = a.G;
+  net.grid_uniform = a.grid_uniform;
+  net.grid_scale = a.grid_scale;
+  net.grid_margin = a.grid_margin;
+  net.sid = (uint32_t)a.stream_id;
+  const uint32_t key0 = (uint32_t)a.seed, key1 = (uint32_t)(a.seed >> 32);
 
   for (;;) {
     unsigned long long next = 0;
@@ -118,186 +101,16 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a) {
     next = __shfl_sync(kFullMask, next, 0);
     if (next >= (unsigned long long)a.N) break;
     const long long li = (long long)next;
-    const unsigned long long traj_id = a.traj_offset + next;
-    int maxx = 0;
-    for (int s = lane; s < S; s += 32) {
-      xs[s] = s_x0[s];
-      maxx = max(maxx, s_x0[s]);
-    }
-    __syncwarp();
-    double av[MAXCH];  // FP64 mode: a_j
-    float af[MAXCH];   // FP32 mode: a_j in binary32
-#pragma unroll
-    for (int q = 0; q < MAXCH; ++q) {
-      av[q] = 0.0;
-      af[q] = 0.0f;
-    }
-    uint32_t dirty = (1u << mine) - 1u;
-    double t = 0.0;
-    uint32_t n = 0;
-    int k = 0;
-    unsigned long long hash = kFnvOffset;
-    int flags = 0;
-    uint32_t base = 0;
-    unsigned long long cE = 0, cU = 0;
-    bool filled = false;
-
-    for (;;) {
-      // propensities of this lane's reactions that the last event touched
-#pragma unroll
-      for (int q = 0; q < MAXCH; ++q) {
-        if ((dirty >> q) & 1u) {
-          const int j = my0 + q;
-          const int32_t w = s_rinfo[j];
-          const int kind = rinfo_kind(w);
-          const long long xa = xs[rinfo_a(w)];
-          const long long xb = xs[rinfo_b(w)];
-          const long long bi = xa * ((kind == kBi) ? xb : (xa - 1));
-          const long long h =
-              (kind == kOrder0) ? 1LL : ((kind == kUni) ? xa : ((kind == kBi) ? bi : (bi >> 1)));
-          if constexpr (F32)
-            af[q] = __fmul_rn(s_c32[j], __ll2float_rn(h));
-          else
-            av[q] = __longlong_as_double((long long)propensity_fp64(s_cbits[j], h));
-        }
-      }
-      // schedule W32: running sums inside the chunk, Kogge-Stone scan of the
-      // chunk sums, prefixes excl + inner.  A past-the-end a_j is +0 and
-      // x + (+0) = x, so the last running sum is the chunk sum (+0 for an
-      // empty lane).
-      double run[MAXCH];   // FP64 mode: running sums
-      float run32[MAXCH];  // FP32 mode: binary32 running sums
-      double a0, excl = 0.0, sel_total;
-      float excl32 = 0.0f;
-      if constexpr (F32) {
-        // binary32 selection sums
-#pragma unroll
-        for (int q = 0; q < MAXCH; ++q) run32[q] = (q == 0) ? af[0] : __fadd_rn(run32[q - 1], af[q]);
-        float v32 = run32[MAXCH - 1];
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const float u = __shfl_up_sync(kFullMask, v32, off);
-          if (lane >= off) v32 = __fadd_rn(v32, u);
-        }
-        excl32 = __shfl_up_sync(kFullMask, v32, 1);
-        sel_total = widen(__shfl_sync(kFullMask, v32, 31));
-        // a0: FP64 sum of the widened a_j in the same schedule, formed anew each event
-        double r64 = widen(af[0]);
-#pragma unroll
-        for (int q = 1; q < MAXCH; ++q) r64 = __dadd_rn(r64, widen(af[q]));
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const double u = __shfl_up_sync(kFullMask, r64, off);
-          if (lane >= off) r64 = __dadd_rn(r64, u);
-        }
-        a0 = __shfl_sync(kFullMask, r64, 31);
-      } else {
-#pragma unroll
-        for (int q = 0; q < MAXCH; ++q) run[q] = (q == 0) ? av[0] : __dadd_rn(run[q - 1], av[q]);
-        double v = run[MAXCH - 1];
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const double u = __shfl_up_sync(kFullMask, v, off);
-          if (lane >= off) v = __dadd_rn(v, u);
-        }
-        excl = __shfl_up_sync(kFullMask, v, 1);
-        a0 = __shfl_sync(kFullMask, v, 31);
-        sel_total = a0;
-      }
-      // random numbers of event n: 32 consecutive events drawn at once, one per lane
-      if (!filled || n >= base + 32u) {
-        base = n;
-        const EventRandom r = event_random(base + (uint32_t)lane, traj_id, sid, key0, key1, s_inv, s_lnf);
-        cE = r.E;
-        cU = r.u2;
-        filled = true;
-      }
-      const int slot = (int)(n - base);
-      const unsigned long long Eb = __shfl_sync(kFullMask, cE, slot);
-      const unsigned long long Ub = __shfl_sync(kFullMask, cU, slot);
-      const double t_next = __dadd_rn(t, quotient(Eb, a0));  // a0 == 0: +inf
-      const long long tb = obits(t_next);
-      if (tb > t_end_bits) break;
-      k = grid_index(a, tb, k);
-      // selection: first j with a_j > 0 and prefix_j > r2 * total (FP64
-      // product; FP32 mode compares the widened binary32 prefixes).  The
-      // a_j > 0 test matters at lane boundaries, where the scan's exclusive
-      // value can exceed the previous lane's last prefix by rounding.
-      const long long gb = obits(__dmul_rn(__longlong_as_double((long long)Ub), sel_total));
-      int myfirst = -1;
-#pragma unroll
-      for (int q = MAXCH - 1; q >= 0; --q) {
-        if (q < mine) {
-          long long pb;
-          bool pos;
-          if constexpr (F32) {
-            pb = obits(widen((lane == 0) ? run32[q] : __fadd_rn(excl32, run32[q])));
-            pos = __float_as_uint(af[q]) != 0u;
-          } else {
-            pb = obits((lane == 0) ? run[q] : __dadd_rn(excl, run[q]));
-            pos = obits(av[q]) > 0;
-          }
-          if (pos && pb > gb) myfirst = my0 + q;
-        }
-      }
-      const unsigned hit = __ballot_sync(kFullMask, myfirst >= 0);
-      int jsel;
-      if (hit) {
-        jsel = __shfl_sync(kFullMask, myfirst, __ffs(hit) - 1);
-      } else {  // rounding left no j: the last reaction with a_j > 0
-        int mylast = -1;
-#pragma unroll
-        for (int q = 0; q < MAXCH; ++q) {
-          const bool pos = F32 ? (__float_as_uint(af[q]) != 0u) : (obits(av[q]) > 0);
-          if (q < mine && pos) mylast = my0 + q;
-        }
-        const unsigned pos = __ballot_sync(kFullMask, mylast >= 0);
-        jsel = __shfl_sync(kFullMask, mylast, 31 - __clz(pos));
-      }
-      // state change of jsel, one nonzero entry per lane
-      const int q0 = s_nuptr[jsel], q1 = s_nuptr[jsel + 1];
-      bool over = false;
-      for (int e = q0 + lane; e < q1; e += 32)
-        over |= (long long)xs[s_nuidx[e]] + (long long)s_nuval[e] > kStateMax;
-      if (__any_sync(kFullMask, over)) {
-        flags |= kWarpFlagOverflow;
-        break;
-      }
-      __syncwarp();
-      for (int e = q0 + lane; e < q1; e += 32) {
-        const int s = s_nuidx[e];
-        const int vv = s_nuval[e];
-        const int xo = xs[s];
-        const int xn = xo + vv;
-        xs[s] = xn;
-        maxx = max(maxx, xn);
-        if (k < G) {
-          atomicAdd(a.D1 + (size_t)k * S + s, (unsigned long long)(long long)vv);
-          atomicAdd(a.D2 + (size_t)k * S + s, (unsigned long long)((2 * (long long)xo + vv) * (long long)vv));
-        }
-      }
-      __syncwarp();
-      t = t_next;
-      ++n;
-      hash = (hash ^ (unsigned long long)jsel) * kFnvPrime;
-      hash = (hash ^ (unsigned long long)tb) * kFnvPrime;
-      dirty = s_depw[jsel * 32 + lane];
-      if ((long long)n == a.max_events) {
-        flags |= kWarpFlagTruncated;
-        break;
-      }
-    }
-    // trajectory done
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) maxx = max(maxx, __shfl_xor_sync(kFullMask, maxx, off));
+    const WarpTraj r =
+        warp_trajectory<MAXCH, F32>(net, xs, a.traj_offset + next, key0, key1, a.max_events, s_inv, s_lnf);
     if (lane == 0) {
-      if (a.traj_events) a.traj_events[li] = (long long)n;
-      if (a.traj_hash) a.traj_hash[li] = hash;
-      if (a.traj_flags) a.traj_flags[li] = flags;
-      atomicAdd(&blk[0], (unsigned long long)n);
-      if (flags & kWarpFlagTruncated) atomicAdd(&blk[1], 1ULL);
-      if (flags & kWarpFlagOverflow) atomicAdd(&blk[2], 1ULL);
-      atomicMax(&blk[3], (unsigned long long)maxx);
+      if (a.traj_events) a.traj_events[li] = (long long)r.n;
+      if (a.traj_hash) a.traj_hash[li] = r.hash;
+      if (a.traj_flags) a.traj_flags[li] = r.flags;
+      atomicAdd(&blk[0], (unsigned long long)r.n);
+      if (r.flags & kWarpFlagTruncated) atomicAdd(&blk[1], 1ULL);
+      if (r.flags & kWarpFlagOverflow) atomicAdd(&blk[2], 1ULL);
+      atomicMax(&blk[3], (unsigned long long)r.maxx);
     }
     __syncwarp();
   }

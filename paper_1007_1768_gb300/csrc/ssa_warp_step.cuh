@@ -1,0 +1,333 @@
+// One trajectory of the direct method on one warp (schedule W32), shared by
+// the single-network warp kernel (tables in shared memory) and the batched
+// kernel (tables of many networks in global memory).
+//
+// Gillespie's direct method (Sec. 2) with the reactions spread over the 32
+// lanes: lane l owns the contiguous chunk of ch = ceil(M / 32) reactions
+// starting at l * ch and keeps their propensities in registers.  Summation
+// schedule W32 (the oracle implements the same order):
+//   part_l = left-to-right sum of lane l's chunk (0 for an empty lane);
+//   inclusive Kogge-Stone scan of the parts with offsets 1, 2, 4, 8, 16
+//     (v_l <- v_l + v_{l - off} for l >= off, all lanes reading the
+//     previous step's values);
+//   prefix_j = inner_j for lane 0, v_{l-1} + inner_j otherwise, with
+//     inner_j the running sum inside the chunk up to j; a0 = v_31.
+// Selection: each lane finds its first reaction with a_j > 0 and
+// prefix_j > r2 a0; a ballot picks the lowest such lane (the first j
+// overall).  After an event every lane reads its bits of the fired
+// reaction's dependency mask (a per-reaction, per-lane table) and recomputes
+// only those propensities.  The state x lives in shared memory (S counts per
+// warp); the changes of the fired reaction are applied one per lane.  The
+// random numbers of 32 consecutive events are drawn at once, one per lane.
+// Selective memory (Sec. 3.2.1) is the difference-sum scheme of the thread
+// kernel: an event at time t changing x_s by v adds v and (2 x_s + v) v at
+// the first grid index k with g_k >= t.
+//
+// FP32-propensity mode (F32): a_j = (float)c_j * (float)h_j in binary32,
+// binary32 selection sums; a0 formed anew at every event from each lane's
+// error-compensated binary32 chunk sum (Ogita-Rump-Oishi Sum2), widened and
+// scanned in FP64; FP64 time; selection compares the widened binary32
+// prefixes with r2 times the binary32 total.
+#ifndef SSA_WARP_STEP_CUH_
+#define SSA_WARP_STEP_CUH_
+
+#include <cstdint>
+
+#include "ssa_thread_kernel.cuh"  // shared helpers: products, random numbers, tables
+
+namespace ssa_impl {
+namespace {
+
+constexpr int kWarpFlagTruncated = 1;  // per-trajectory flag bits
+constexpr int kWarpFlagOverflow = 2;
+
+// Exact binary32 -> binary64 widening of a non-negative value on the integer pipe.
+__device__ __forceinline__ double widen(float f) {
+  return __longlong_as_double((long long)ssa_sf::f32_to_f64(__float_as_uint(f)));
+}
+
+// Exact widening of any finite binary32 value (sign applied to the widened magnitude).
+__device__ __forceinline__ double widen_signed(float f) {
+  const uint32_t fb = __float_as_uint(f);
+  const unsigned long long mag = ssa_sf::f32_to_f64(fb & 0x7FFFFFFFu);
+  return __longlong_as_double((long long)(mag | ((unsigned long long)(fb >> 31) << 63)));
+}
+
+// Everything a warp needs to run trajectories of one network.
+struct WarpNet {
+  const int32_t* rinfo;               // [M] packed reactant words
+  const unsigned long long* cbits;    // [M] rates (double bits)
+  const float* c32;                   // [M] rates rounded to binary32 (FP32 mode)
+  const int32_t* nu_ptr;              // [M + 1] CSR of nonzero net changes
+  const int32_t* nu_idx;
+  const int32_t* nu_val;
+  const uint16_t* depw;               // [M * 32] per-lane dependency bits
+  const int32_t* x0;                  // [S]
+  const double* grid;                 // [G]
+  unsigned long long* D1;             // [G * S] difference sums
+  unsigned long long* D2;
+  long long t_end_bits;
+  int S, M, G;
+  int grid_uniform;
+  float grid_scale, grid_margin;
+  uint32_t sid;                       // fourth Philox counter word
+};
+
+// Outcome of one trajectory (the same on every lane).
+struct WarpTraj {
+  uint32_t n;
+  unsigned long long hash;
+  int flags;
+  int maxx;
+};
+
+// First index k' >= k with g_{k'} >= t (t given by its bits tb <= t_end), or
+// G; the uniform-grid estimate is checked against the grid near cell edges.
+__device__ __forceinline__ int grid_index_net(const WarpNet& net, long long tb, int k) {
+  const int G = net.G;
+  if (net.grid_uniform) {
+    const float est = approx_float_rz(tb) * net.grid_scale;
+    const float fl = floorf(est);
+    const float fr = est - fl;
+    int ke = min(max((int)fl + 1, k), G);
+    if (fr > net.grid_margin && fr < 1.0f - net.grid_margin) return ke;
+    if (ke > k && obits(__ldg(net.grid + ke - 1)) >= tb) --ke;
+    if (ke > k && obits(__ldg(net.grid + ke - 1)) >= tb) --ke;
+    if (ke < G && obits(__ldg(net.grid + ke)) < tb) ++ke;
+    return ke;
+  }
+  while (k < G && obits(__ldg(net.grid + k)) < tb) ++k;
+  return k;
+}
+
+// Dependency-bit table entry (j, l): bit q set when reaction l * ch + q
+// reads a species that reaction j changes.
+__host__ __device__ inline uint16_t depw_entry(const int32_t* dep_ptr, const int32_t* dep_idx, int ch, int j,
+                                               int l) {
+  uint32_t bits = 0;
+  for (int q = dep_ptr[j]; q < dep_ptr[j + 1]; ++q) {
+    const int kk = dep_idx[q];
+    if (kk / ch == l) bits |= 1u << (kk - l * ch);
+  }
+  return (uint16_t)bits;
+}
+
+// Runs trajectory traj_id of `net` on the calling warp (all 32 lanes), with
+// the state in xs[0..S) (shared memory, this warp's own).  MAXCH bounds the
+// chunk ceil(M / 32) (registers only; the chunk itself is the runtime value).
+template <int MAXCH, bool F32>
+__device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t* xs, unsigned long long traj_id,
+                                                    uint32_t key0, uint32_t key1, long long max_events,
+                                                    const uint64_t* s_inv, const uint64_t* s_lnf) {
+  const int lane = threadIdx.x & 31;
+  const int S = net.S, M = net.M;
+  const int ch = (M + 31) / 32;
+  const int my0 = lane * ch;                          // first reaction of this lane
+  const int mine = max(0, min(ch, M - my0));          // reactions this lane owns
+  int maxx = 0;
+  for (int s = lane; s < S; s += 32) {
+    const int v = net.x0[s];
+    xs[s] = v;
+    maxx = max(maxx, v);
+  }
+  __syncwarp();
+  double av[MAXCH];  // FP64 mode: a_j
+  float af[MAXCH];   // FP32 mode: a_j in binary32
+#pragma unroll
+  for (int q = 0; q < MAXCH; ++q) {
+    av[q] = 0.0;
+    af[q] = 0.0f;
+  }
+  uint32_t dirty = (1u << mine) - 1u;
+  double t = 0.0;
+  uint32_t n = 0;
+  int k = 0;
+  unsigned long long hash = kFnvOffset;
+  int flags = 0;
+  uint32_t base = 0;
+  unsigned long long cE = 0, cU = 0;
+  bool filled = false;
+
+  for (;;) {
+    // propensities of this lane's reactions that the last event touched
+#pragma unroll
+    for (int q = 0; q < MAXCH; ++q) {
+      if (q >= ch) break;
+      if ((dirty >> q) & 1u) {
+        const int j = my0 + q;
+        const int32_t w = net.rinfo[j];
+        const int kind = rinfo_kind(w);
+        const long long xa = xs[rinfo_a(w)];
+        const long long xb = xs[rinfo_b(w)];
+        const long long bi = xa * ((kind == kBi) ? xb : (xa - 1));
+        const long long h =
+            (kind == kOrder0) ? 1LL : ((kind == kUni) ? xa : ((kind == kBi) ? bi : (bi >> 1)));
+        if constexpr (F32)
+          af[q] = __fmul_rn(net.c32[j], __ll2float_rn(h));
+        else
+          av[q] = __longlong_as_double((long long)propensity_fp64(net.cbits[j], h));
+      }
+    }
+    // schedule W32: running sums inside the chunk, Kogge-Stone scan of the
+    // chunk sums, prefixes excl + inner.  A past-the-end a_j (lanes owning
+    // fewer than ch reactions) is +0 and x + (+0) = x, so the last running
+    // sum is the chunk sum (+0 for an empty lane).
+    double run[MAXCH];   // FP64 mode: running sums
+    float run32[MAXCH];  // FP32 mode: binary32 running sums
+    double a0, excl = 0.0, sel_total;
+    float excl32 = 0.0f;
+    // loops over the chunk stop at ch (warp-uniform), the runtime chunk size
+    if constexpr (F32) {
+      // binary32 selection sums
+      float v32 = af[0];
+      run32[0] = v32;
+#pragma unroll
+      for (int q = 1; q < MAXCH; ++q) {
+        if (q >= ch) break;
+        v32 = __fadd_rn(v32, af[q]);
+        run32[q] = v32;
+      }
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const float u = __shfl_up_sync(kFullMask, v32, off);
+        if (lane >= off) v32 = __fadd_rn(v32, u);
+      }
+      excl32 = __shfl_up_sync(kFullMask, v32, 1);
+      sel_total = widen(__shfl_sync(kFullMask, v32, 31));
+      // a0, formed anew each event: the lane's chunk summed left to right in
+      // binary32 with its rounding errors carried (cascaded TwoSum), the two
+      // parts widened and added in FP64, the lane values scanned in FP64.
+      // A past-the-end a_j = +0 leaves both parts unchanged.
+      float cs = af[0], cerr = 0.0f;
+#pragma unroll
+      for (int q = 1; q < MAXCH; ++q) {
+        if (q >= ch) break;
+        const float x = af[q];
+        const float tt = __fadd_rn(cs, x);
+        const float bp = __fsub_rn(tt, cs);
+        const float d = __fadd_rn(__fsub_rn(cs, __fsub_rn(tt, bp)), __fsub_rn(x, bp));
+        cerr = __fadd_rn(cerr, d);
+        cs = tt;
+      }
+      double r64 = __dadd_rn(widen(cs), widen_signed(cerr));
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const double u = __shfl_up_sync(kFullMask, r64, off);
+        if (lane >= off) r64 = __dadd_rn(r64, u);
+      }
+      a0 = __shfl_sync(kFullMask, r64, 31);
+    } else {
+      double v = av[0];
+      run[0] = v;
+#pragma unroll
+      for (int q = 1; q < MAXCH; ++q) {
+        if (q >= ch) break;
+        v = __dadd_rn(v, av[q]);
+        run[q] = v;
+      }
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const double u = __shfl_up_sync(kFullMask, v, off);
+        if (lane >= off) v = __dadd_rn(v, u);
+      }
+      excl = __shfl_up_sync(kFullMask, v, 1);
+      a0 = __shfl_sync(kFullMask, v, 31);
+      sel_total = a0;
+    }
+    // random numbers of event n: 32 consecutive events drawn at once, one per lane
+    if (!filled || n >= base + 32u) {
+      base = n;
+      const EventRandom r = event_random(base + (uint32_t)lane, traj_id, net.sid, key0, key1, s_inv, s_lnf);
+      cE = r.E;
+      cU = r.u2;
+      filled = true;
+    }
+    const int slot = (int)(n - base);
+    const unsigned long long Eb = __shfl_sync(kFullMask, cE, slot);
+    const unsigned long long Ub = __shfl_sync(kFullMask, cU, slot);
+    const double t_next = __dadd_rn(t, quotient(Eb, a0));  // a0 == 0: +inf
+    const long long tb = obits(t_next);
+    if (tb > net.t_end_bits) break;
+    k = grid_index_net(net, tb, k);
+    // selection: first j with a_j > 0 and prefix_j > r2 * total (FP64
+    // product).  The a_j > 0 test matters at lane boundaries, where the
+    // scan's exclusive value can exceed the previous lane's last prefix by
+    // rounding.  FP32 mode: for a binary32 p and a double T >= 0,
+    // (double)p > T exactly when p > RD32(T), T rounded down to binary32, so
+    // the widened comparison runs on the binary32 bit patterns.
+    const double target = __dmul_rn(__longlong_as_double((long long)Ub), sel_total);
+    const long long gb = obits(target);
+    unsigned gf = 0;
+    if constexpr (F32) gf = __float_as_uint(__double2float_rd(target));
+    int myfirst = -1;
+#pragma unroll
+    for (int q = 0; q < MAXCH; ++q) {
+      if (q >= ch) break;
+      bool hitq;
+      if constexpr (F32) {
+        const float pre = (lane == 0) ? run32[q] : __fadd_rn(excl32, run32[q]);
+        hitq = (__float_as_uint(af[q]) != 0u) && (__float_as_uint(pre) > gf);
+      } else {
+        const double pre = (lane == 0) ? run[q] : __dadd_rn(excl, run[q]);
+        hitq = (obits(av[q]) > 0) && (obits(pre) > gb);
+      }
+      if (hitq && myfirst < 0 && q < mine) myfirst = my0 + q;
+    }
+    const unsigned hit = __ballot_sync(kFullMask, myfirst >= 0);
+    int jsel;
+    if (hit) {
+      jsel = __shfl_sync(kFullMask, myfirst, __ffs(hit) - 1);
+    } else {  // rounding left no j: the last reaction with a_j > 0
+      int mylast = -1;
+#pragma unroll
+      for (int q = 0; q < MAXCH; ++q) {
+        if (q >= ch) break;
+        const bool pos = F32 ? (__float_as_uint(af[q]) != 0u) : (obits(av[q]) > 0);
+        if (q < mine && pos) mylast = my0 + q;
+      }
+      const unsigned pos = __ballot_sync(kFullMask, mylast >= 0);
+      jsel = __shfl_sync(kFullMask, mylast, 31 - __clz(pos));
+    }
+    // state change of jsel, one nonzero entry per lane
+    const int q0 = net.nu_ptr[jsel], q1 = net.nu_ptr[jsel + 1];
+    bool over = false;
+    for (int e = q0 + lane; e < q1; e += 32)
+      over |= (long long)xs[net.nu_idx[e]] + (long long)net.nu_val[e] > kStateMax;
+    if (__any_sync(kFullMask, over)) {
+      flags |= kWarpFlagOverflow;
+      break;
+    }
+    __syncwarp();
+    for (int e = q0 + lane; e < q1; e += 32) {
+      const int s = net.nu_idx[e];
+      const int vv = net.nu_val[e];
+      const int xo = xs[s];
+      const int xn = xo + vv;
+      xs[s] = xn;
+      maxx = max(maxx, xn);
+      if (k < net.G) {
+        atomicAdd(net.D1 + (size_t)k * S + s, (unsigned long long)(long long)vv);
+        atomicAdd(net.D2 + (size_t)k * S + s, (unsigned long long)((2 * (long long)xo + vv) * (long long)vv));
+      }
+    }
+    __syncwarp();
+    t = t_next;
+    ++n;
+    hash = (hash ^ (unsigned long long)jsel) * kFnvPrime;
+    hash = (hash ^ (unsigned long long)tb) * kFnvPrime;
+    dirty = net.depw[jsel * 32 + lane];
+    if ((long long)n == max_events) {
+      flags |= kWarpFlagTruncated;
+      break;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) maxx = max(maxx, __shfl_xor_sync(kFullMask, maxx, off));
+  __syncwarp();
+  return WarpTraj{n, hash, flags, maxx};
+}
+
+}  // namespace
+}  // namespace ssa_impl
+
+#endif  // SSA_WARP_STEP_CUH_

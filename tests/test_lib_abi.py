@@ -155,3 +155,21 @@ def test_fp32_mode_limits_are_refused_before_touching_the_gpu():
         ssa.ensemble_run(model, 10, 1.0, 11, seed=1, precision="fp32")
     assert e.value.status == binding.SSA_EINVAL and "binary32" in str(e.value)
     model.close()
+
+
+def test_batch_arguments_are_refused_before_touching_the_gpu():
+    net_R, net_P = [[0], [1]], [[1], [0]]
+    m = ssa.Model(net_R, net_P, [10.0, 0.1], [0])
+    with pytest.raises(ssa.SSAError) as e:
+        ssa.Batch([m, m], [10, 10], [1.0, 1.0], [11, 11], stream_id=(1 << 32) - 1)
+    assert e.value.status == binding.SSA_EINVAL
+    with pytest.raises(ssa.SSAError) as e:
+        ssa.Batch([m], [10], [1.0], [11], schedule="thread")
+    assert e.value.status == binding.SSA_EUNSUPPORTED
+    with pytest.raises(ssa.SSAError) as e:
+        ssa.Batch([m], [0], [1.0], [11])
+    assert e.value.status == binding.SSA_EINVAL
+    with pytest.raises(ssa.SSAError) as e:
+        ssa.Batch([m], [10], [1.0], [11], block_threads=96)
+    assert e.value.status == binding.SSA_EINVAL
+    m.close()

@@ -20,6 +20,7 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 import math
+import os
 
 import numpy as np
 
@@ -158,18 +159,38 @@ def workload_random(n_traj: int = 262144, net_seed: int = 3, seed: int = 1) -> W
     return Workload(random_network(net_seed), n_traj, 10.0, 1001, seed)
 
 
-def batch_networks(n_networks: int = 256, first_seed: int = 1000, traj_lo: int = 1024,
-                   traj_hi: int = 65536):
-    """Uneven batch: species in [4, 64], reactions in [8, 512], trajectory counts
-    log-uniform in [traj_lo, traj_hi] (rounded), t_end = 10, 501-point grids."""
+def batch_network(seed: int, traj_lo: int = 1024, traj_hi: int = 65536) -> Workload:
+    """One network of the uneven batch, drawn from `seed`: species in [4, 64],
+    reactions in [8, 512], trajectory count log-uniform in [traj_lo, traj_hi]
+    (rounded), t_end = 10, 501-point grid."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    S = int(rng.integers(4, 65))
+    M = int(rng.integers(8, 513))
+    n = int(round(math.exp(rng.uniform(math.log(traj_lo), math.log(traj_hi)))))
+    net = random_network(seed, S, M)
+    return Workload(net, n, 10.0, 501, 1, {"seed": seed})
+
+
+BATCH_SEEDS_FILE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden",
+                                "batch_networks.txt")
+
+
+def batch_seeds() -> list:
+    """Accepted network seeds of the batched workload (written by
+    tests/golden/make_batch_networks.py: draws whose 16-trajectory pilot
+    runs away are rejected)."""
+    with open(BATCH_SEEDS_FILE) as f:
+        return [int(line) for line in f if line.strip() and not line.startswith("#")]
+
+
+def batch_networks(n_networks: int = 256, traj_div: int = 1):
+    """The uneven batch: the first n_networks accepted seeds, trajectory counts
+    divided by traj_div (at least 1)."""
     out = []
-    for b in range(n_networks):
-        rng = np.random.Generator(np.random.PCG64(first_seed + b))
-        S = int(rng.integers(4, 65))
-        M = int(rng.integers(8, 513))
-        n = int(round(math.exp(rng.uniform(math.log(traj_lo), math.log(traj_hi)))))
-        net = random_network(first_seed + b, S, M)
-        out.append(Workload(net, n, 10.0, 501, 1, {"index": b}))
+    for b, seed in enumerate(batch_seeds()[:n_networks]):
+        w = batch_network(seed)
+        w = Workload(w.net, max(1, w.n_traj // traj_div), w.t_end, w.n_grid, w.seed, {"index": b, "seed": seed})
+        out.append(w)
     return out
 
 
