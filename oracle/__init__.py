@@ -143,6 +143,9 @@ def lib():
         L.oracle_trace.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, i64, f64, ctypes.c_int, vp, u64,
                                    u64, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
         L.oracle_trace.restype = ctypes.c_int
+        L.oracle_grad.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, i64, i64, f64, ctypes.c_int, vp,
+                                  u64, u64, i64, ctypes.c_int, vp, vp, vp]
+        L.oracle_grad.restype = ctypes.c_int
         L.oracle_select.argtypes = [ctypes.c_int, vp, ctypes.c_int, f64]
         L.oracle_select.restype = ctypes.c_int
         L.oracle_prefix.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, vp]
@@ -298,6 +301,43 @@ def trace(net, traj_id: int, t_end: float, n_grid: int, seed: int, grid=None, st
                            xs.ctypes.data, ne.ctypes.data)
     n = int(min(ne[0], record_max))
     return rt[:n], rj[:n], xs, int(flags), int(ne[0])
+
+
+def grad(net, n_traj: int, t_end: float, n_grid: int, seed: int, dL_dmean, mean, grid=None, traj_begin: int = 0,
+         stream: int = 0, max_events: int = MAX_EVENTS, schedule: int = SCHEDULE_L, threads: int = 1,
+         ids=None):
+    """Per-trajectory likelihood-ratio contributions g [n, M] (FP64 mode):
+    dL/dc = g.mean(axis=0), its standard error g.std(ddof=1) / sqrt(n)."""
+    L = lib()
+    R, P, c, x0 = _model_arrays(net)
+    S, M = net.n_species, net.n_reactions
+    g = uniform_grid(n_grid, t_end) if grid is None else np.ascontiguousarray(grid, dtype=np.float64)
+    G = int(g.shape[0])
+    w = np.ascontiguousarray(dL_dmean, dtype=np.float64).reshape(G, S)
+    mu = np.ascontiguousarray(mean, dtype=np.float64).reshape(G, S)
+    spans = [(int(i), int(i) + 1) for i in ids] if ids is not None else [(traj_begin, traj_begin + n_traj)]
+    if ids is None and threads > 1 and n_traj > 1:
+        bounds = np.linspace(traj_begin, traj_begin + n_traj, threads + 1).astype(np.int64)
+        spans = [(int(bounds[i]), int(bounds[i + 1])) for i in range(threads) if bounds[i + 1] > bounds[i]]
+    rows = sum(e - b for b, e in spans)
+    out = np.zeros((rows, M), dtype=np.float64)
+    offs = np.cumsum([0] + [e - b for b, e in spans])
+
+    def work(i):
+        b, e = spans[i]
+        view = out[offs[i]:offs[i + 1]]
+        rc = L.oracle_grad(S, M, R.ctypes.data, P.ctypes.data, c.ctypes.data, x0.ctypes.data, b, e, float(t_end),
+                           G, g.ctypes.data, int(seed), int(stream), int(max_events), int(schedule), w.ctypes.data,
+                           mu.ctypes.data, view.ctypes.data)
+        if rc != 0:
+            raise ValueError("oracle_grad rejected its arguments")
+    if threads > 1 and len(spans) > 1:
+        with ThreadPoolExecutor(max_workers=min(threads, len(spans))) as ex:
+            list(ex.map(work, range(len(spans))))
+    else:
+        for i in range(len(spans)):
+            work(i)
+    return out
 
 
 def select(a, target: float, schedule: int = SCHEDULE_L) -> int:

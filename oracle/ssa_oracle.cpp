@@ -378,6 +378,77 @@ TrajResult run_one(const Model& m, uint64_t traj_id, double t_end, int G, const 
   return res;
 }
 
+// Likelihood-ratio sensitivities of one FP64 trajectory (the reading of the
+// score of a CTMC path under mass action): for reaction r with rate c_r,
+//   Z_r(t) = N_r(t) / c_r - I_r(t),  I_r(t) = integral_0^t h_r(x(s)) ds,
+// N_r(t) the firings of r up to t.  The path's contribution to dL/dc_r is
+//   g_r = sum_k u_k Z_r(g_k),  u_k = sum_s w[k][s] (x_s(g_k) - m[k][s]),
+// with w = dL/dmean and m the ensemble mean (centering).  The trajectory is
+// the same as run_one's (same draws, schedule L or W32, FP64 propensities).
+// I_r accumulates h_r (t_next - t) over each inter-event interval; at a grid
+// point inside the current interval, I_r(g_k) = I_r(t) + h_r (g_k - t).
+void run_one_grad(const Model& m, uint64_t traj_id, double t_end, int G, const double* grid, uint64_t seed,
+                  uint64_t stream, int64_t max_events, int schedule, const double* w, const double* mu,
+                  double* g_out) {
+  std::vector<int64_t> x(m.S), nfire(m.M, 0), h(m.M);
+  for (int s = 0; s < m.S; ++s) x[s] = m.x0[s];
+  std::vector<double> a(m.M), prefix(m.M), I(m.M, 0.0), g(m.M, 0.0);
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t words[4] = {0, 0, 0, 0};
+  double t = 0.0;
+  int64_t n = 0;
+  int k = 0;
+  auto emit_until = [&](double t_next) {
+    while (k < G && grid[k] < t_next) {
+      double u = 0.0;
+      for (int s = 0; s < m.S; ++s) u += w[(size_t)k * m.S + s] * ((double)x[s] - mu[(size_t)k * m.S + s]);
+      for (int r = 0; r < m.M; ++r) {
+        const double Z = (double)nfire[r] / m.c[r] - (I[r] + (double)h[r] * (grid[k] - t));
+        g[r] += u * Z;
+      }
+      ++k;
+    }
+  };
+  for (;;) {
+    for (int j = 0; j < m.M; ++j) {
+      h[j] = mass_action_h(m, j, x);
+      a[j] = m.c[j] * (double)h[j];
+    }
+    double a0 = 0.0;
+    if (schedule == 0) {
+      for (int j = 0; j < m.M; ++j) { a0 = (j == 0) ? a[0] : a0 + a[j]; prefix[j] = a0; }
+    } else {
+      w32_prefix(a, m.M, prefix, &a0);
+    }
+    const uint32_t ctr[4] = {(uint32_t)n, (uint32_t)traj_id, (uint32_t)(traj_id >> 32), (uint32_t)stream};
+    philox4x32_10(ctr, key, words);
+    double t_next;
+    if (a0 > 0.0) {
+      double E = neg_log_u(odd53(words[0], words[1]));
+      t_next = t + E / a0;
+    } else {
+      t_next = std::numeric_limits<double>::infinity();
+    }
+    emit_until(t_next);
+    if (t_next > t_end) break;
+    const double target = ((double)odd53(words[2], words[3]) * 0x1p-53) * a0;
+    const int jsel = select_reaction(a, prefix, m.M, target);
+    bool over = false;
+    for (int s = 0; s < m.S; ++s)
+      if (x[s] + m.nu[(size_t)jsel * m.S + s] > kStateLimit) over = true;
+    if (over) break;
+    for (int r = 0; r < m.M; ++r) I[r] += (double)h[r] * (t_next - t);
+    for (int s = 0; s < m.S; ++s) x[s] += m.nu[(size_t)jsel * m.S + s];
+    nfire[jsel] += 1;
+    t = t_next;
+    ++n;
+    if (n == max_events) break;
+  }
+  for (int j = 0; j < m.M; ++j) h[j] = mass_action_h(m, j, x);
+  emit_until(std::numeric_limits<double>::infinity());
+  for (int r = 0; r < m.M; ++r) g_out[r] = g[r];
+}
+
 bool build_model(int S, int M, const int32_t* R, const int32_t* P, const double* c,
                  const int32_t* x0, Model* m) {
   if (S <= 0 || M <= 0) return false;
@@ -497,6 +568,24 @@ int oracle_select(int M, const double* a, int schedule, double target) {
     w32_prefix(av, M, pv, &a0);
   }
   return select_reaction(av, pv, M, target);
+}
+
+// Per-trajectory likelihood-ratio contributions g[i][r] (run_one_grad) of
+// trajectories [traj_begin, traj_end), FP64 mode; w, mu are G x S.  The
+// gradient of L is the mean of g over trajectories.  Returns 0, or -1 on bad
+// arguments (including a zero rate: the score needs c_r > 0).
+int oracle_grad(int S, int M, const int32_t* R, const int32_t* P, const double* c, const int32_t* x0,
+                int64_t traj_begin, int64_t traj_end, double t_end, int G, const double* grid, uint64_t seed,
+                uint64_t stream, int64_t max_events, int schedule, const double* w, const double* mu, double* g) {
+  if (!g_log.ready || traj_end < traj_begin || G < 1 || (schedule != 0 && schedule != 1)) return -1;
+  Model m;
+  if (!build_model(S, M, R, P, c, x0, &m)) return -1;
+  for (int r = 0; r < M; ++r)
+    if (!(c[r] > 0.0)) return -1;
+  for (int64_t id = traj_begin; id < traj_end; ++id)
+    run_one_grad(m, (uint64_t)id, t_end, G, grid, seed, stream, max_events, schedule, w, mu,
+                 g + (size_t)(id - traj_begin) * M);
+  return 0;
 }
 
 // mean = S1 / N; var = (N S2 - S1^2) / (N (N - 1)), numerator exact in int128
