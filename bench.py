@@ -53,6 +53,9 @@ WORKLOADS = {
     "random": {"factory": "workload_random", "name": "random_S32_M128_G1001_T10_netseed3", "n_traj": 262144,
                "steps": 10, "e2e_steps": 3, "cpu_sample": 2048, "ref_sample": 512,
                "kernel": "k_ssa_warp", "dram_bytes": None},
+    "grad": {"factory": "workload_hiv_shaped", "name": "hiv_shaped_grad_S4_M10_G3001_T30_loss_V", "n_traj": 1048576,
+             "steps": 5, "e2e_steps": 2, "cpu_sample": 2048, "ref_sample": 1024,
+             "kernel": "k_ssa_grad", "dram_bytes": None},
     "batch": {"factory": None, "name": "batch256_S4-64_M8-512_N1024-65536_G501_T10_fp32", "n_traj": None,
               "steps": 2, "e2e_steps": 1, "cpu_sample": 64, "ref_sample": 16,
               "kernel": "k_ssa_batch", "dram_bytes": None},
@@ -94,8 +97,8 @@ def parse_args():
     spec = WORKLOADS[args.workload]
     args.steps = spec["steps"] if args.steps is None else args.steps
     args.n_traj = spec["n_traj"] if args.n_traj is None else args.n_traj
-    if args.workload == "batch" and args.impl == "reference":
-        p.error("--impl reference times single-network workloads")
+    if args.workload in ("batch", "grad") and args.impl == "reference":
+        p.error("--impl reference times the forward single-network workloads")
     args.e2e_steps = spec["e2e_steps"] if args.e2e_steps is None else args.e2e_steps
     return args
 
@@ -426,6 +429,144 @@ def compare_with_fp64(args, ssa, torch, model, w, n, run_step, totals, stream, f
     return same_gpu, report
 
 
+def run_grad(args):
+    """Rate sensitivities on the HIV-shaped model: one step is the forward
+    ensemble (1,048,576 trajectories, 3001-point grid), the loss
+    sum_g (mean V(g) - target_g)^2 and its likelihood-ratio gradient for all
+    ten rates, the trajectories replayed from their Philox counters."""
+    import numpy as np
+    import torch
+
+    import paper_1007_1768_gb300 as ssa
+    import workloads as W
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    spec = WORKLOADS["grad"]
+    n = args.n_traj
+    w = W.workload_hiv_shaped(n)
+    model = ssa.Model.from_network(w.net)
+    G, S, M = w.n_grid, w.net.n_species, w.net.n_reactions
+    target = torch.as_tensor(W.hiv_target_v(), device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    kb = torch.cuda.Event(enable_timing=True)
+    ke = torch.cuda.Event(enable_timing=True)
+
+    def step(seed, timed=False):
+        r = ssa.ensemble_run(model, n, w.t_end, G, seed, device=dev, want_sums=False, traj_offset=rank * n)
+        wgt = torch.zeros((G, S), dtype=torch.float64, device=dev)
+        wgt[:, 2] = 2.0 * (r.mean[:, 2] - target)
+        opt = {}
+        if timed:
+            opt = {"sim_event_begin": kb.cuda_event, "sim_event_end": ke.cuda_event}
+        g, se, _ = ssa.ensemble_grad(model, n, w.t_end, G, seed, wgt, r.mean, device=dev, traj_offset=rank * n,
+                                     **opt)
+        return r.events, g, se
+
+    for i in range(args.warmup):
+        step(1 + i)
+    torch.cuda.synchronize()
+    K = args.steps
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    kb.record(stream)
+    ke.record(stream)
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    events = 0
+    grad_ms = []
+    last = None
+    for i in range(K):
+        flush.fill_(i & 0xFF)
+        ev_s[i].record(stream)
+        ev, g, se = step(1000 + i, timed=True)
+        ev_e[i].record(stream)
+        torch.cuda.synchronize()
+        grad_ms.append(kb.elapsed_time(ke))
+        events += 2 * ev  # forward events and the same events replayed
+        last = (g, se)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = sum(ev_s[i].elapsed_time(ev_e[i]) for i in range(K))
+    if pg:
+        t = torch.tensor([total_ms, float(events)], dtype=torch.float64)
+        mx = t.clone()
+        pg.all_reduce(mx, op=pg.ReduceOp.MAX)
+        sm = t.clone()
+        pg.all_reduce(sm, op=pg.ReduceOp.SUM)
+        total_ms, events_all = float(mx[0]), float(sm[1])
+    else:
+        events_all = float(events)
+    value = events_all / (total_ms * 1e-3)
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    peak = FP64_OPS_PER_SM_CLK * SMS_GB300 * sm_mhz * 1e6 * 1e-9
+    kern = statistics.mean(grad_ms)
+    ops_bwd = (4 * M + 2) * (events / 2 / K)
+    achieved = ops_bwd / (kern * 1e-3) * 1e-9
+    if rank == 0:
+        t0 = time.perf_counter()
+        e_ev = 0
+        for i in range(args.e2e_steps):
+            rates = torch.tensor(w.net.rates, dtype=torch.float64, requires_grad=True)
+            from paper_1007_1768_gb300.autograd import ssa_ensemble
+            mean, _ = ssa_ensemble(rates, w.net, n, w.t_end, G, 7000 + i, device=dev)
+            loss = ((mean[:, 2] - target) ** 2).sum()
+            loss.backward()
+            _ = rates.grad.numpy().copy()
+            e_ev += 2 * int(ssa_events_estimate(events, K))
+        e_dt = time.perf_counter() - t0
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_baseline(w, min(n, spec["cpu_sample"]))
+        g, se = last
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": spec["name"], "n_traj_per_gpu": n, "n_grid": G, "t_end": w.t_end,
+                       "precision": "fp64-exact", "loss": "sum_g (mean V(g) - target_g)^2, target file",
+                       "events": "forward events + the same events replayed in the backward pass",
+                       "l2": "flushed between timed steps (256 MiB write outside the step events)",
+                       "parallelism": f"replicas x{world} (trajectory-id shards)"},
+            "traj_per_s": world * n / (total_ms * 1e-3 / K),
+            "grad_kernel_ms": kern,
+            "grad_last_step": [float(v) for v in g.cpu().numpy()],
+            "grad_se_last_step": [float(v) for v in se.cpu().numpy()],
+            "roofline": {"bound": "alu", "kernel": spec["kernel"], "achieved": achieved, "peak": peak,
+                         "unit": "GFLOP/s (FP64 ops)", "frac": achieved / peak, "traffic": None,
+                         "ops_per_event": 4 * M + 2,
+                         "peak_basis": "2 FP64 ops/clk/SM x 152 SMs x median SM clock"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e_ev / e_dt, "unit": UNIT, "h2d_bytes_per_step": int(8 * M),
+                    "d2h_bytes_per_step": int(8 * M), "steps": args.e2e_steps,
+                    "note": "torch autograd: rates in, loss.backward(), rates.grad read back; events as timed"},
+            "gpu_launches": K * 7,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    model.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def ssa_events_estimate(events_total, steps):
+    """Forward events of one step (mean over the timed steps)."""
+    return events_total / 2 / steps
+
+
 def run_batch(args):
     """The uneven batch of 256 random networks in one graph replay per step
     (FP32 propensities, FP64 time): persistent kernels per register bucket,
@@ -620,6 +761,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "grad":
+        return run_grad(args)
     return run_ours(args)
 
 

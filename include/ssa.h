@@ -198,6 +198,30 @@ ssa_status ssa_ensemble_run(const ssa_model* model, int64_t n_traj, double t_end
                             ssa_run_stats* stats);
 
 /*
+ * ssa_ensemble_grad -- likelihood-ratio sensitivities of a loss on the grid
+ * mean with respect to the rate constants (FP64, thread schedule: networks of
+ * at most 16 reactions and 16 species, every rate > 0).
+ *
+ * The trajectories of ssa_ensemble_run with the same model, n_traj, t_end,
+ * grid, seed and opts are replayed from their Philox counters (nothing of the
+ * forward pass is stored).  For reaction r the score of a path is
+ *   Z_r(t) = N_r(t) / c_r - int_0^t h_r(x(s)) ds
+ * (N_r: firings of r up to t), and trajectory i contributes
+ *   g_ir = sum_k u_k Z_r(g_k),  u_k = sum_s dL_dmean[k][s] (x_is(g_k) - mean[k][s]).
+ *   dL_drates[r]    = (1/N) sum_i g_ir
+ *   dL_drates_se[r] = sample standard deviation of g_ir / sqrt(N)   (may be NULL)
+ * dL_dmean, mean [G x S] and the outputs [M] live in opts->memory's space.
+ * opts->workspace, when non-NULL, receives the per-trajectory contributions
+ * g (M x N, column r at r * N, same memory space; workspace_bytes >= 8 M N).
+ * Host memory: synchronous.  Device memory: enqueued on opts->cuda_stream.
+ * Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA, SSA_EUNSUPPORTED (FP32 mode, the
+ * warp schedule, larger networks, a zero rate).
+ */
+ssa_status ssa_ensemble_grad(const ssa_model* model, int64_t n_traj, double t_end, int32_t n_grid,
+                             const double* grid, uint64_t seed, const ssa_run_opts* opts, const double* dL_dmean,
+                             const double* mean, double* dL_drates, double* dL_drates_se);
+
+/*
  * Size of the fixed device scratch used by ssa_ensemble_run_noalloc: 4 MiB,
  * held by every GPU that loads the library until the process exits.
  */

@@ -29,7 +29,7 @@ EXPORTS = [
     "ssa_status_string", "ssa_last_error", "ssa_run_opts_init", "ssa_model_create", "ssa_model_destroy",
     "ssa_model_info", "ssa_ensemble_workspace_size", "ssa_ensemble_run", "ssa_ensemble_run_noalloc",
     "ssa_batch_create", "ssa_batch_tune", "ssa_batch_launch", "ssa_batch_result", "ssa_batch_network_stats",
-    "ssa_batch_destroy", "ssa_batch_run",
+    "ssa_batch_destroy", "ssa_batch_run", "ssa_ensemble_grad",
 ]
 
 
@@ -107,6 +107,8 @@ def lib():
         L.ssa_batch_destroy.restype = None
         L.ssa_batch_run.argtypes = [i32, vp, vp, vp, vp, vp, u64, ctypes.POINTER(RunOpts), vp, vp]
         L.ssa_batch_run.restype = ctypes.c_int
+        L.ssa_ensemble_grad.argtypes = [vp, i64, f64, i32, vp, u64, ctypes.POINTER(RunOpts), vp, vp, vp, vp]
+        L.ssa_ensemble_grad.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -249,6 +251,45 @@ def ensemble_run(model: Model, n_traj: int, t_end: float, n_grid: int, seed: int
                                       None if s2 is None else s2.data_ptr(), ctypes.byref(st) if stats else None))
     return EnsembleResult(mean, var, s1, s2, int(st.events), int(st.truncated), int(st.overflowed), int(st.max_x),
                           float(st.kernel_ms), tev, ths, tfl)
+
+
+def ensemble_grad(model: Model, n_traj: int, t_end: float, n_grid: int, seed: int, dL_dmean, mean, grid=None, *,
+                  device=None, per_traj: bool = False, **opt_kw):
+    """ssa_ensemble_grad: (dL/drates [M], standard errors [M], per-trajectory
+    contributions [M, N] or None).  ``device=None``: numpy in and out;
+    a torch device: torch tensors on that device (torch's current stream)."""
+    L = lib()
+    M = model.n_reactions
+    G = int(n_grid if grid is None else len(grid))
+    if device is None:
+        w = np.ascontiguousarray(dL_dmean, dtype=np.float64)
+        mu = np.ascontiguousarray(mean, dtype=np.float64)
+        g = None if grid is None else np.ascontiguousarray(grid, dtype=np.float64)
+        out = np.empty(M)
+        se = np.empty(M)
+        traj = np.empty((M, int(n_traj))) if per_traj else None
+        opts = make_opts(memory=MEM_HOST, workspace=None if traj is None else traj.ctypes.data,
+                         workspace_bytes=0 if traj is None else traj.nbytes, **opt_kw)
+        _check(L.ssa_ensemble_grad(model.handle, int(n_traj), float(t_end), G,
+                                   None if g is None else g.ctypes.data, int(seed), ctypes.byref(opts),
+                                   w.ctypes.data, mu.ctypes.data, out.ctypes.data, se.ctypes.data))
+        return out, se, traj
+    import torch
+    dev = torch.device(device)
+    stream = torch.cuda.current_stream(dev)
+    w = torch.as_tensor(dL_dmean, dtype=torch.float64, device=dev).contiguous()
+    mu = torch.as_tensor(mean, dtype=torch.float64, device=dev).contiguous()
+    g = None if grid is None else torch.as_tensor(grid, dtype=torch.float64, device=dev).contiguous()
+    out = torch.empty(M, dtype=torch.float64, device=dev)
+    se = torch.empty(M, dtype=torch.float64, device=dev)
+    traj = torch.empty((M, int(n_traj)), dtype=torch.float64, device=dev) if per_traj else None
+    opts = make_opts(memory=MEM_DEVICE, cuda_stream=stream.cuda_stream,
+                     workspace=None if traj is None else traj.data_ptr(),
+                     workspace_bytes=0 if traj is None else traj.numel() * 8, **opt_kw)
+    _check(L.ssa_ensemble_grad(model.handle, int(n_traj), float(t_end), G, None if g is None else g.data_ptr(),
+                               int(seed), ctypes.byref(opts), w.data_ptr(), mu.data_ptr(), out.data_ptr(),
+                               se.data_ptr()))
+    return out, se, traj
 
 
 def _ptr_array(ptrs):

@@ -144,6 +144,25 @@ def random_network(seed: int, n_species: int = 32, n_reactions: int = 128,
                    rates.astype(np.float64), x0)
 
 
+def hiv_target_rates(seed: int = 2) -> np.ndarray:
+    """Rates of the HIV-shaped model each scaled by exp(U(-0.2, 0.2)), seeded:
+    the parameters whose ensemble mean of V is the gradient workload's target."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return hiv_shaped().rates * np.exp(rng.uniform(-0.2, 0.2, size=10))
+
+
+HIV_TARGET_FILE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden",
+                               "hiv_target_v.txt")
+
+
+def hiv_target_v() -> np.ndarray:
+    """The gradient workload's target trajectory: mean V(g) on the 3001-point
+    grid of [0, 30] (written by tests/golden/make_hiv_target.py)."""
+    with open(HIV_TARGET_FILE) as f:
+        vals = [float.fromhex(line.split()[0]) for line in f if line.strip() and not line.startswith("#")]
+    return np.array(vals, dtype=np.float64)
+
+
 def workload_birth_death(n_traj: int = 1000) -> Workload:
     """Birth-death, t_end = 100, 1001-point uniform grid, seed 1."""
     return Workload(birth_death(), n_traj, 100.0, 1001, 1)
