@@ -451,7 +451,7 @@ def run_grad(args):
         dist.init_process_group("gloo")
         pg = dist
     spec = WORKLOADS["grad"]
-    n = args.n_traj
+    n = args.n_traj if not args.profile_small else args.profile_n
     w = W.workload_hiv_shaped(n)
     model = ssa.Model.from_network(w.net)
     G, S, M = w.n_grid, w.net.n_species, w.net.n_reactions
@@ -472,6 +472,11 @@ def run_grad(args):
                                      **opt)
         return r.events, g, se
 
+    if args.profile_small:
+        step(1)
+        torch.cuda.synchronize()
+        model.close()
+        return 0
     for i in range(args.warmup):
         step(1 + i)
     torch.cuda.synchronize()

@@ -17,8 +17,13 @@
 // interval contribute
 //   sum_k u_k Z_r(g_k) = B_r U - h_r UG,   U = sum_k u_k,  UG = sum_k u_k g_k,
 // and U, UG come from prefix sums over the grid of w, c = sum_s w m, g w and
-// g c in O(S) per interval.  The oracle states the definition point by point;
-// the two agree up to FP64 rounding order.
+// g c in O(S) per interval.  U and UG are added into running sums SU, SUG;
+// reaction r's gradient takes B_r (SU - SU0_r) - h_r (SUG - SUG0_r) only when
+// B_r or h_r is about to change (r fired or its propensity changed) and at
+// the end, SU0_r / SUG0_r being the running sums at its previous update.
+// B, the gradients and SU0 / SUG0 sit in per-thread shared-memory slots.  The
+// oracle states the definition point by point; the two agree up to FP64
+// rounding order.
 //
 // The trajectory itself is the thread kernel's: FP64 propensities, schedule
 // L prefix sums, the same random numbers, selection and stopping rules.
@@ -73,13 +78,44 @@ __device__ __forceinline__ int grad_grid_index(const GradArgs& a, long long tb, 
   return k;
 }
 
+constexpr int kGradThreads = 128;
+
+// Per-thread score state in shared memory, slot (j, tid) at j * 128 + tid:
+// B_j, the gradient g_j, and the running interval sums at g_j's last update.
+struct GradSlots {
+  double* B;
+  double* g;
+  double* su0;
+  double* sug0;
+};
+
+// g_j += B_j (SU - SU0_j) - h_j (SUG - SUG0_j): the intervals since B_j or h_j
+// last changed, all with the same B_j and h_j.
+__device__ __forceinline__ void flush_slot(const GradSlots& sl, int idx, double hj, double SU, double SUG) {
+  const double inc = __dsub_rn(__dmul_rn(sl.B[idx], __dsub_rn(SU, sl.su0[idx])),
+                               __dmul_rn(hj, __dsub_rn(SUG, sl.sug0[idx])));
+  sl.g[idx] = __dadd_rn(sl.g[idx], inc);
+  sl.su0[idx] = SU;
+  sl.sug0[idx] = SUG;
+}
+
 template <int MAXM, int MAXS>
-__global__ void __launch_bounds__(128) k_ssa_grad(const GradArgs a) {
-  __shared__ uint64_t s_inv[kLogCells], s_lnf[kLogCells];
-  for (int i = threadIdx.x; i < kLogCells; i += blockDim.x) {
+__global__ void __launch_bounds__(kGradThreads) k_ssa_grad(const GradArgs a) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  uint64_t* s_inv = reinterpret_cast<uint64_t*>(gsm);
+  uint64_t* s_lnf = s_inv + kLogCells;
+  double* slots = reinterpret_cast<double*>(s_lnf + kLogCells);
+  const int T = kGradThreads, tid = threadIdx.x;
+  GradSlots sl{slots, slots + MAXM * T, slots + 2 * MAXM * T, slots + 3 * MAXM * T};
+  // rows read with the fired reaction's index: net changes and dependency masks
+  int32_t* s_nu = reinterpret_cast<int32_t*>(slots + 4 * MAXM * T);  // [MAXM][MAXS]
+  uint32_t* s_dep = reinterpret_cast<uint32_t*>(s_nu + MAXM * MAXS);  // [MAXM]
+  for (int i = tid; i < kLogCells; i += T) {
     s_inv[i] = d_log_tables.inv[i];
     s_lnf[i] = d_log_tables.lnf[i];
   }
+  for (int i = tid; i < MAXM * MAXS; i += T) s_nu[i] = a.sm.nu[(i / MAXS) * kSmallMax + (i % MAXS)];
+  for (int j = tid; j < MAXM; j += T) s_dep[j] = a.sm.depmask[j];
   __syncthreads();
   const int S = a.S, M = a.M, G = a.G;
   const uint32_t key0 = (uint32_t)a.seed, key1 = (uint32_t)(a.seed >> 32), sid = (uint32_t)a.stream_id;
@@ -91,30 +127,44 @@ __global__ void __launch_bounds__(128) k_ssa_grad(const GradArgs a) {
 #pragma unroll
     for (int s = 0; s < MAXS; ++s) x[s] = (s < S) ? a.sm.x0[s] : 0;
     long long h[MAXM];
-    double av[MAXM], B[MAXM], gacc[MAXM];
+    double av[MAXM];
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) {
       h[j] = 0;
       av[j] = 0.0;
-      B[j] = 0.0;
-      gacc[j] = 0.0;
+      sl.B[j * T + tid] = 0.0;
+      sl.g[j * T + tid] = 0.0;
+      sl.su0[j * T + tid] = 0.0;
+      sl.sug0[j * T + tid] = 0.0;
     }
-    uint32_t dirty = (M >= 32) ? 0xFFFFFFFFu : ((1u << M) - 1u);
+    double SU = 0.0, SUG = 0.0;  // running sums of U and UG over the intervals so far
+    uint32_t dirty = (1u << M) - 1u;
+    int fired = -1;
     double t = 0.0;
     uint32_t n = 0;
     int k = 0;
     bool done = false;
-    while (!done) {
-      // propensities the last event changed; B_r follows h_r's jump at time t
+    for (;;) {
+      // the event at t: flush the score of the fired reaction and of every
+      // reaction whose propensity it changed, then update B and h
 #pragma unroll
       for (int j = 0; j < MAXM; ++j) {
-        if (j < M && ((dirty >> j) & 1u)) {
-          const long long hn = mass_action_h<MAXS>(a.sm.rinfo[j], x);
-          B[j] = __dadd_rn(B[j], __dmul_rn(__ll2double_rn(hn - h[j]), t));
-          h[j] = hn;
-          av[j] = __longlong_as_double((long long)propensity_fp64(a.sm.cbits[j], hn));
+        const bool dj = j < M && ((dirty >> j) & 1u);
+        if (dj || j == fired) {
+          const int idx = j * T + tid;
+          flush_slot(sl, idx, __ll2double_rn(h[j]), SU, SUG);
+          double Bj = sl.B[idx];
+          if (j == fired) Bj = __dadd_rn(Bj, a.invc[j]);
+          if (dj) {
+            const long long hn = mass_action_h<MAXS>(a.sm.rinfo[j], x);
+            Bj = __dadd_rn(Bj, __dmul_rn(__ll2double_rn(hn - h[j]), t));
+            h[j] = hn;
+            av[j] = __longlong_as_double((long long)propensity_fp64(a.sm.cbits[j], hn));
+          }
+          sl.B[idx] = Bj;
         }
       }
+      if (done) break;
       // schedule L prefix sums
       double pre[MAXM];
       pre[0] = av[0];
@@ -124,7 +174,7 @@ __global__ void __launch_bounds__(128) k_ssa_grad(const GradArgs a) {
       const EventRandom r = event_random(n, traj_id, sid, key0, key1, s_inv, s_lnf);
       const double t_next = __dadd_rn(t, quotient(r.E, a0));  // a0 == 0: +inf
       const long long tb = obits(t_next);
-      // grid points g_k < t_next see the current state: B_r U - h_r UG
+      // grid points g_k < t_next see the current state: U and UG of the interval
       const int k2 = grad_grid_index(a, tb, k);
       if (k2 > k) {
         double U = __dsub_rn(a.Pc[k], a.Pc[k2]), UG = __dsub_rn(a.Pgc[k], a.Pgc[k2]);
@@ -136,9 +186,8 @@ __global__ void __launch_bounds__(128) k_ssa_grad(const GradArgs a) {
             UG = __dadd_rn(UG, __dmul_rn(xd, __dsub_rn(a.Pgw[(size_t)k2 * S + s], a.Pgw[(size_t)k * S + s])));
           }
         }
-#pragma unroll
-        for (int j = 0; j < MAXM; ++j)
-          if (j < M) gacc[j] = __dadd_rn(gacc[j], __dsub_rn(__dmul_rn(B[j], U), __dmul_rn(__ll2double_rn(h[j]), UG)));
+        SU = __dadd_rn(SU, U);
+        SUG = __dadd_rn(SUG, UG);
         k = k2;
       }
       if (tb > obits(a.t_end)) break;
@@ -156,31 +205,19 @@ __global__ void __launch_bounds__(128) k_ssa_grad(const GradArgs a) {
       bool over = false;
 #pragma unroll
       for (int s = 0; s < MAXS; ++s)
-        if (s < S) over |= (long long)x[s] + (long long)a.sm.nu[jsel * kSmallMax + s] > kStateMax;
+        if (s < S) over |= (long long)x[s] + (long long)s_nu[jsel * MAXS + s] > kStateMax;
       if (over) break;  // the state stays; later grid points see it
 #pragma unroll
       for (int s = 0; s < MAXS; ++s)
-        if (s < S) x[s] += a.sm.nu[jsel * kSmallMax + s];
-#pragma unroll
-      for (int j = 0; j < MAXM; ++j)
-        if (j == jsel) B[j] = __dadd_rn(B[j], a.invc[j]);
-      dirty = a.sm.depmask[jsel];
+        if (s < S) x[s] += s_nu[jsel * MAXS + s];
+      dirty = s_dep[jsel];
+      fired = jsel;
       t = t_next;
       ++n;
-      if ((long long)n == a.max_events) done = true;
+      if ((long long)n == a.max_events) done = true;  // flush this event, then stop
     }
+    // every later grid point sees the final state
     if (k < G) {
-      // truncated: h follows the last event; every later grid point sees this state
-      if (done) {
-#pragma unroll
-        for (int j = 0; j < MAXM; ++j) {
-          if (j < M && ((dirty >> j) & 1u)) {
-            const long long hn = mass_action_h<MAXS>(a.sm.rinfo[j], x);
-            B[j] = __dadd_rn(B[j], __dmul_rn(__ll2double_rn(hn - h[j]), t));
-            h[j] = hn;
-          }
-        }
-      }
       double U = __dsub_rn(a.Pc[k], a.Pc[G]), UG = __dsub_rn(a.Pgc[k], a.Pgc[G]);
 #pragma unroll
       for (int s = 0; s < MAXS; ++s) {
@@ -190,13 +227,17 @@ __global__ void __launch_bounds__(128) k_ssa_grad(const GradArgs a) {
           UG = __dadd_rn(UG, __dmul_rn(xd, __dsub_rn(a.Pgw[(size_t)G * S + s], a.Pgw[(size_t)k * S + s])));
         }
       }
-#pragma unroll
-      for (int j = 0; j < MAXM; ++j)
-        if (j < M) gacc[j] = __dadd_rn(gacc[j], __dsub_rn(__dmul_rn(B[j], U), __dmul_rn(__ll2double_rn(h[j]), UG)));
+      SU = __dadd_rn(SU, U);
+      SUG = __dadd_rn(SUG, UG);
     }
 #pragma unroll
-    for (int j = 0; j < MAXM; ++j)
-      if (j < M) a.gtraj[(size_t)j * a.N + li] = gacc[j];
+    for (int j = 0; j < MAXM; ++j) {
+      if (j < M) {
+        const int idx = j * T + tid;
+        flush_slot(sl, idx, __ll2double_rn(h[j]), SU, SUG);
+        a.gtraj[(size_t)j * a.N + li] = sl.g[idx];
+      }
+    }
   }
 }
 
@@ -267,7 +308,11 @@ __global__ void __launch_bounds__(1024) k_grad_reduce(const double* gtraj, long 
 
 template <int MAXM, int MAXS>
 cudaError_t launch_grad_t(const GradArgs& a, int blocks, cudaStream_t st) {
-  k_ssa_grad<MAXM, MAXS><<<blocks, 128, 0, st>>>(a);
+  const size_t smem = (size_t)kLogCells * 16 + (size_t)4 * MAXM * kGradThreads * 8 + (size_t)MAXM * MAXS * 4 +
+                      (size_t)MAXM * 4;
+  cudaError_t e = cudaFuncSetAttribute(k_ssa_grad<MAXM, MAXS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_ssa_grad<MAXM, MAXS><<<blocks, kGradThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
