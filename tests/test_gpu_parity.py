@@ -178,3 +178,19 @@ def test_repeatable_and_seed_sensitive():
     c = _gpu(net, 1000, 30.0, 301, 8)
     assert np.array_equal(a["sum2"], b["sum2"]) and np.array_equal(a["traj_hash"], b["traj_hash"])
     assert not np.array_equal(a["sum2"], c["sum2"])
+
+
+def test_shards_finalised_on_the_host_match_one_run():
+    from paper_1007_1768_gb300.shards import finalize_sums, shard_range
+    net = W.hiv_shaped()
+    n, world = 3001, 3
+    s1 = s2 = 0
+    for rank in range(world):
+        off, cnt = shard_range(n, rank, world)
+        g = _gpu(net, cnt, 30.0, 301, 12, device=False, traj_offset=off)
+        s1, s2 = s1 + g["sum1"], s2 + g["sum2"]
+    full = _gpu(net, n, 30.0, 301, 12, device=False)
+    assert np.array_equal(s1, full["sum1"]) and np.array_equal(s2, full["sum2"])
+    mean, var = finalize_sums(s1, s2, n)
+    assert np.array_equal(mean.view(np.int64), full["mean"].view(np.int64))
+    assert np.array_equal(var.view(np.int64), full["var"].view(np.int64))
