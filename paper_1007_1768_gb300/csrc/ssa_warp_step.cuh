@@ -162,10 +162,15 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
         const long long bi = xa * ((kind == kBi) ? xb : (xa - 1));
         const long long h =
             (kind == kOrder0) ? 1LL : ((kind == kUni) ? xa : ((kind == kBi) ? bi : (bi >> 1)));
-        if constexpr (F32)
+        // products on the FP32 pipe (FP32 mode) or as exact integer
+        // arithmetic (FP64 mode: the SM's FP64 unit binds the warp kernel)
+        if constexpr (F32) {
           af[q] = __fmul_rn(net.c32[j], __ll2float_rn(h));
-        else
-          av[q] = __longlong_as_double((long long)propensity_fp64(net.cbits[j], h));
+        } else {
+          unsigned long long ab;
+          if (!propensity_int(net.cbits[j], h, ab)) ab = propensity_fp64(net.cbits[j], h);
+          av[q] = __longlong_as_double((long long)ab);
+        }
       }
     }
     // schedule W32: running sums inside the chunk, Kogge-Stone scan of the
