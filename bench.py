@@ -50,15 +50,17 @@ WORKLOADS = {
     "hiv_shaped": {"factory": "workload_hiv_shaped", "name": "hiv_shaped_S4_M10_G3001_T30", "n_traj": 65536,
                    "steps": 100, "e2e_steps": 20, "cpu_sample": 16384, "ref_sample": 4096,
                    "kernel": "k_ssa_thread", "dram_bytes": SIM_KERNEL_DRAM_BYTES},
+    # DRAM bytes per launch of the simulation kernel from the ncu captures in
+    # profiles/ (model tables and grid; independent of the trajectory count)
     "random": {"factory": "workload_random", "name": "random_S32_M128_G1001_T10_netseed3", "n_traj": 262144,
                "steps": 10, "e2e_steps": 3, "cpu_sample": 2048, "ref_sample": 512,
-               "kernel": "k_ssa_warp", "dram_bytes": None},
+               "kernel": "k_ssa_warp", "dram_bytes": {"fp64": 592128, "fp32": 588032}},
     "grad": {"factory": "workload_hiv_shaped", "name": "hiv_shaped_grad_S4_M10_G3001_T30_loss_V", "n_traj": 1048576,
              "steps": 5, "e2e_steps": 2, "cpu_sample": 2048, "ref_sample": 1024,
-             "kernel": "k_ssa_grad", "dram_bytes": None},
+             "kernel": "k_ssa_grad", "dram_bytes": 336896},
     "batch": {"factory": None, "name": "batch256_S4-64_M8-512_N1024-65536_G501_T10_fp32", "n_traj": None,
-              "steps": 2, "e2e_steps": 1, "cpu_sample": 64, "ref_sample": 16,
-              "kernel": "k_ssa_batch", "dram_bytes": None},
+              "steps": 2, "e2e_steps": 1, "cpu_sample": 16, "ref_sample": 16,
+              "kernel": "k_ssa_batch", "dram_bytes": 4043520},
 }
 FP64_OPS_PER_SM_CLK = 2.0  # 1.25 TFLOP/s dense FP64 (FMA = 2 flops) / (152 SMs * 2.07 GHz)
 
@@ -172,12 +174,23 @@ def fp64_ops_per_event(n_reactions: int) -> int:
     return 2 * n_reactions + 2
 
 
-def cpu_baseline(w, n_traj_sample: int):
+def oracle_mode(args):
+    """(schedule, precision) of the oracle matching the GPU run: the warp
+    layout's W32 order for the random network, FP32 when asked."""
+    import oracle
+    schedule = oracle.SCHEDULE_W32 if args.workload == "random" else oracle.SCHEDULE_L
+    precision = oracle.PRECISION_FP32 if getattr(args, "precision", "fp64") == "fp32" else oracle.PRECISION_FP64
+    return schedule, precision
+
+
+def cpu_baseline(w, n_traj_sample: int, args=None):
     """The oracle as it stands, on all host cores (one thread per id range)."""
     import oracle
     cores = os.cpu_count() or 1
+    schedule, precision = oracle_mode(args) if args is not None else (oracle.SCHEDULE_L, oracle.PRECISION_FP64)
     t0 = time.perf_counter()
-    r = oracle.run(w.net, n_traj_sample, w.t_end, w.n_grid, w.seed, threads=cores)
+    r = oracle.run(w.net, n_traj_sample, w.t_end, w.n_grid, w.seed, threads=cores, schedule=schedule,
+                   precision=precision)
     dt = time.perf_counter() - t0
     return {"value": r.events / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"trajectories 0..{n_traj_sample - 1} of the workload (seed {w.seed}), "
@@ -194,12 +207,14 @@ def run_reference(args):
     oracle.lib()
     cores = os.cpu_count() or 1
     sample = min(args.n_traj, spec["ref_sample"])
+    schedule, precision = oracle_mode(args)
     for i in range(args.warmup):
-        oracle.run(w.net, sample, w.t_end, w.n_grid, 1 + i, threads=cores)
+        oracle.run(w.net, sample, w.t_end, w.n_grid, 1 + i, threads=cores, schedule=schedule, precision=precision)
     events = 0
     t0 = time.perf_counter()
     for i in range(args.steps):
-        r = oracle.run(w.net, sample, w.t_end, w.n_grid, 1000 + i, threads=cores)
+        r = oracle.run(w.net, sample, w.t_end, w.n_grid, 1000 + i, threads=cores, schedule=schedule,
+                       precision=precision)
         events += r.events
     dt = time.perf_counter() - t0
     value = events / dt
@@ -208,7 +223,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": spec["name"], "n_traj": args.n_traj, "n_grid": w.n_grid,
-                   "t_end": w.t_end, "precision": "fp64", "sample_per_step": sample},
+                   "t_end": w.t_end, "precision": args.precision, "sample_per_step": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{sample} trajectories per step (seeds 1000..), {cores} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -338,7 +353,7 @@ def run_ours(args):
         e_dt = time.perf_counter() - t0
         e2e = {"value": e_ev / e_dt, "unit": UNIT, "h2d_bytes_per_step": int(grid_h.nbytes),
                "d2h_bytes_per_step": int(2 * G * S * 8 + 8 * 8), "steps": args.e2e_steps}
-        cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(w, min(n, spec["cpu_sample"]))
+        cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(w, min(n, spec["cpu_sample"]), args)
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -353,7 +368,9 @@ def run_ours(args):
             "events_per_step": events_all / K,
             "wall_s_timed_region": wall,
             "roofline": {"bound": "alu", "kernel": spec["kernel"], "achieved": achieved, "peak": peak,
-                         "unit": "GFLOP/s (FP64 ops)", "frac": achieved / peak, "traffic": spec["dram_bytes"],
+                         "unit": "GFLOP/s (FP64 ops)", "frac": achieved / peak,
+                         "traffic": (spec["dram_bytes"][args.precision] if isinstance(spec["dram_bytes"], dict)
+                                     else spec["dram_bytes"]),
                          "kernel_ms": kern_avg, "ops_per_event": fp64_ops_per_event(M),
                          "peak_basis": "2 FP64 ops/clk/SM x 152 SMs x median SM clock (nominal 1.25 TFLOP/s dense)"},
             "cpu_baseline": cpu,
@@ -550,7 +567,7 @@ def run_grad(args):
             "grad_last_step": [float(v) for v in g.cpu().numpy()],
             "grad_se_last_step": [float(v) for v in se.cpu().numpy()],
             "roofline": {"bound": "alu", "kernel": spec["kernel"], "achieved": achieved, "peak": peak,
-                         "unit": "GFLOP/s (FP64 ops)", "frac": achieved / peak, "traffic": None,
+                         "unit": "GFLOP/s (FP64 ops)", "frac": achieved / peak, "traffic": spec["dram_bytes"],
                          "ops_per_event": 4 * M + 2,
                          "peak_basis": "2 FP64 ops/clk/SM x 152 SMs x median SM clock"},
             "cpu_baseline": cpu,
@@ -679,7 +696,7 @@ def run_batch(args):
             "traj_per_s": world * sum(n_traj) / (total_ms * 1e-3 / K),
             "events_per_step": events_all / K,
             "roofline": {"bound": "alu", "kernel": spec["kernel"], "achieved": achieved, "peak": peak,
-                         "unit": "GFLOP/s (FP64 ops)", "frac": achieved / peak, "traffic": None,
+                         "unit": "GFLOP/s (FP64 ops)", "frac": achieved / peak, "traffic": spec["dram_bytes"],
                          "ops_per_event": "M_b + 2 (FP64 re-summation of a0, r2 * A32, quotient, t add)",
                          "peak_basis": "2 FP64 ops/clk/SM x 152 SMs x median SM clock"},
             "cpu_baseline": cpu,
