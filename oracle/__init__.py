@@ -146,6 +146,9 @@ def lib():
         L.oracle_grad.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, i64, i64, f64, ctypes.c_int, vp,
                                   u64, u64, i64, ctypes.c_int, vp, vp, vp]
         L.oracle_grad.restype = ctypes.c_int
+        L.oracle_avg_xy.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, i64, i64, f64, u64, u64, i64,
+                                    ctypes.c_int, ctypes.c_int, i64, i64, vp, vp, vp, vp, vp]
+        L.oracle_avg_xy.restype = ctypes.c_int
         L.oracle_select.argtypes = [ctypes.c_int, vp, ctypes.c_int, f64]
         L.oracle_select.restype = ctypes.c_int
         L.oracle_prefix.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, vp]
@@ -338,6 +341,36 @@ def grad(net, n_traj: int, t_end: float, n_grid: int, seed: int, dL_dmean, mean,
         for i in range(len(spans)):
             work(i)
     return out
+
+
+def avg_xy(net, n_traj: int, t_end: float, seed: int, window: int, traj_begin: int = 0, stream: int = 0,
+           max_events: int = MAX_EVENTS, schedule: int = SCHEDULE_W32, precision: int = PRECISION_FP64,
+           max_points: int = None):
+    """Selective memory along time: (t [P], mean [P, S], mean of x^2 [P, S],
+    number of union points U).  Window p averages union points
+    [p window, (p + 1) window) of the Avg-Y curve; window 1 returns Avg-Y
+    itself (t = the union of event times with 0)."""
+    L = lib()
+    R, P, c, x0 = _model_arrays(net)
+    S, M = net.n_species, net.n_reactions
+    cap = int(max_points) if max_points is not None else 0
+    npts = np.zeros(1, dtype=np.int64)
+    nu = np.zeros(1, dtype=np.int64)
+    for attempt in range(2):
+        t = np.zeros(max(cap, 1))
+        mean = np.zeros((max(cap, 1), S))
+        msq = np.zeros((max(cap, 1), S))
+        rc = L.oracle_avg_xy(S, M, R.ctypes.data, P.ctypes.data, c.ctypes.data, x0.ctypes.data, int(traj_begin),
+                             int(n_traj), float(t_end), int(seed), int(stream), int(max_events), int(schedule),
+                             int(precision), int(window), cap, t.ctypes.data, mean.ctypes.data, msq.ctypes.data,
+                             npts.ctypes.data, nu.ctypes.data)
+        if rc != 0:
+            raise ValueError("oracle_avg_xy rejected its arguments")
+        if cap >= npts[0] or max_points is not None:
+            break
+        cap = int(npts[0])
+    n = int(min(npts[0], cap))
+    return t[:n], mean[:n], msq[:n], int(nu[0])
 
 
 def select(a, target: float, schedule: int = SCHEDULE_L) -> int:

@@ -543,6 +543,82 @@ int oracle_trace(int S, int M, const int32_t* R, const int32_t* P, const double*
   return r.flags;
 }
 
+// Selective memory along the time axis (Sec. 3.2.1, Fig. 3), for
+// trajectories [traj_begin, traj_begin + N):
+//   Avg-Y: the union of every trajectory's event times, with t = 0, gives
+//     points T_0 = 0 < T_1 < ... < T_{U-1}; at each, S1_m[s] = sum_i x_is(T_m)
+//     and S2_m[s] = sum_i x_is(T_m)^2 (right-continuous states; int64);
+//   Avg-XY: window p covers union points [p k, min(U, (p + 1) k)) of size n_p;
+//     t_p = (T_a + ... + T_{b-1}) / n_p (FP64, ascending order), and
+//     mean_p[s] = (double)(sum_m S1_m[s]) / (double)(N n_p),
+//     msq_p[s]  = (double)(sum_m S2_m[s]) / (double)(N n_p).
+// Writes min(P, max_points) points (P = ceil(U / k)); *n_points = P and
+// *n_union = U.  Returns 0, or -1 on bad arguments.
+int oracle_avg_xy(int S, int M, const int32_t* R, const int32_t* P, const double* c, const int32_t* x0,
+                  int64_t traj_begin, int64_t N, double t_end, uint64_t seed, uint64_t stream, int64_t max_events,
+                  int schedule, int precision, int64_t window, int64_t max_points, double* t_out, double* mean_out,
+                  double* msq_out, int64_t* n_points, int64_t* n_union) {
+  if (!g_log.ready || N < 1 || window < 1 || (schedule != 0 && schedule != 1) || (precision != 0 && precision != 1))
+    return -1;
+  Model m;
+  if (!build_model(S, M, R, P, c, x0, &m)) return -1;
+  // every trajectory's event list (a grid beyond t_end: no grid point is emitted)
+  const double no_grid[1] = {std::numeric_limits<double>::infinity()};
+  std::vector<std::vector<double>> times(N);
+  std::vector<std::vector<int32_t>> rxn(N);
+  std::vector<uint64_t> d1(S, 0), d2(S, 0);
+  std::vector<double> all;
+  for (int64_t i = 0; i < N; ++i) {
+    const uint64_t id = (uint64_t)(traj_begin + i);
+    TrajResult r = run_one(m, id, t_end, 1, no_grid, seed, stream, max_events, schedule, precision, d1.data(),
+                           d2.data(), nullptr, nullptr, 0, nullptr, nullptr);
+    times[i].resize(r.events);
+    rxn[i].resize(r.events);
+    run_one(m, id, t_end, 1, no_grid, seed, stream, max_events, schedule, precision, d1.data(), d2.data(),
+            nullptr, nullptr, (int)r.events, times[i].data(), rxn[i].data());
+    all.insert(all.end(), times[i].begin(), times[i].end());
+  }
+  std::sort(all.begin(), all.end());
+  std::vector<double> T(1, 0.0);
+  for (double v : all)
+    if (v != T.back()) T.push_back(v);
+  const int64_t U = (int64_t)T.size();
+  std::vector<int64_t> S1((size_t)U * S, 0), S2((size_t)U * S, 0);
+  for (int64_t i = 0; i < N; ++i) {
+    std::vector<int64_t> x(m.x0.begin(), m.x0.end());
+    size_t e = 0;
+    for (int64_t q = 0; q < U; ++q) {
+      while (e < times[i].size() && times[i][e] <= T[q]) {
+        for (int s = 0; s < S; ++s) x[s] += m.nu[(size_t)rxn[i][e] * S + s];
+        ++e;
+      }
+      for (int s = 0; s < S; ++s) {
+        S1[(size_t)q * S + s] += x[s];
+        S2[(size_t)q * S + s] += x[s] * x[s];
+      }
+    }
+  }
+  const int64_t Pn = (U + window - 1) / window;
+  for (int64_t p = 0; p < Pn && p < max_points; ++p) {
+    const int64_t a = p * window, b = std::min(U, a + window), n_p = b - a;
+    double tsum = 0.0;
+    for (int64_t q = a; q < b; ++q) tsum += T[q];
+    t_out[p] = tsum / (double)n_p;
+    for (int s = 0; s < S; ++s) {
+      int64_t w1 = 0, w2 = 0;
+      for (int64_t q = a; q < b; ++q) {
+        w1 += S1[(size_t)q * S + s];
+        w2 += S2[(size_t)q * S + s];
+      }
+      mean_out[(size_t)p * S + s] = (double)w1 / (double)(N * n_p);
+      msq_out[(size_t)p * S + s] = (double)w2 / (double)(N * n_p);
+    }
+  }
+  *n_points = Pn;
+  *n_union = U;
+  return 0;
+}
+
 // Prefix sums of a[0..M) in the given schedule (0 = L, 1 = W32); for tests.
 void oracle_prefix(int M, const double* a, int schedule, double* prefix, double* a0) {
   std::vector<double> av(a, a + M), pv(M);
