@@ -222,6 +222,34 @@ ssa_status ssa_ensemble_grad(const ssa_model* model, int64_t n_traj, double t_en
                              const double* mean, double* dL_drates, double* dL_drates_se);
 
 /*
+ * ssa_ensemble_avg_xy -- selective memory along the time axis (Sec. 3.2.1,
+ * Fig. 3): Avg-Y on the union of every trajectory's event times, reduced
+ * along time into Avg-XY (adaptive sampling: more points where more events
+ * happen).
+ *
+ * Union points T_0 = 0 < T_1 < ... < T_{U-1} are 0 and the distinct event
+ * times of all n_traj trajectories (ids traj_offset + i, warp schedule,
+ * opts->precision); S1_m[s] and S2_m[s] are the sums over trajectories of
+ * x_s(T_m) and x_s(T_m)^2 (right-continuous states).  Window p covers union
+ * points [p k, min(U, (p + 1) k)) with n_p points, k = window (0: n_traj):
+ *   t_out[p]         = (T_pk + ... ) / n_p      (FP64, ascending order)
+ *   mean_out[p][s]   = (sum over the window of S1_m[s]) / (N n_p)
+ *   msq_out[p][s]    = (sum over the window of S2_m[s]) / (N n_p)
+ * window = 1 returns Avg-Y itself.  Outputs hold max_points entries (x S for
+ * mean and msq) in opts->memory's space; *n_points receives the number of
+ * windows P (only min(P, max_points) are written; max_points = 0 only
+ * counts) and *n_union (may be NULL) the number of union points U.
+ * Runs the ensemble twice (once to size the event log, once writing it:
+ * about 48 bytes of device memory per (event, species changed)); synchronous.
+ * Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA, SSA_EUNSUPPORTED (thread
+ * schedule, networks beyond the warp schedule, more than 2^31 log records),
+ * SSA_EOVERFLOW (n_traj * max_x^2 * window could leave int64).
+ */
+ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj, double t_end, uint64_t seed,
+                               const ssa_run_opts* opts, int64_t window, int64_t max_points, double* t_out,
+                               double* mean_out, double* msq_out, int64_t* n_points, int64_t* n_union);
+
+/*
  * Size of the fixed device scratch used by ssa_ensemble_run_noalloc: 4 MiB,
  * held by every GPU that loads the library until the process exits.
  */

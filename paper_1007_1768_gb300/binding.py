@@ -29,7 +29,7 @@ EXPORTS = [
     "ssa_status_string", "ssa_last_error", "ssa_run_opts_init", "ssa_model_create", "ssa_model_destroy",
     "ssa_model_info", "ssa_ensemble_workspace_size", "ssa_ensemble_run", "ssa_ensemble_run_noalloc",
     "ssa_batch_create", "ssa_batch_tune", "ssa_batch_launch", "ssa_batch_result", "ssa_batch_network_stats",
-    "ssa_batch_destroy", "ssa_batch_run", "ssa_ensemble_grad",
+    "ssa_batch_destroy", "ssa_batch_run", "ssa_ensemble_grad", "ssa_ensemble_avg_xy",
 ]
 
 
@@ -109,6 +109,9 @@ def lib():
         L.ssa_batch_run.restype = ctypes.c_int
         L.ssa_ensemble_grad.argtypes = [vp, i64, f64, i32, vp, u64, ctypes.POINTER(RunOpts), vp, vp, vp, vp]
         L.ssa_ensemble_grad.restype = ctypes.c_int
+        L.ssa_ensemble_avg_xy.argtypes = [vp, i64, f64, u64, ctypes.POINTER(RunOpts), i64, i64, vp, vp, vp,
+                                          ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.ssa_ensemble_avg_xy.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -290,6 +293,32 @@ def ensemble_grad(model: Model, n_traj: int, t_end: float, n_grid: int, seed: in
                                int(seed), ctypes.byref(opts), w.data_ptr(), mu.data_ptr(), out.data_ptr(),
                                se.data_ptr()))
     return out, se, traj
+
+
+def ensemble_avg_xy(model: Model, n_traj: int, t_end: float, seed: int, window: int = 0, *, max_points=None,
+                    **opt_kw):
+    """ssa_ensemble_avg_xy with host outputs: (t [P], mean [P, S], mean of
+    x^2 [P, S], number of union points U).  window 0 means n_traj; window 1
+    gives Avg-Y on the union of event times."""
+    L = lib()
+    S = model.n_species
+    P = ctypes.c_int64()
+    U = ctypes.c_int64()
+    cap = max_points
+    if cap is None:  # count first
+        opts = make_opts(memory=MEM_HOST, **opt_kw)
+        _check(L.ssa_ensemble_avg_xy(model.handle, int(n_traj), float(t_end), int(seed), ctypes.byref(opts),
+                                     int(window), 0, None, None, None, ctypes.byref(P), ctypes.byref(U)))
+        cap = int(P.value)
+    t = np.empty(max(cap, 1))
+    mean = np.empty((max(cap, 1), S))
+    msq = np.empty((max(cap, 1), S))
+    opts = make_opts(memory=MEM_HOST, **opt_kw)
+    _check(L.ssa_ensemble_avg_xy(model.handle, int(n_traj), float(t_end), int(seed), ctypes.byref(opts),
+                                 int(window), int(cap), t.ctypes.data, mean.ctypes.data, msq.ctypes.data,
+                                 ctypes.byref(P), ctypes.byref(U)))
+    n = min(int(P.value), int(cap))
+    return t[:n], mean[:n], msq[:n], int(U.value)
 
 
 def _ptr_array(ptrs):

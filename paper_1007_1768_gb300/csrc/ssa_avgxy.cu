@@ -1,0 +1,578 @@
+// Selective memory along the time axis (Sec. 3.2.1, Fig. 3): Avg-Y on the
+// union of every trajectory's event times, and Avg-XY, the average of k
+// successive Avg-Y points in time and value (ssa_ensemble_avg_xy).
+//
+// Definitions (the oracle states them point by point): union points
+// T_0 = 0 < T_1 < ... < T_{U-1} are 0 and the distinct event times of all
+// trajectories; S1_m[s] = sum_i x_is(T_m), S2_m[s] = sum_i x_is(T_m)^2
+// (right-continuous states).  Window p covers union points [p k, b_p),
+// b_p = min(U, (p + 1) k), n_p = b_p - p k points:
+//   t_p    = (T_{pk} + ... + T_{b_p - 1}) / n_p        (FP64, ascending order)
+//   mean_p = sum_m S1_m / (N n_p),  msq_p = sum_m S2_m / (N n_p).
+//
+// Pipeline:
+//   1. the warp kernel runs the ensemble once to count events and the
+//      largest count (capacity and overflow bounds), then again writing the
+//      event log: one record per (event, species changed) with the event
+//      time's bits, the species, v and (2 x_old + v) v;
+//   2. a stable least-significant-digit radix sort of the 64-bit time keys
+//      (8-bit digits; digits that are equal across all keys are skipped),
+//      carrying each record's index;
+//   3. head flags (first record of each distinct time) and their scan give
+//      every record its union index u; the distinct times are scattered to
+//      T[u];
+//   4. window sums without materialising S1_m: with C_s(m) the change of
+//      species s up to union point m,
+//        sum_{m in window p} S1_m = n_p (N x0_s + C_s(pk - 1)) + sum_{r in p} v_r (b_p - u_r),
+//      and C_s(pk - 1) is the exclusive scan over windows of W1[p] =
+//      sum_{r in p} v_r; the same with x0^2 and (2 x_old + v) v for S2.
+//      Records of a block accumulate in shared memory per (window, species)
+//      and flush with one global integer atomic each;
+//   5. one thread per window sums its times in ascending order; the final
+//      kernel forms t, mean and msq.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "ssa.h"
+#include "ssa_internal.h"
+
+namespace ssa_impl {
+namespace {
+
+typedef unsigned long long u64;
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+// ------------------------------------------------------------ device scan
+// Exclusive scan of n values (in place) with the total written to *total.
+constexpr int kScanThreads = 1024;
+
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* warp_sums, T* block_total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const T y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) warp_sums[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    T s = (lane < nw) ? warp_sums[lane] : T(0);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const T y = __shfl_up_sync(0xFFFFFFFFu, s, off);
+      if (lane >= off) s += y;
+    }
+    warp_sums[lane] = s;
+  }
+  __syncthreads();
+  const T excl = x - v + ((w > 0) ? warp_sums[w - 1] : T(0));
+  *block_total = warp_sums[nw - 1];
+  __syncthreads();
+  return excl;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(T* data, long long n, T* block_sums) {
+  __shared__ T ws[32];
+  const long long i = (long long)blockIdx.x * kScanThreads + threadIdx.x;
+  const T v = (i < n) ? data[i] : T(0);
+  T tot;
+  const T e = block_exclusive_scan(v, ws, &tot);
+  if (i < n) data[i] = e;
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+template <typename T>
+__global__ void k_scan_add(T* data, long long n, const T* block_offsets) {
+  const long long i = (long long)blockIdx.x * kScanThreads + threadIdx.x;
+  if (i < n) data[i] += block_offsets[blockIdx.x];
+}
+
+template <typename T>
+__global__ void k_scan_single(T* data, long long n, T* total) {  // one block, sequential chunks
+  __shared__ T ws[32];
+  T carry = 0;
+  for (long long base = 0; base < n; base += kScanThreads) {
+    const long long i = base + threadIdx.x;
+    const T v = (i < n) ? data[i] : T(0);
+    T tot;
+    const T e = block_exclusive_scan(v, ws, &tot);
+    if (i < n) data[i] = e + carry;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+// Scratch of the scan for n values: the block sums of every level.
+template <typename T>
+size_t scan_scratch_elems(long long n) {
+  size_t total = 0;
+  while (n > kScanThreads) {
+    n = (n + kScanThreads - 1) / kScanThreads;
+    total += (size_t)n;
+  }
+  return total + 1;
+}
+
+template <typename T>
+cudaError_t device_exclusive_scan(T* data, long long n, T* scratch, T* total, cudaStream_t st) {
+  if (n <= kScanThreads * 64) {
+    k_scan_single<T><<<1, kScanThreads, 0, st>>>(data, n, total);
+    return cudaGetLastError();
+  }
+  const long long nb = (n + kScanThreads - 1) / kScanThreads;
+  k_scan_blocks<T><<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = device_exclusive_scan<T>(scratch, nb, scratch + nb, total, st);
+  if (e != cudaSuccess) return e;
+  k_scan_add<T><<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, scratch);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ radix sort
+// Counts of every 8-bit digit at every position (8 x 256), for pass skipping.
+__global__ void k_digit_hist_all(const u64* keys, long long n, unsigned long long* hist) {
+  __shared__ unsigned int h[8 * 256];
+  for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const u64 k = keys[i];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) atomicAdd(&h[p * 256 + (int)((k >> (8 * p)) & 255)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+
+// Per-tile digit counts, digit-major: tile_hist[d * ntiles + tile].
+__global__ void __launch_bounds__(kSortThreads) k_tile_hist(const u64* keys, long long n, int shift,
+                                                            unsigned int* tile_hist, long long ntiles) {
+  __shared__ unsigned int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const long long t0 = (long long)blockIdx.x * kSortTile;
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const long long i = t0 + (long long)r * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(int)((keys[i] >> shift) & 255)], 1u);
+  }
+  __syncthreads();
+  tile_hist[(long long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter of one tile: items are taken in index order (round r holds
+// indices r * 256 + tid of the tile); within a round, lanes of a warp with
+// the same digit are ranked by __match_any_sync, warps in order by a
+// per-round count table, rounds by running digit counts.
+__global__ void __launch_bounds__(kSortThreads) k_tile_scatter(const u64* kin, const unsigned int* vin, u64* kout,
+                                                               unsigned int* vout, long long n, int shift,
+                                                               const unsigned int* offs, long long ntiles) {
+  __shared__ unsigned int base[256];
+  __shared__ unsigned int wcnt[kSortThreads / 32][256];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  base[tid] = offs[(long long)tid * ntiles + blockIdx.x];
+  const long long t0 = (long long)blockIdx.x * kSortTile;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int r = 0; r < kSortItems; ++r) {
+    const long long i = t0 + (long long)r * kSortThreads + tid;
+    const bool valid = i < n;
+    const u64 key = valid ? kin[i] : 0ULL;
+    const unsigned dig = valid ? (unsigned)((key >> shift) & 255) : 256u;
+    for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
+    __syncthreads();  // also orders this round's base reads after the last round's update
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, dig);
+    const unsigned rank = __popc(peers & lt);
+    if (valid && rank == 0) wcnt[w][dig] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      unsigned before = 0;
+      for (int ww = 0; ww < w; ++ww) before += wcnt[ww][dig];
+      const unsigned pos = base[dig] + before + rank;
+      kout[pos] = key;
+      vout[pos] = vin[i];
+    }
+    __syncthreads();
+    unsigned add = 0;
+    for (int ww = 0; ww < kSortThreads / 32; ++ww) add += wcnt[ww][tid];
+    base[tid] += add;
+    __syncthreads();  // every thread has read this round's counts before they are cleared
+  }
+}
+
+__global__ void k_iota(unsigned int* v, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = (unsigned int)i;
+}
+
+// ------------------------------------------------------------ union and windows
+// head[r] = 1 for the first record of each distinct time (records [0, nv)).
+__global__ void k_heads(const u64* keys, long long nv, unsigned int* head) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nv) head[r] = (r == 0 || keys[r] != keys[r - 1]) ? 1u : 0u;
+}
+
+// uidx holds the exclusive scan of head: union index u_r = uidx[r] + head[r]
+// (union point 0 is t = 0).  Distinct times go to T[u].
+__global__ void k_union_times(const u64* keys, long long nv, const unsigned int* head, const unsigned int* uidx,
+                              double* T) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r == 0) T[0] = 0.0;
+  if (r < nv && head[r]) T[uidx[r] + 1] = __longlong_as_double((long long)keys[r]);
+}
+
+// Window sums of one block's records, in shared memory per (window, species)
+// when the block's windows fit (else straight to global), then one global
+// integer atomic per entry.  W*[s * P + p] (species-major for the scans).
+constexpr int kWinThreads = 256;
+constexpr int kWinRecords = 4096;
+constexpr int kWinSlots = 512;
+
+__global__ void __launch_bounds__(kWinThreads) k_window_sums(
+    const unsigned int* head, const unsigned int* uidx, const unsigned int* perm, const int32_t* species,
+    const int32_t* change, const long long* d2, long long nv, long long U, long long k, int S, long long P,
+    long long* W1, long long* A1, long long* W2, long long* A2) {
+  __shared__ long long sW1[kWinSlots], sA1[kWinSlots], sW2[kWinSlots], sA2[kWinSlots];
+  const long long r0 = (long long)blockIdx.x * kWinRecords;
+  const long long r1 = min(nv, r0 + kWinRecords);
+  const long long p_lo = (long long)(uidx[r0] + head[r0]) / k;
+  const long long p_hi = (long long)(uidx[r1 - 1] + head[r1 - 1]) / k;
+  const bool local = (p_hi - p_lo + 1) * S <= kWinSlots;
+  for (int i = threadIdx.x; i < kWinSlots; i += blockDim.x) sW1[i] = sA1[i] = sW2[i] = sA2[i] = 0;
+  __syncthreads();
+  for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const long long u = (long long)uidx[r] + head[r];
+    const long long p = u / k;
+    const long long b = min(U, (p + 1) * k);
+    const unsigned int q = perm[r];
+    const int s = species[q];
+    const long long v = change[q], dd = d2[q], wt = b - u;
+    if (local) {
+      const int slot = (int)((p - p_lo) * S + s);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&sW1[slot]), (unsigned long long)v);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&sA1[slot]), (unsigned long long)(v * wt));
+      atomicAdd(reinterpret_cast<unsigned long long*>(&sW2[slot]), (unsigned long long)dd);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&sA2[slot]), (unsigned long long)(dd * wt));
+    } else {
+      const long long g = (long long)s * P + p;
+      atomicAdd(reinterpret_cast<unsigned long long*>(W1 + g), (unsigned long long)v);
+      atomicAdd(reinterpret_cast<unsigned long long*>(A1 + g), (unsigned long long)(v * wt));
+      atomicAdd(reinterpret_cast<unsigned long long*>(W2 + g), (unsigned long long)dd);
+      atomicAdd(reinterpret_cast<unsigned long long*>(A2 + g), (unsigned long long)(dd * wt));
+    }
+  }
+  __syncthreads();
+  if (local) {
+    const int used = (int)((p_hi - p_lo + 1) * S);
+    for (int i = threadIdx.x; i < used; i += blockDim.x) {
+      const long long p = p_lo + i / S;
+      const int s = i % S;
+      const long long g = (long long)s * P + p;
+      if (sW1[i]) atomicAdd(reinterpret_cast<unsigned long long*>(W1 + g), (unsigned long long)sW1[i]);
+      if (sA1[i]) atomicAdd(reinterpret_cast<unsigned long long*>(A1 + g), (unsigned long long)sA1[i]);
+      if (sW2[i]) atomicAdd(reinterpret_cast<unsigned long long*>(W2 + g), (unsigned long long)sW2[i]);
+      if (sA2[i]) atomicAdd(reinterpret_cast<unsigned long long*>(A2 + g), (unsigned long long)sA2[i]);
+    }
+  }
+}
+
+// One thread per window: the times of its union points summed in ascending order.
+__global__ void k_window_times(const double* T, long long U, long long k, long long P, double* t_out) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const long long a = p * k, b = min(U, a + k);
+  double sum = 0.0;
+  for (long long q = a; q < b; ++q) sum = __dadd_rn(sum, T[q]);
+  t_out[p] = __ddiv_rn(sum, (double)(b - a));
+}
+
+// mean and msq per (window, species); CW* hold the exclusive scans of W* along p.
+__global__ void k_window_final(const long long* CW1, const long long* A1, const long long* CW2, const long long* A2,
+                               const int32_t* x0, long long N, long long U, long long k, int S, long long P,
+                               double* mean, double* msq) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P * S) return;
+  const long long p = i / S;
+  const int s = (int)(i % S);
+  const long long n_p = min(U, (p + 1) * k) - p * k;
+  const long long g = (long long)s * P + p;
+  const long long xv = x0[s];
+  const long long s1 = n_p * (N * xv + CW1[g]) + A1[g];
+  const long long s2 = n_p * (N * xv * xv + CW2[g]) + A2[g];
+  const double den = (double)(N * n_p);
+  mean[i] = __ddiv_rn(__ll2double_rn(s1), den);
+  msq[i] = __ddiv_rn(__ll2double_rn(s2), den);
+}
+
+__global__ void k_fill_f64(double* p, double v) { *p = v; }
+
+}  // namespace
+}  // namespace ssa_impl
+
+using namespace ssa_impl;
+
+extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj, double t_end, uint64_t seed,
+                                          const ssa_run_opts* opts, int64_t window, int64_t max_points,
+                                          double* t_out, double* mean_out, double* msq_out, int64_t* n_points,
+                                          int64_t* n_union) {
+  ssa_run_opts o;
+  if (opts) o = *opts; else ssa_run_opts_init(&o);
+  if (!model || !n_points) return (ssa_status)set_error(SSA_EINVAL, "model and n_points must not be NULL");
+  if (n_traj < 1) return (ssa_status)set_error(SSA_EINVAL, "n_traj must be >= 1");
+  if (!(t_end > 0.0) || !std::isfinite(t_end)) return (ssa_status)set_error(SSA_EINVAL, "t_end must be finite and > 0");
+  if (window < 0) return (ssa_status)set_error(SSA_EINVAL, "window must be >= 0 (0: n_traj)");
+  if (max_points < 0 || (max_points > 0 && (!t_out || !mean_out || !msq_out)))
+    return (ssa_status)set_error(SSA_EINVAL, "outputs of max_points entries are required");
+  if (o.memory != SSA_MEM_HOST && o.memory != SSA_MEM_DEVICE) return (ssa_status)set_error(SSA_EINVAL, "bad memory kind");
+  if (o.schedule == SSA_SCHED_THREAD)
+    return (ssa_status)set_error(SSA_EUNSUPPORTED, "the event log runs on the warp schedule");
+  if (o.max_events <= 0) o.max_events = SSA_DEFAULT_MAX_EVENTS;
+  const long long k = window ? window : n_traj;
+  ModelImageView mv;
+  if (!model_image_view(model, &mv)) return (ssa_status)set_error(SSA_EINVAL, "bad model");
+  const int S = mv.S, M = mv.M;
+  if (warp_max_chunk(M) == 0) return (ssa_status)set_error(SSA_EUNSUPPORTED, "the warp schedule takes at most 512 reactions");
+  // the largest number of species one reaction changes (records per event)
+  const int32_t* nu_ptr = reinterpret_cast<const int32_t*>(mv.image + mv.off_nu_ptr);
+  int max_nnz = 1;
+  for (int j = 0; j < M; ++j) max_nnz = std::max(max_nnz, nu_ptr[j + 1] - nu_ptr[j]);
+  if (max_nnz > kLogChunk)
+    return (ssa_status)set_error(SSA_EUNSUPPORTED, "a reaction changes more species than an event-log chunk holds");
+  cudaStream_t st = static_cast<cudaStream_t>(o.cuda_stream);
+
+  // pass 1: event count and largest count (warp schedule, one grid point)
+  ssa_run_opts o1 = o;
+  o1.memory = SSA_MEM_DEVICE;
+  o1.schedule = SSA_SCHED_WARP;
+  o1.traj_events = nullptr;
+  o1.traj_hash = nullptr;
+  o1.traj_flags = nullptr;
+  o1.workspace = nullptr;
+  o1.workspace_bytes = 0;
+  o1.device_totals = nullptr;
+  o1.sim_event_begin = o1.sim_event_end = nullptr;
+  double* d_small = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_small), 16 * (size_t)S + 16, st);
+  if (e != cudaSuccess) return (ssa_status)set_error(SSA_ENOMEM, cudaGetErrorString(e));
+  ssa_run_stats st1;
+  ssa_status rs = ssa_ensemble_run(model, n_traj, t_end, 1, nullptr, seed, &o1, d_small, d_small + S, nullptr, nullptr,
+                                   &st1);
+  cudaFreeAsync(d_small, st);
+  if (rs != SSA_OK) return rs;
+  const long double mx = (long double)st1.max_x;
+  if ((long double)n_traj * mx * mx * (long double)k >= 4.6e18L)
+    return (ssa_status)set_error(SSA_EOVERFLOW, "window sums of x^2 could leave int64 (N * max_x^2 * window)");
+
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (ssa_status)set_error(SSA_ECUDA, cudaGetErrorString(e));
+  cudaDeviceProp prop;
+  if ((e = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess) return (ssa_status)set_error(SSA_ECUDA, cudaGetErrorString(e));
+  DevModel dm;
+  int mst = model_device_tables(model, dev, &dm);
+  if (mst != SSA_OK) return (ssa_status)mst;
+  const int threads = 256;
+  const size_t smem = warp_kernel_smem(M, S, dm.nnz, threads);
+  if (smem > prop.sharedMemPerBlockOptin) return (ssa_status)set_error(SSA_EUNSUPPORTED, "network too large for shared memory");
+  int per_sm = 0;
+  const bool fp32 = o.precision == SSA_PREC_FP32;
+  if ((e = warp_log_kernel_prepare(M, fp32, smem, threads, &per_sm)) != cudaSuccess)
+    return (ssa_status)set_error(SSA_ECUDA, cudaGetErrorString(e));
+  if (per_sm < 1) return (ssa_status)set_error(SSA_EUNSUPPORTED, "the logging kernel cannot be resident");
+  const long long want = (n_traj + threads / 32 - 1) / (threads / 32);
+  const long long capb = (long long)prop.multiProcessorCount * per_sm;
+  const int blocks = (int)(want < capb ? want : capb);
+  const unsigned long long cap =
+      (unsigned long long)st1.events * (unsigned long long)max_nnz +
+      (unsigned long long)(blocks * (threads / 32) + 1) * (unsigned long long)kLogChunk * 2ULL;
+  if (cap >= (1ULL << 31))
+    return (ssa_status)set_error(SSA_EUNSUPPORTED, "the event log would exceed 2^31 records; use fewer trajectories");
+
+  // device memory: one allocation
+  const long long ntiles = (long long)((cap + kSortTile - 1) / kSortTile);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes, 256);
+    return at;
+  };
+  const size_t o_key = take(8 * cap), o_key2 = take(8 * cap), o_sp = take(4 * cap), o_ch = take(4 * cap),
+               o_d2 = take(8 * cap), o_perm = take(4 * cap), o_perm2 = take(4 * cap), o_head = take(4 * cap),
+               o_uidx = take(4 * cap), o_T = take(8 * (cap + 1)),
+               o_th = take(4 * (size_t)(256 * ntiles)), o_sc32 = take(4 * scan_scratch_elems<unsigned>(256 * ntiles + cap)),
+               o_hist = take(8 * 8 * 256), o_cnt = take(8 * 4), o_grid = take(8), o_d = take(16 * (size_t)S),
+               o_stats = take(8 * kStatCount), o_counter = take(8);
+  unsigned char* ws = nullptr;
+  if ((e = cudaMallocAsync(reinterpret_cast<void**>(&ws), off, st)) != cudaSuccess)
+    return (ssa_status)set_error(SSA_ENOMEM, cudaGetErrorString(e));
+  unsigned char* ws2 = nullptr;  // window arrays, sized after the union is known
+  auto fail = [&](int status, const char* msg) {
+    cudaFreeAsync(ws, st);
+    if (ws2) cudaFreeAsync(ws2, st);
+    return (ssa_status)set_error(status, msg);
+  };
+#define SSA_A_TRY(expr)                                           \
+  do {                                                            \
+    const cudaError_t e_ = (expr);                                \
+    if (e_ != cudaSuccess) return fail(SSA_ECUDA, cudaGetErrorString(e_)); \
+  } while (0)
+  u64* key = reinterpret_cast<u64*>(ws + o_key);
+  u64* key2 = reinterpret_cast<u64*>(ws + o_key2);
+  unsigned int* perm = reinterpret_cast<unsigned int*>(ws + o_perm);
+  unsigned int* perm2 = reinterpret_cast<unsigned int*>(ws + o_perm2);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ws + o_cnt);  // counter, padded, overflow
+  SSA_A_TRY(cudaMemsetAsync(ws + o_cnt, 0, 8 * 4, st));
+  SSA_A_TRY(cudaMemsetAsync(ws + o_d, 0, 16 * (size_t)S, st));
+  SSA_A_TRY(cudaMemsetAsync(ws + o_stats, 0, 8 * kStatCount, st));
+  SSA_A_TRY(cudaMemsetAsync(ws + o_counter, 0, 8, st));
+  SSA_A_TRY(cudaMemsetAsync(ws + o_hist, 0, 8 * 8 * 256, st));
+  k_fill_f64<<<1, 1, 0, st>>>(reinterpret_cast<double*>(ws + o_grid), t_end);
+  SSA_A_TRY(cudaGetLastError());
+
+  // pass 2: the same trajectories, writing the event log
+  RunArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.m = dm;
+  a.G = 1;
+  a.N = n_traj;
+  a.traj_offset = o.traj_offset;
+  a.seed = seed;
+  a.stream_id = o.stream_id;
+  a.max_events = o.max_events;
+  a.t_end = t_end;
+  a.grid = reinterpret_cast<const double*>(ws + o_grid);
+  a.D1 = reinterpret_cast<unsigned long long*>(ws + o_d);
+  a.D2 = a.D1 + S;
+  a.counter = reinterpret_cast<unsigned long long*>(ws + o_counter);
+  a.stats = reinterpret_cast<unsigned long long*>(ws + o_stats);
+  a.grid_uniform = 0;
+  EventLog lg;
+  lg.key = key;
+  lg.species = reinterpret_cast<int32_t*>(ws + o_sp);
+  lg.change = reinterpret_cast<int32_t*>(ws + o_ch);
+  lg.d2 = reinterpret_cast<long long*>(ws + o_d2);
+  lg.counter = cnt;
+  lg.padded = cnt + 1;
+  lg.overflow = cnt + 2;
+  lg.capacity = cap;
+  SSA_A_TRY(launch_warp_log_kernel(a, lg, fp32, blocks, threads, smem, st));
+  unsigned long long hc[4];
+  SSA_A_TRY(cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, st));
+  SSA_A_TRY(cudaStreamSynchronize(st));
+  if (hc[2]) return fail(SSA_ECUDA, "the event log overflowed its capacity");
+  const long long n_all = (long long)std::min<unsigned long long>(hc[0], cap);
+  const long long nv = n_all - (long long)hc[1];  // valid records; sentinels sort last
+
+  // sort (keys, record index) by time
+  const int thr = 256;
+  k_iota<<<(unsigned)((n_all + thr - 1) / thr), thr, 0, st>>>(perm, n_all);
+  SSA_A_TRY(cudaGetLastError());
+  k_digit_hist_all<<<std::max(1, std::min((int)((n_all + 4095) / 4096), 4 * prop.multiProcessorCount)), 256, 0, st>>>(
+      key, n_all, reinterpret_cast<unsigned long long*>(ws + o_hist));
+  SSA_A_TRY(cudaGetLastError());
+  unsigned long long hh[8 * 256];
+  SSA_A_TRY(cudaMemcpyAsync(hh, ws + o_hist, sizeof hh, cudaMemcpyDeviceToHost, st));
+  SSA_A_TRY(cudaStreamSynchronize(st));
+  const long long nt = (n_all + kSortTile - 1) / kSortTile;
+  unsigned int* th = reinterpret_cast<unsigned int*>(ws + o_th);
+  unsigned int* sc = reinterpret_cast<unsigned int*>(ws + o_sc32);
+  for (int pass = 0; pass < 8; ++pass) {
+    bool varies = true;
+    for (int d = 0; d < 256; ++d)
+      if (hh[pass * 256 + d] == (unsigned long long)n_all) varies = false;
+    if (!varies || n_all == 0) continue;
+    const int shift = 8 * pass;
+    k_tile_hist<<<(unsigned)nt, kSortThreads, 0, st>>>(key, n_all, shift, th, nt);
+    SSA_A_TRY(cudaGetLastError());
+    SSA_A_TRY(device_exclusive_scan<unsigned int>(th, 256 * nt, sc, nullptr, st));
+    k_tile_scatter<<<(unsigned)nt, kSortThreads, 0, st>>>(key, perm, key2, perm2, n_all, shift, th, nt);
+    SSA_A_TRY(cudaGetLastError());
+    std::swap(key, key2);
+    std::swap(perm, perm2);
+  }
+
+  // union indices and times
+  unsigned int* head = reinterpret_cast<unsigned int*>(ws + o_head);
+  unsigned int* uidx = reinterpret_cast<unsigned int*>(ws + o_uidx);
+  double* T = reinterpret_cast<double*>(ws + o_T);
+  long long U = 1;
+  if (nv > 0) {
+    k_heads<<<(unsigned)((nv + thr - 1) / thr), thr, 0, st>>>(key, nv, head);
+    SSA_A_TRY(cudaGetLastError());
+    SSA_A_TRY(cudaMemcpyAsync(uidx, head, 4 * (size_t)nv, cudaMemcpyDeviceToDevice, st));
+    unsigned int* dtot = reinterpret_cast<unsigned int*>(ws + o_cnt + 24);
+    SSA_A_TRY(device_exclusive_scan<unsigned int>(uidx, nv, sc, dtot, st));
+    unsigned int heads = 0;
+    SSA_A_TRY(cudaMemcpyAsync(&heads, dtot, 4, cudaMemcpyDeviceToHost, st));
+    SSA_A_TRY(cudaStreamSynchronize(st));
+    U = 1 + (long long)heads;
+  }
+  k_union_times<<<(unsigned)((std::max(nv, 1LL) + thr - 1) / thr), thr, 0, st>>>(key, nv, head, uidx, T);
+  SSA_A_TRY(cudaGetLastError());
+  const long long P = (U + k - 1) / k;
+  *n_points = P;
+  if (n_union) *n_union = U;
+  if (max_points == 0) {
+    cudaFreeAsync(ws, st);
+    SSA_A_TRY(cudaStreamSynchronize(st));
+    return SSA_OK;
+  }
+  const long long Pw = std::min<long long>(P, max_points);
+
+  // window sums (species-major arrays of P entries), scans, outputs
+  size_t off2 = 0;
+  auto take2 = [&](size_t bytes) {
+    const size_t at = off2;
+    off2 = align_up(off2 + bytes, 256);
+    return at;
+  };
+  const size_t PS = (size_t)P * S;
+  const size_t o_W1 = take2(8 * PS), o_A1 = take2(8 * PS), o_W2 = take2(8 * PS), o_A2 = take2(8 * PS),
+               o_sc64 = take2(8 * scan_scratch_elems<long long>((long long)P) + 8), o_x0 = take2(4 * (size_t)S),
+               o_t = take2(8 * (size_t)P), o_mean = take2(8 * PS), o_msq = take2(8 * PS);
+  if ((e = cudaMallocAsync(reinterpret_cast<void**>(&ws2), off2, st)) != cudaSuccess)
+    return fail(SSA_ENOMEM, cudaGetErrorString(e));
+  long long* W1 = reinterpret_cast<long long*>(ws2 + o_W1);
+  long long* A1 = reinterpret_cast<long long*>(ws2 + o_A1);
+  long long* W2 = reinterpret_cast<long long*>(ws2 + o_W2);
+  long long* A2 = reinterpret_cast<long long*>(ws2 + o_A2);
+  SSA_A_TRY(cudaMemsetAsync(ws2, 0, o_sc64, st));
+  if (nv > 0) {
+    k_window_sums<<<(unsigned)((nv + kWinRecords - 1) / kWinRecords), kWinThreads, 0, st>>>(
+        head, uidx, perm, lg.species, lg.change, lg.d2, nv, U, k, S, P, W1, A1, W2, A2);
+    SSA_A_TRY(cudaGetLastError());
+  }
+  long long* sc64 = reinterpret_cast<long long*>(ws2 + o_sc64);
+  for (int s = 0; s < S; ++s) {
+    SSA_A_TRY(device_exclusive_scan<long long>(W1 + (size_t)s * P, P, sc64, nullptr, st));
+    SSA_A_TRY(device_exclusive_scan<long long>(W2 + (size_t)s * P, P, sc64, nullptr, st));
+  }
+  int32_t* x0d = reinterpret_cast<int32_t*>(ws2 + o_x0);
+  SSA_A_TRY(cudaMemcpyAsync(x0d, dm.x0, 4 * (size_t)S, cudaMemcpyDeviceToDevice, st));
+  double* dt = reinterpret_cast<double*>(ws2 + o_t);
+  double* dmean = reinterpret_cast<double*>(ws2 + o_mean);
+  double* dmsq = reinterpret_cast<double*>(ws2 + o_msq);
+  k_window_times<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(T, U, k, P, dt);
+  SSA_A_TRY(cudaGetLastError());
+  k_window_final<<<(unsigned)((PS + 255) / 256), 256, 0, st>>>(W1, A1, W2, A2, x0d, n_traj, U, k, S, P, dmean, dmsq);
+  SSA_A_TRY(cudaGetLastError());
+  const cudaMemcpyKind kind = (o.memory == SSA_MEM_HOST) ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  SSA_A_TRY(cudaMemcpyAsync(t_out, dt, 8 * (size_t)Pw, kind, st));
+  SSA_A_TRY(cudaMemcpyAsync(mean_out, dmean, 8 * (size_t)Pw * S, kind, st));
+  SSA_A_TRY(cudaMemcpyAsync(msq_out, dmsq, 8 * (size_t)Pw * S, kind, st));
+  cudaFreeAsync(ws2, st);
+  cudaFreeAsync(ws, st);
+  SSA_A_TRY(cudaStreamSynchronize(st));
+#undef SSA_A_TRY
+  return SSA_OK;
+}

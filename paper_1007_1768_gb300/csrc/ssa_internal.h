@@ -148,6 +148,21 @@ constexpr int kThreadMaxM = 16;
 constexpr int kThreadMaxS = 16;
 cudaError_t thread_kernel_set_smem(int M, int S, bool shared_d, size_t smem_bytes);
 
+// Event log of the warp kernel (selective memory along the time axis): one
+// record per (kept event, species it changes), handed out in per-warp chunks.
+constexpr int kLogChunk = 256;
+constexpr unsigned long long kLogSentinel = 0xFFFFFFFFFFFFFFFFULL;  // key of an unused slot
+struct EventLog {
+  unsigned long long* key;       // [capacity] bits of the event time
+  int32_t* species;              // [capacity]
+  int32_t* change;               // [capacity] v
+  long long* d2;                 // [capacity] (2 x_old + v) v
+  unsigned long long* counter;   // slots handed out (in chunks)
+  unsigned long long* padded;    // unused slots (sentinel keys)
+  unsigned long long* overflow;  // nonzero when the capacity ran out
+  unsigned long long capacity;
+};
+
 // Warp-per-trajectory kernel (ssa_warp_kernel.cu), schedule W32.  Chunk
 // bound of the instantiation serving M reactions (0 when M > 512).
 int warp_max_chunk(int M);
@@ -159,6 +174,10 @@ size_t warp_kernel_smem(int M, int S, int nnz, int threads);
 cudaError_t warp_kernel_prepare(int M, bool fp32, size_t smem, int threads, int* blocks_per_sm);
 cudaError_t launch_warp_kernel(const RunArgs& a, bool fp32, int blocks, int threads, size_t smem,
                                cudaStream_t stream);
+// The same kernel writing the event log.
+cudaError_t warp_log_kernel_prepare(int M, bool fp32, size_t smem, int threads, int* blocks_per_sm);
+cudaError_t launch_warp_log_kernel(const RunArgs& a, const EventLog& lg, bool fp32, int blocks, int threads,
+                                   size_t smem, cudaStream_t stream);
 
 // Host image of a model's device tables (see DevModel for the layout), for
 // entry points that place the tables themselves.

@@ -33,9 +33,10 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int M, int S, int nnz, int 
   return L;
 }
 
-// MAXCH bounds the chunk ceil(M / 32); F32 selects the FP32-propensity mode.
-template <int MAXCH, bool F32>
-__global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a) {
+// MAXCH bounds the chunk ceil(M / 32); F32 selects the FP32-propensity mode;
+// LOG also writes the event log (selective memory along the time axis).
+template <int MAXCH, bool F32, bool LOG>
+__global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a, const EventLog lg) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long blk[4];
   const int S = a.m.S, M = a.m.M, T = blockDim.x, tid = threadIdx.x;
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a) {
   net.grid_margin = a.grid_margin;
   net.sid = (uint32_t)a.stream_id;
   const uint32_t key0 = (uint32_t)a.seed, key1 = (uint32_t)(a.seed >> 32);
+  WarpLogState lst{kLogSentinel, 0};
 
   for (;;) {
     unsigned long long next = 0;
@@ -101,8 +103,8 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a) {
     next = __shfl_sync(kFullMask, next, 0);
     if (next >= (unsigned long long)a.N) break;
     const long long li = (long long)next;
-    const WarpTraj r =
-        warp_trajectory<MAXCH, F32>(net, xs, a.traj_offset + next, key0, key1, a.max_events, s_inv, s_lnf);
+    const WarpTraj r = warp_trajectory<MAXCH, F32, LOG>(net, xs, a.traj_offset + next, key0, key1, a.max_events,
+                                                        s_inv, s_lnf, &lg, &lst);
     if (lane == 0) {
       if (a.traj_events) a.traj_events[li] = (long long)r.n;
       if (a.traj_hash) a.traj_hash[li] = r.hash;
@@ -114,6 +116,7 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a) {
     }
     __syncwarp();
   }
+  if constexpr (LOG) log_close(lg, lst);
 
   __syncthreads();
   if (tid == 0) {
@@ -130,42 +133,46 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a) {
   }
 }
 
-template <int MAXCH, bool F32>
-cudaError_t launch_ch(const RunArgs& a, int blocks, int threads, size_t smem, cudaStream_t st) {
-  k_ssa_warp<MAXCH, F32><<<blocks, threads, smem, st>>>(a);
+template <int MAXCH, bool F32, bool LOG>
+cudaError_t launch_ch(const RunArgs& a, const EventLog& lg, int blocks, int threads, size_t smem, cudaStream_t st) {
+  k_ssa_warp<MAXCH, F32, LOG><<<blocks, threads, smem, st>>>(a, lg);
   return cudaGetLastError();
 }
 
-template <int MAXCH, bool F32>
+template <int MAXCH, bool F32, bool LOG>
 cudaError_t prepare_ch(size_t smem, int threads, int* per_sm) {
   cudaError_t e =
-      cudaFuncSetAttribute(k_ssa_warp<MAXCH, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_ssa_warp<MAXCH, F32, LOG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_ssa_warp<MAXCH, F32>, threads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_ssa_warp<MAXCH, F32, LOG>, threads, smem);
 }
 
-template <bool F32>
-cudaError_t prepare_prec(int M, size_t smem, int threads, int* per_sm) {
+template <bool F32, bool LOG>
+cudaError_t dispatch(int M, bool launch, const RunArgs* a, const EventLog* lg, int blocks, int threads, size_t smem,
+                     cudaStream_t st, int* per_sm) {
   switch (warp_max_chunk(M)) {
-    case 1: return prepare_ch<1, F32>(smem, threads, per_sm);
-    case 2: return prepare_ch<2, F32>(smem, threads, per_sm);
-    case 4: return prepare_ch<4, F32>(smem, threads, per_sm);
-    case 8: return prepare_ch<8, F32>(smem, threads, per_sm);
-    case 16: return prepare_ch<16, F32>(smem, threads, per_sm);
+#define SSA_CH_CASE(C)                                                                     \
+  case C:                                                                                  \
+    return launch ? launch_ch<C, F32, LOG>(*a, *lg, blocks, threads, smem, st)            \
+                  : prepare_ch<C, F32, LOG>(smem, threads, per_sm);
+    SSA_CH_CASE(1)
+    SSA_CH_CASE(2)
+    SSA_CH_CASE(4)
+    SSA_CH_CASE(8)
+    SSA_CH_CASE(16)
+#undef SSA_CH_CASE
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <bool F32>
-cudaError_t launch_prec(const RunArgs& a, int blocks, int threads, size_t smem, cudaStream_t stream) {
-  switch (warp_max_chunk(a.m.M)) {
-    case 1: return launch_ch<1, F32>(a, blocks, threads, smem, stream);
-    case 2: return launch_ch<2, F32>(a, blocks, threads, smem, stream);
-    case 4: return launch_ch<4, F32>(a, blocks, threads, smem, stream);
-    case 8: return launch_ch<8, F32>(a, blocks, threads, smem, stream);
-    case 16: return launch_ch<16, F32>(a, blocks, threads, smem, stream);
-    default: return cudaErrorInvalidValue;
+cudaError_t dispatch_all(int M, bool fp32, bool log, bool launch, const RunArgs* a, const EventLog* lg, int blocks,
+                         int threads, size_t smem, cudaStream_t st, int* per_sm) {
+  if (fp32) {
+    return log ? dispatch<true, true>(M, launch, a, lg, blocks, threads, smem, st, per_sm)
+               : dispatch<true, false>(M, launch, a, lg, blocks, threads, smem, st, per_sm);
   }
+  return log ? dispatch<false, true>(M, launch, a, lg, blocks, threads, smem, st, per_sm)
+             : dispatch<false, false>(M, launch, a, lg, blocks, threads, smem, st, per_sm);
 }
 
 }  // namespace
@@ -180,14 +187,22 @@ size_t warp_kernel_smem(int M, int S, int nnz, int threads) {
 }
 
 cudaError_t warp_kernel_prepare(int M, bool fp32, size_t smem, int threads, int* blocks_per_sm) {
-  return fp32 ? prepare_prec<true>(M, smem, threads, blocks_per_sm)
-              : prepare_prec<false>(M, smem, threads, blocks_per_sm);
+  return dispatch_all(M, fp32, false, false, nullptr, nullptr, 0, threads, smem, nullptr, blocks_per_sm);
 }
 
 cudaError_t launch_warp_kernel(const RunArgs& a, bool fp32, int blocks, int threads, size_t smem,
                                cudaStream_t stream) {
-  return fp32 ? launch_prec<true>(a, blocks, threads, smem, stream)
-              : launch_prec<false>(a, blocks, threads, smem, stream);
+  const EventLog none{};
+  return dispatch_all(a.m.M, fp32, false, true, &a, &none, blocks, threads, smem, stream, nullptr);
+}
+
+cudaError_t warp_log_kernel_prepare(int M, bool fp32, size_t smem, int threads, int* blocks_per_sm) {
+  return dispatch_all(M, fp32, true, false, nullptr, nullptr, 0, threads, smem, nullptr, blocks_per_sm);
+}
+
+cudaError_t launch_warp_log_kernel(const RunArgs& a, const EventLog& lg, bool fp32, int blocks, int threads,
+                                   size_t smem, cudaStream_t stream) {
+  return dispatch_all(a.m.M, fp32, true, true, &a, &lg, blocks, threads, smem, stream, nullptr);
 }
 
 }  // namespace ssa_impl

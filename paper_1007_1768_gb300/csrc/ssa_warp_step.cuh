@@ -112,13 +112,61 @@ __host__ __device__ inline uint16_t depw_entry(const int32_t* dep_ptr, const int
   return (uint16_t)bits;
 }
 
+// Optional event log (selective memory along the time axis): every kept
+// event writes one record per species it changes -- key = bits of the event
+// time, species, change v and (2 x_old + v) v -- or one record with v = 0
+// when it changes none.  A warp fills chunks of
+// kLogChunk records taken from a global counter; the unused tail of a chunk
+// holds the sentinel key kLogSentinel (sorted after every time).
+// (EventLog, kLogChunk and kLogSentinel are declared in ssa_internal.h.)
+
+// Per-warp position in the current chunk (identical on every lane).
+struct WarpLogState {
+  unsigned long long base;  // first slot of the chunk, or kLogSentinel when none
+  int fill;
+};
+
+// Makes room for `cnt` (<= kLogChunk) records in this warp's chunk: pads the
+// old chunk's tail with sentinels and takes a new chunk when it is full.
+// Returns false (every lane) when the capacity is exhausted.
+__device__ __forceinline__ bool log_reserve(const EventLog& lg, WarpLogState& st, int cnt) {
+  const int lane = threadIdx.x & 31;
+  if (st.base != kLogSentinel && st.fill + cnt <= kLogChunk) return true;
+  if (st.base != kLogSentinel) {
+    for (int q = st.fill + lane; q < kLogChunk; q += 32) lg.key[st.base + q] = kLogSentinel;
+    if (lane == 0) atomicAdd(lg.padded, (unsigned long long)(kLogChunk - st.fill));
+  }
+  unsigned long long b = 0;
+  if (lane == 0) b = atomicAdd(lg.counter, (unsigned long long)kLogChunk);
+  b = __shfl_sync(kFullMask, b, 0);
+  if (b + kLogChunk > lg.capacity) {
+    if (lane == 0) atomicExch(lg.overflow, 1ULL);
+    st.base = kLogSentinel;
+    return false;
+  }
+  st.base = b;
+  st.fill = 0;
+  return true;
+}
+
+// Pads the tail of the warp's last chunk (call once, when the warp is done).
+__device__ __forceinline__ void log_close(const EventLog& lg, WarpLogState& st) {
+  const int lane = threadIdx.x & 31;
+  if (st.base == kLogSentinel) return;
+  for (int q = st.fill + lane; q < kLogChunk; q += 32) lg.key[st.base + q] = kLogSentinel;
+  if (lane == 0) atomicAdd(lg.padded, (unsigned long long)(kLogChunk - st.fill));
+  st.base = kLogSentinel;
+}
+
 // Runs trajectory traj_id of `net` on the calling warp (all 32 lanes), with
 // the state in xs[0..S) (shared memory, this warp's own).  MAXCH bounds the
 // chunk ceil(M / 32) (registers only; the chunk itself is the runtime value).
-template <int MAXCH, bool F32>
+// LOG: also write the event log (lg, lst).
+template <int MAXCH, bool F32, bool LOG = false>
 __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t* xs, unsigned long long traj_id,
                                                     uint32_t key0, uint32_t key1, long long max_events,
-                                                    const uint64_t* s_inv, const uint64_t* s_lnf) {
+                                                    const uint64_t* s_inv, const uint64_t* s_lnf,
+                                                    const EventLog* lg = nullptr, WarpLogState* lst = nullptr) {
   const int lane = threadIdx.x & 31;
   const int S = net.S, M = net.M;
   const int ch = (M + 31) / 32;
@@ -303,6 +351,20 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
       break;
     }
     __syncwarp();
+    bool logged = false;
+    // an event with no net change still adds its time to the union: one
+    // record with v = 0 (species 0, no effect on the sums)
+    const int nrec = (q1 > q0) ? (q1 - q0) : 1;
+    if constexpr (LOG) {
+      logged = log_reserve(*lg, *lst, nrec);
+      if (logged && q1 == q0 && lane == 0) {
+        const unsigned long long slot = lst->base + (unsigned long long)lst->fill;
+        lg->key[slot] = (unsigned long long)tb;
+        lg->species[slot] = 0;
+        lg->change[slot] = 0;
+        lg->d2[slot] = 0;
+      }
+    }
     for (int e = q0 + lane; e < q1; e += 32) {
       const int s = net.nu_idx[e];
       const int vv = net.nu_val[e];
@@ -310,10 +372,23 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
       const int xn = xo + vv;
       xs[s] = xn;
       maxx = max(maxx, xn);
+      const long long d2 = (2 * (long long)xo + vv) * (long long)vv;
       if (k < net.G) {
         atomicAdd(net.D1 + (size_t)k * S + s, (unsigned long long)(long long)vv);
-        atomicAdd(net.D2 + (size_t)k * S + s, (unsigned long long)((2 * (long long)xo + vv) * (long long)vv));
+        atomicAdd(net.D2 + (size_t)k * S + s, (unsigned long long)d2);
       }
+      if constexpr (LOG) {
+        if (logged) {
+          const unsigned long long slot = lst->base + (unsigned long long)(lst->fill + (e - q0));
+          lg->key[slot] = (unsigned long long)tb;
+          lg->species[slot] = s;
+          lg->change[slot] = vv;
+          lg->d2[slot] = d2;
+        }
+      }
+    }
+    if constexpr (LOG) {
+      if (logged) lst->fill += nrec;
     }
     __syncwarp();
     t = t_next;
