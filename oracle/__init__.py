@@ -149,6 +149,8 @@ def lib():
         L.oracle_avg_xy.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, i64, i64, f64, u64, u64, i64,
                                     ctypes.c_int, ctypes.c_int, i64, i64, vp, vp, vp, vp, vp]
         L.oracle_avg_xy.restype = ctypes.c_int
+        L.oracle_set_modifiers.argtypes = [ctypes.c_int, vp, vp, vp, vp]
+        L.oracle_set_modifiers.restype = ctypes.c_int
         L.oracle_select.argtypes = [ctypes.c_int, vp, ctypes.c_int, f64]
         L.oracle_select.restype = ctypes.c_int
         L.oracle_prefix.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, vp]
@@ -187,6 +189,17 @@ def uniform_grid(n_grid: int, t_end: float) -> np.ndarray:
     g = np.empty(n_grid, dtype=np.float64)
     lib().oracle_uniform_grid(n_grid, float(t_end), g.ctypes.data)
     return g
+
+
+def _set_modifiers(L, net):
+    """Rate modifiers of `net` for the oracle calls this thread makes next."""
+    mods = getattr(net, "modifier_arrays", lambda: None)()
+    if mods is None:
+        L.oracle_set_modifiers(0, None, None, None, None)
+        return None
+    f, k, lo, hi = (np.ascontiguousarray(a) for a in mods)
+    L.oracle_set_modifiers(net.n_reactions, f.ctypes.data, k.ctypes.data, lo.ctypes.data, hi.ctypes.data)
+    return (f, k, lo, hi)  # keep the arrays alive for the call
 
 
 def _model_arrays(net):
@@ -238,6 +251,7 @@ def run(net, n_traj: int, t_end: float, n_grid: int, seed: int, grid=None, traj_
         off = 0
         for b, e in span_list:
             n = e - b
+            keep = _set_modifiers(L, net)  # noqa: F841
             rc = L.oracle_run(S, M, R.ctypes.data, P.ctypes.data, c.ctypes.data, x0.ctypes.data, b, e,
                               float(t_end), G, g.ctypes.data, int(seed), int(stream), int(max_events),
                               int(schedule), int(precision), s1.ctypes.data, s2.ctypes.data,
@@ -297,6 +311,7 @@ def trace(net, traj_id: int, t_end: float, n_grid: int, seed: int, grid=None, st
     rj = np.zeros(record_max, dtype=np.int32)
     xs = np.zeros((G, net.n_species), dtype=np.int64)
     ne = np.zeros(1, dtype=np.int64)
+    keep = _set_modifiers(L, net)  # noqa: F841
     flags = L.oracle_trace(net.n_species, net.n_reactions, R.ctypes.data, P.ctypes.data, c.ctypes.data,
                            x0.ctypes.data, int(traj_id), float(t_end), G, g.ctypes.data, int(seed), int(stream),
                            int(max_events), int(schedule), int(precision), record_max, rt.ctypes.data,
@@ -329,6 +344,7 @@ def grad(net, n_traj: int, t_end: float, n_grid: int, seed: int, dL_dmean, mean,
     def work(i):
         b, e = spans[i]
         view = out[offs[i]:offs[i + 1]]
+        keep = _set_modifiers(L, net)  # noqa: F841
         rc = L.oracle_grad(S, M, R.ctypes.data, P.ctypes.data, c.ctypes.data, x0.ctypes.data, b, e, float(t_end),
                            G, g.ctypes.data, int(seed), int(stream), int(max_events), int(schedule), w.ctypes.data,
                            mu.ctypes.data, view.ctypes.data)
@@ -360,6 +376,7 @@ def avg_xy(net, n_traj: int, t_end: float, seed: int, window: int, traj_begin: i
         t = np.zeros(max(cap, 1))
         mean = np.zeros((max(cap, 1), S))
         msq = np.zeros((max(cap, 1), S))
+        keep = _set_modifiers(L, net)  # noqa: F841
         rc = L.oracle_avg_xy(S, M, R.ctypes.data, P.ctypes.data, c.ctypes.data, x0.ctypes.data, int(traj_begin),
                              int(n_traj), float(t_end), int(seed), int(stream), int(max_events), int(schedule),
                              int(precision), int(window), cap, t.ctypes.data, mean.ctypes.data, msq.ctypes.data,

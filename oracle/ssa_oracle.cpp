@@ -56,6 +56,7 @@
 //
 // Build: g++ -O2 -ffp-contract=off (no FMA contraction), no -ffast-math.
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <limits>
@@ -155,7 +156,25 @@ struct Model {
   std::vector<int32_t> R, P, nu;  // M x S
   std::vector<double> c;          // M
   std::vector<int32_t> x0;        // S
+  // rate modifiers (state-dependent rates): reaction j with mod_f[j] >= 0
+  // uses min(max(c_j + mod_k[j] * x_{mod_f[j]}, mod_lo[j]), mod_hi[j])
+  std::vector<int32_t> mod_f;
+  std::vector<double> mod_k, mod_lo, mod_hi;
 };
+
+// Modifiers for the models the calling thread builds next (set by
+// oracle_set_modifiers; empty = plain mass action).
+thread_local std::vector<int32_t> t_mod_f;
+thread_local std::vector<double> t_mod_k, t_mod_lo, t_mod_hi;
+
+// The rate of reaction j in state x: c_j, or for a modified reaction the
+// clamped linear function of its modifier species' count (FP64: one product,
+// one sum, then the clamp).
+double rate(const Model& m, int j, const std::vector<int64_t>& x) {
+  if (m.mod_f.empty() || m.mod_f[j] < 0) return m.c[j];
+  const double v = m.c[j] + m.mod_k[j] * (double)x[m.mod_f[j]];
+  return std::fmin(std::fmax(v, m.mod_lo[j]), m.mod_hi[j]);
+}
 
 // Mass-action combinatorial factor: h_j(x) = prod_s C(x_s, R_js)  (R_js in 0..2).
 int64_t mass_action_h(const Model& m, int j, const std::vector<int64_t>& x) {
@@ -304,7 +323,7 @@ TrajResult run_one(const Model& m, uint64_t traj_id, double t_end, int G, const 
     double a0 = 0.0;
     float a0_32 = 0.0f;
     if (precision == 0) {
-      for (int j = 0; j < m.M; ++j) a[j] = m.c[j] * (double)mass_action_h(m, j, x);
+      for (int j = 0; j < m.M; ++j) a[j] = rate(m, j, x) * (double)mass_action_h(m, j, x);
       if (schedule == 0) {
         for (int j = 0; j < m.M; ++j) { a0 = (j == 0) ? a[0] : a0 + a[j]; prefix[j] = a0; }
       } else {
@@ -312,7 +331,7 @@ TrajResult run_one(const Model& m, uint64_t traj_id, double t_end, int G, const 
       }
     } else {
       for (int j = 0; j < m.M; ++j) {
-        a32[j] = (float)m.c[j] * (float)mass_action_h(m, j, x);
+        a32[j] = (float)m.c[j] * (float)mass_action_h(m, j, x);  // FP32 mode has no modifiers
         a_wide[j] = (double)a32[j];
         a[j] = a_wide[j];
       }
@@ -412,7 +431,7 @@ void run_one_grad(const Model& m, uint64_t traj_id, double t_end, int G, const d
   for (;;) {
     for (int j = 0; j < m.M; ++j) {
       h[j] = mass_action_h(m, j, x);
-      a[j] = m.c[j] * (double)h[j];
+      a[j] = rate(m, j, x) * (double)h[j];
     }
     double a0 = 0.0;
     if (schedule == 0) {
@@ -452,6 +471,13 @@ void run_one_grad(const Model& m, uint64_t traj_id, double t_end, int G, const d
 bool build_model(int S, int M, const int32_t* R, const int32_t* P, const double* c,
                  const int32_t* x0, Model* m) {
   if (S <= 0 || M <= 0) return false;
+  if (!t_mod_f.empty()) {
+    if ((int)t_mod_f.size() != M) return false;
+    m->mod_f = t_mod_f;
+    m->mod_k = t_mod_k;
+    m->mod_lo = t_mod_lo;
+    m->mod_hi = t_mod_hi;
+  }
   m->S = S; m->M = M;
   m->R.assign(R, R + (size_t)M * S);
   m->P.assign(P, P + (size_t)M * S);
@@ -508,6 +534,7 @@ int oracle_run(int S, int M, const int32_t* R, const int32_t* P, const double* c
     return -1;
   Model m;
   if (!build_model(S, M, R, P, c, x0, &m)) return -1;
+  if (precision == 1 && !m.mod_f.empty()) return -1;
   for (int64_t id = traj_begin; id < traj_end; ++id) {
     TrajResult r = run_one(m, (uint64_t)id, t_end, G, grid, seed, stream, max_events, schedule, precision,
                            (uint64_t*)S1, (uint64_t*)S2, S3, S4, 0, nullptr, nullptr);
@@ -619,6 +646,25 @@ int oracle_avg_xy(int S, int M, const int32_t* R, const int32_t* P, const double
   return 0;
 }
 
+// Sets (M > 0) or clears (M == 0) the rate modifiers of the models the
+// calling thread builds next: for reaction j with f[j] >= 0 the rate is
+// min(max(c_j + k[j] * x_{f[j]}, lo[j]), hi[j]) (the paper's TNF-dependent
+// infectivities, Sec. 2.1).  Returns 0.
+int oracle_set_modifiers(int M, const int32_t* f, const double* k, const double* lo, const double* hi) {
+  if (M <= 0) {
+    t_mod_f.clear();
+    t_mod_k.clear();
+    t_mod_lo.clear();
+    t_mod_hi.clear();
+    return 0;
+  }
+  t_mod_f.assign(f, f + M);
+  t_mod_k.assign(k, k + M);
+  t_mod_lo.assign(lo, lo + M);
+  t_mod_hi.assign(hi, hi + M);
+  return 0;
+}
+
 // Prefix sums of a[0..M) in the given schedule (0 = L, 1 = W32); for tests.
 void oracle_prefix(int M, const double* a, int schedule, double* prefix, double* a0) {
   std::vector<double> av(a, a + M), pv(M);
@@ -656,6 +702,7 @@ int oracle_grad(int S, int M, const int32_t* R, const int32_t* P, const double* 
   if (!g_log.ready || traj_end < traj_begin || G < 1 || (schedule != 0 && schedule != 1)) return -1;
   Model m;
   if (!build_model(S, M, R, P, c, x0, &m)) return -1;
+  if (!m.mod_f.empty()) return -1;  // the score below is for plain mass action
   for (int r = 0; r < M; ++r)
     if (!(c[r] > 0.0)) return -1;
   for (int64_t id = traj_begin; id < traj_end; ++id)

@@ -28,7 +28,7 @@ __all__ = [
     "Network", "Workload", "birth_death", "hiv_shaped", "isomerisation",
     "dimerisation", "random_network", "workload_birth_death",
     "workload_hiv_shaped", "workload_random", "batch_networks",
-    "tiny_networks",
+    "tiny_networks", "paper_hiv",
 ]
 
 
@@ -41,6 +41,9 @@ class Network:
     products: np.ndarray   # int32 [M, S], >= 0
     rates: np.ndarray      # float64 [M], stochastic rate constants c_j >= 0
     x0: np.ndarray         # int32 [S], initial counts >= 0
+    # state-dependent rates: (reaction j, species f, slope k, lo, hi) -- the
+    # rate of j is min(max(c_j + k x_f, lo), hi)
+    modifiers: list = field(default_factory=list)
 
     @property
     def n_species(self) -> int:
@@ -53,7 +56,21 @@ class Network:
     def with_rates(self, rates) -> "Network":
         return Network(self.name, list(self.species), self.reactants.copy(),
                        self.products.copy(), np.ascontiguousarray(rates, dtype=np.float64),
-                       self.x0.copy())
+                       self.x0.copy(), list(self.modifiers))
+
+    def modifier_arrays(self):
+        """(f [M] int32, k, lo, hi [M] float64) with f = -1 for unmodified
+        reactions, or None when the network has no modifiers."""
+        if not self.modifiers:
+            return None
+        M = self.n_reactions
+        f = np.full(M, -1, dtype=np.int32)
+        k = np.zeros(M)
+        lo = np.zeros(M)
+        hi = np.full(M, np.inf)
+        for j, sp, slope, a, b in self.modifiers:
+            f[j], k[j], lo[j], hi[j] = sp, slope, a, b
+        return f, k, lo, hi
 
 
 @dataclass
@@ -79,7 +96,7 @@ def _net(name, species, rxns, rates, x0) -> Network:
         for s, v in pd.items():
             P[j, idx[s]] += v
     return Network(name, list(species), R, P, np.asarray(rates, dtype=np.float64),
-                   np.asarray([x0[s] for s in species], dtype=np.int32))
+                   np.asarray([x0.get(s, 0) for s in species], dtype=np.int32))
 
 
 def birth_death(k1: float = 10.0, k2: float = 0.1, x0: int = 0) -> Network:
@@ -142,6 +159,55 @@ def random_network(seed: int, n_species: int = 32, n_reactions: int = 128,
     x0 = rng.integers(0, x0_hi + 1, size=S).astype(np.int32)
     return Network(f"random_s{S}_m{M}_seed{seed}", [f"X{i}" for i in range(S)], R, P,
                    rates.astype(np.float64), x0)
+
+
+def paper_hiv() -> Network:
+    """The paper's model of the immune response to HIV (Table 1, Sec. 2.1):
+    species U0 (constant source), U, T, Z5, Z4, I5, I4, V5, V4, F; 27
+    reactions with the stochastic rates of Sec. 2.1 used as stated (volume
+    1).  The bursts I -> 200 V consume the infected cell.  The infectivities
+    depend on TNF: beta_R5 = beta - K F (clamped to [0, beta]),
+    beta_X4 = beta + K F, gamma_R5/X4 = gamma -/+ K F, as rate modifiers.
+    Initial state U0 = 1, U = 200, T = 1000, Z4 = Z5 = 250, V5 = 100."""
+    lam, d_uf, d_ut, d_uz, d_t, d_tf = 200.0, 1e-5, 0.129, 0.005, 0.01, 1e-5
+    beta, gamma, K = 4e-5, 2e-5, 1e-7
+    s1, s2, s3, d_iz, mu, pi, d_i, d_z, d_v = 1e-4, 1e-3, 1e-4, 0.06, 2.5e-3, 200.0, 0.33, 0.01, 2.0
+    sp = ["U0", "U", "T", "Z5", "Z4", "I5", "I4", "V5", "V4", "F"]
+    rx = [
+        ({"U0": 1}, {"U0": 1, "U": 1}, lam),
+        ({"U": 1, "F": 1}, {"F": 1}, d_uf),
+        ({"U": 1}, {"T": 1}, d_ut),
+        ({"U": 1}, {"Z4": 1}, d_uz),
+        ({"U": 1}, {"Z5": 1}, d_uz),
+        ({"T": 1}, {}, d_t),
+        ({"T": 1, "F": 1}, {"F": 1}, d_tf),
+        ({"T": 1, "V5": 1}, {"I5": 1}, beta),          # beta_R5
+        ({"T": 1, "V4": 1}, {"I4": 1}, beta),          # beta_X4
+        ({"Z5": 1, "V5": 1}, {"I5": 1}, gamma),        # gamma_R5
+        ({"Z4": 1, "V4": 1}, {"I4": 1}, gamma),        # gamma_X4
+        ({"I5": 1}, {"I5": 1, "Z5": 1}, s2),
+        ({"I4": 1}, {"I4": 1, "Z4": 1}, s2),
+        ({"I5": 1, "Z5": 1}, {"U": 1, "I5": 1, "Z5": 1}, s1),
+        ({"I4": 1, "Z4": 1}, {"U": 1, "I4": 1, "Z4": 1}, s1),
+        ({"I5": 1, "Z5": 1}, {"Z5": 1}, d_iz),
+        ({"I4": 1, "Z4": 1}, {"Z4": 1}, d_iz),
+        ({"V5": 1}, {"V4": 1}, mu),
+        ({"I5": 1}, {"V5": 200}, pi),
+        ({"I4": 1}, {"V4": 200}, pi),
+        ({"V4": 1}, {"F": 1, "V4": 1}, s3),
+        ({"I5": 1}, {}, d_i),
+        ({"I4": 1}, {}, d_i),
+        ({"Z5": 1}, {}, d_z),
+        ({"Z4": 1}, {}, d_z),
+        ({"V5": 1}, {}, d_v),
+        ({"V4": 1}, {}, d_v),
+    ]
+    x0 = {"U0": 1, "U": 200, "T": 1000, "Z4": 250, "Z5": 250, "V5": 100}
+    net = _net("paper_hiv", sp, [(a, b) for a, b, _ in rx], [c for _, _, c in rx], x0)
+    F = sp.index("F")
+    net.modifiers = [(7, F, -K, 0.0, beta), (8, F, K, 0.0, float("inf")),
+                     (9, F, -K, 0.0, gamma), (10, F, K, 0.0, float("inf"))]
+    return net
 
 
 def hiv_target_rates(seed: int = 2) -> np.ndarray:
