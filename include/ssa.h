@@ -156,6 +156,23 @@ ssa_status ssa_model_create(int32_t n_species, int32_t n_reactions, const int32_
                             const int32_t* products, const double* rates, const int32_t* x0,
                             ssa_model** out);
 
+/*
+ * Makes the rate of `reaction` state dependent (the paper's TNF-dependent
+ * infectivities, Sec. 2.1: beta_R5 = beta - K F clamped to [0, beta],
+ * beta_X4 = beta + K F):
+ *   rate = min(max(c + slope * x_species, lo), hi)      (FP64: product, sum, clamp)
+ * where c is the reaction's rate constant; the propensity is rate * h(x).
+ * species = -1 removes the modifier.  0 <= lo <= hi, lo finite (hi may be
+ * +infinity); slope finite.  Models with modifiers run FP64 on the warp
+ * schedule (ssa_ensemble_run, ssa_ensemble_avg_xy, FP64 batches); the
+ * thread schedule, FP32 mode, ssa_ensemble_grad and ssa_ensemble_run_noalloc
+ * refuse them (SSA_EUNSUPPORTED).  Not thread-safe against runs of the same
+ * model in flight.
+ * Errors: SSA_EINVAL.
+ */
+ssa_status ssa_model_set_rate_modifier(ssa_model* model, int32_t reaction, int32_t species, double slope, double lo,
+                                       double hi);
+
 /* Releases a model and its device copies.  NULL is ignored.  No run using the
  * model may be pending on any stream. */
 void ssa_model_destroy(ssa_model* model);

@@ -30,6 +30,7 @@ EXPORTS = [
     "ssa_model_info", "ssa_ensemble_workspace_size", "ssa_ensemble_run", "ssa_ensemble_run_noalloc",
     "ssa_batch_create", "ssa_batch_tune", "ssa_batch_launch", "ssa_batch_result", "ssa_batch_network_stats",
     "ssa_batch_destroy", "ssa_batch_run", "ssa_ensemble_grad", "ssa_ensemble_avg_xy",
+    "ssa_model_set_rate_modifier",
 ]
 
 
@@ -81,6 +82,8 @@ def lib():
         L.ssa_run_opts_init.restype = None
         L.ssa_model_create.argtypes = [i32, i32, vp, vp, vp, vp, ctypes.POINTER(vp)]
         L.ssa_model_create.restype = ctypes.c_int
+        L.ssa_model_set_rate_modifier.argtypes = [vp, i32, i32, f64, f64, f64]
+        L.ssa_model_set_rate_modifier.restype = ctypes.c_int
         L.ssa_model_destroy.argtypes = [vp]
         L.ssa_model_destroy.restype = None
         L.ssa_model_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
@@ -140,7 +143,16 @@ class Model:
 
     @classmethod
     def from_network(cls, net) -> "Model":
-        return cls(net.reactants, net.products, net.rates, net.x0)
+        m = cls(net.reactants, net.products, net.rates, net.x0)
+        for j, sp, slope, lo, hi in getattr(net, "modifiers", []):
+            m.set_rate_modifier(j, sp, slope, lo, hi)
+        return m
+
+    def set_rate_modifier(self, reaction: int, species: int, slope: float, lo: float = 0.0,
+                          hi: float = float("inf")):
+        """ssa_model_set_rate_modifier: rate = min(max(c + slope x_species, lo), hi)."""
+        _check(lib().ssa_model_set_rate_modifier(self._h, int(reaction), int(species), float(slope), float(lo),
+                                                 float(hi)))
 
     @property
     def handle(self):

@@ -75,6 +75,11 @@ struct ssa_model {
          off_dep_idx = 0;
   SmallModel small = {};
   bool has_small = false;
+  // rate modifiers (ssa_model_set_rate_modifier); mod_f[j] = -1 when none
+  std::vector<int32_t> mod_f;
+  std::vector<double> mod_k, mod_lo, mod_hi;
+  bool has_mod = false;
+  size_t off_mod_f = 0, off_mod_k = 0, off_mod_lo = 0, off_mod_hi = 0;
   std::mutex mu;
   void* dev_image[kMaxDevices] = {};
 };
@@ -127,7 +132,7 @@ void plan_model(ssa_model* m) {
   std::vector<std::vector<int>> readers(S);
   for (int k = 0; k < M; ++k)
     for (int s = 0; s < S; ++s)
-      if (m->R[(size_t)k * S + s] > 0) readers[s].push_back(k);
+      if (m->R[(size_t)k * S + s] > 0 || (m->has_mod && m->mod_f[k] == s)) readers[s].push_back(k);
   m->dep_ptr.assign(M + 1, 0);
   m->dep_idx.clear();
   std::vector<char> mark(M, 0);
@@ -144,8 +149,8 @@ void plan_model(ssa_model* m) {
     for (int k : deps) m->dep_idx.push_back(k);
     m->dep_ptr[j + 1] = (int32_t)m->dep_idx.size();
   }
-  // by-value tables of the thread kernel
-  m->has_small = (M <= kSmallMax && S <= kSmallMax);
+  // by-value tables of the thread kernel (plain mass action only)
+  m->has_small = (M <= kSmallMax && S <= kSmallMax && !m->has_mod);
   if (m->has_small) {
     SmallModel& sm = m->small;
     std::memset(&sm, 0, sizeof sm);
@@ -169,6 +174,12 @@ void plan_model(ssa_model* m) {
   m->off_x0 = put(img, m->x0.data(), sizeof(int32_t) * S);
   m->off_dep_ptr = put(img, m->dep_ptr.data(), sizeof(int32_t) * (M + 1));
   m->off_dep_idx = put(img, m->dep_idx.data(), sizeof(int32_t) * m->dep_idx.size());
+  if (m->has_mod) {
+    m->off_mod_f = put(img, m->mod_f.data(), sizeof(int32_t) * M);
+    m->off_mod_k = put(img, m->mod_k.data(), sizeof(double) * M);
+    m->off_mod_lo = put(img, m->mod_lo.data(), sizeof(double) * M);
+    m->off_mod_hi = put(img, m->mod_hi.data(), sizeof(double) * M);
+  }
   img.resize(align_up(img.size(), 16));
 }
 
@@ -200,6 +211,10 @@ ssa_status model_on_device(const ssa_model* cm, int dev, DevModel* out) {
   out->x0 = reinterpret_cast<const int32_t*>(b + m->off_x0);
   out->dep_ptr = reinterpret_cast<const int32_t*>(b + m->off_dep_ptr);
   out->dep_idx = reinterpret_cast<const int32_t*>(b + m->off_dep_idx);
+  out->mod_f = m->has_mod ? reinterpret_cast<const int32_t*>(b + m->off_mod_f) : nullptr;
+  out->mod_k = m->has_mod ? reinterpret_cast<const double*>(b + m->off_mod_k) : nullptr;
+  out->mod_lo = m->has_mod ? reinterpret_cast<const double*>(b + m->off_mod_lo) : nullptr;
+  out->mod_hi = m->has_mod ? reinterpret_cast<const double*>(b + m->off_mod_hi) : nullptr;
   return SSA_OK;
 }
 
@@ -325,6 +340,49 @@ ssa_status ssa_model_create(int32_t S, int32_t M, const int32_t* R, const int32_
   return SSA_OK;
 }
 
+ssa_status ssa_model_set_rate_modifier(ssa_model* m, int32_t reaction, int32_t species, double slope, double lo,
+                                       double hi) {
+  g_last_error.clear();
+  if (!m) return fail(SSA_EINVAL, "model is NULL");
+  if (reaction < 0 || reaction >= m->M) return fail(SSA_EINVAL, "reaction %d out of range", reaction);
+  if (species < -1 || species >= m->S) return fail(SSA_EINVAL, "species %d out of range", species);
+  if (!std::isfinite(slope)) return fail(SSA_EINVAL, "slope must be finite");
+  if (!(lo >= 0.0) || !std::isfinite(lo) || !(hi >= lo)) return fail(SSA_EINVAL, "need 0 <= lo <= hi (hi may be +inf)");
+  std::lock_guard<std::mutex> lk(m->mu);
+  if (!m->has_mod) {
+    m->mod_f.assign(m->M, -1);
+    m->mod_k.assign(m->M, 0.0);
+    m->mod_lo.assign(m->M, 0.0);
+    m->mod_hi.assign(m->M, 0.0);
+  }
+  m->mod_f[reaction] = species;
+  m->mod_k[reaction] = slope;
+  m->mod_lo[reaction] = lo;
+  m->mod_hi[reaction] = hi;
+  m->has_mod = false;
+  for (int j = 0; j < m->M; ++j)
+    if (m->mod_f[j] >= 0) m->has_mod = true;
+  if (!m->has_mod) {
+    m->mod_f.clear();
+    m->mod_k.clear();
+    m->mod_lo.clear();
+    m->mod_hi.clear();
+  }
+  // the device copies are stale: free them (made again at the next run)
+  int prev = -1;
+  cudaGetDevice(&prev);
+  for (int d = 0; d < kMaxDevices; ++d) {
+    if (m->dev_image[d]) {
+      cudaSetDevice(d);
+      cudaFree(m->dev_image[d]);
+      m->dev_image[d] = nullptr;
+    }
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  plan_model(m);
+  return SSA_OK;
+}
+
 void ssa_model_destroy(ssa_model* m) {
   if (!m) return;
   int prev = -1;
@@ -370,6 +428,8 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
     if (st != SSA_OK) return st;
   }
   const bool fp32 = o.precision == SSA_PREC_FP32;
+  if (m->has_mod && (fp32 || o.schedule == SSA_SCHED_THREAD))
+    return fail(SSA_EUNSUPPORTED, "models with rate modifiers run FP64 on the warp schedule");
   if (fp32) {
     if (o.schedule == SSA_SCHED_THREAD)
       return fail(SSA_EUNSUPPORTED, "the FP32-propensity mode runs on the warp schedule");
@@ -579,6 +639,7 @@ bool model_image_view(const ssa_model* m, ModelImageView* v) {
   v->off_dep_ptr = m->off_dep_ptr;
   v->off_dep_idx = m->off_dep_idx;
   v->small = m->has_small ? &m->small : nullptr;
+  v->has_mod = m->has_mod;
   return true;
 }
 

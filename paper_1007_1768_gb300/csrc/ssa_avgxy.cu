@@ -337,6 +337,11 @@ extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj
   if (o.memory != SSA_MEM_HOST && o.memory != SSA_MEM_DEVICE) return (ssa_status)set_error(SSA_EINVAL, "bad memory kind");
   if (o.schedule == SSA_SCHED_THREAD)
     return (ssa_status)set_error(SSA_EUNSUPPORTED, "the event log runs on the warp schedule");
+  {
+    ModelImageView mv0;
+    if (model_image_view(model, &mv0) && mv0.has_mod && o.precision == SSA_PREC_FP32)
+      return (ssa_status)set_error(SSA_EUNSUPPORTED, "models with rate modifiers run FP64");
+  }
   if (o.max_events <= 0) o.max_events = SSA_DEFAULT_MAX_EVENTS;
   const long long k = window ? window : n_traj;
   ModelImageView mv;

@@ -378,6 +378,9 @@ ssa_status ssa_batch_create(int32_t n_models, const ssa_model* const* models, co
         if (!(gr[k] >= gr[k - 1])) return bail(set_error(SSA_EINVAL, "grids must be ascending"));
       if (!(gr[n_grid[i] - 1] <= t_end[i])) return bail(set_error(SSA_EINVAL, "grid values must be <= t_end"));
     }
+    ModelImageView mv;
+    if (b->fp32 && model_image_view(m, &mv) && mv.has_mod)
+      return bail(set_error(SSA_EUNSUPPORTED, "models with rate modifiers run FP64"));
     if (b->fp32) {
       const double* c = model_rates(m);
       for (int j = 0; j < M; ++j)
@@ -491,6 +494,10 @@ ssa_status ssa_batch_create(int32_t n_models, const ssa_model* const* models, co
     w.grid = dgrid;
     w.D1 = reinterpret_cast<unsigned long long*>(s + b->off_d1[i]);
     w.D2 = reinterpret_cast<unsigned long long*>(s + b->off_d2[i]);
+    w.mod_f = dm.mod_f;
+    w.mod_k = dm.mod_k;
+    w.mod_lo = dm.mod_lo;
+    w.mod_hi = dm.mod_hi;
     double te = b->t_end[i];
     std::memcpy(&w.t_end_bits, &te, 8);
     w.S = b->S[i];

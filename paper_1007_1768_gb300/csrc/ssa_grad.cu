@@ -358,6 +358,8 @@ extern "C" ssa_status ssa_ensemble_grad(const ssa_model* model, int64_t n_traj, 
     return (ssa_status)set_error(SSA_EUNSUPPORTED, "gradients replay the thread schedule");
   ModelImageView mv;
   if (!model_image_view(model, &mv)) return (ssa_status)set_error(SSA_EINVAL, "bad model");
+  if (mv.has_mod)
+    return (ssa_status)set_error(SSA_EUNSUPPORTED, "gradients take plain mass-action models (no rate modifiers)");
   if (!mv.small)
     return (ssa_status)set_error(SSA_EUNSUPPORTED, "gradients take networks of at most 16 reactions and 16 species");
   const double* c = model_rates(model);

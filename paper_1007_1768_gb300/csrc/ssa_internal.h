@@ -40,6 +40,12 @@ struct DevModel {
   const int32_t* x0;
   const int32_t* dep_ptr;
   const int32_t* dep_idx;
+  // rate modifiers (null when the model has none): reaction j with
+  // mod_f[j] >= 0 has rate min(max(c_j + mod_k[j] x_{mod_f[j]}, mod_lo[j]), mod_hi[j])
+  const int32_t* mod_f;
+  const double* mod_k;
+  const double* mod_lo;
+  const double* mod_hi;
 };
 
 // Slots of the per-run device totals.
@@ -186,7 +192,8 @@ struct ModelImageView {
   const unsigned char* image;
   size_t bytes;
   size_t off_c, off_rinfo, off_nu_ptr, off_nu_idx, off_nu_val, off_x0, off_dep_ptr, off_dep_idx;
-  const SmallModel* small;  // filled when M <= 16 and S <= 16
+  const SmallModel* small;  // filled when M <= 16, S <= 16 and no rate modifiers
+  bool has_mod;             // rate modifiers present (warp schedule, FP64 only)
 };
 
 // Launch shape of the thread kernel.

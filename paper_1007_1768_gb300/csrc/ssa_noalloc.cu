@@ -172,6 +172,8 @@ extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n
   a.m.x0 = reinterpret_cast<const int32_t*>(b + mv.off_x0);
   a.m.dep_ptr = reinterpret_cast<const int32_t*>(b + mv.off_dep_ptr);
   a.m.dep_idx = reinterpret_cast<const int32_t*>(b + mv.off_dep_idx);
+  a.m.mod_f = nullptr;  // the thread schedule serves plain mass action only
+  a.m.mod_k = a.m.mod_lo = a.m.mod_hi = nullptr;
   a.G = n_grid;
   a.N = n_traj;
   a.traj_offset = o.traj_offset;

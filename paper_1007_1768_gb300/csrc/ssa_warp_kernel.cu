@@ -12,9 +12,11 @@ namespace {
 
 // Shared-memory layout of the warp kernel (bytes).
 struct WarpSmem {
-  size_t log_inv, log_lnf, cbits, c32, rinfo, nu_ptr, nu_idx, nu_val, x0, depw, x, total;
+  size_t log_inv, log_lnf, cbits, c32, rinfo, nu_ptr, nu_idx, nu_val, x0, depw, mod, x, total;
 };
 
+// The rate-modifier tables (4 x M words) are always reserved: they are small
+// and keep the layout independent of the model's contents.
 __host__ __device__ inline WarpSmem warp_smem_layout(int M, int S, int nnz, int warps) {
   WarpSmem L;
   size_t o = 0;
@@ -28,6 +30,7 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int M, int S, int nnz, int 
   L.nu_val = o; o += align_up((size_t)nnz * 4, 16);
   L.x0 = o; o += align_up((size_t)S * 4, 16);
   L.depw = o; o += align_up((size_t)M * 32 * 2, 16);
+  L.mod = o; o += align_up((size_t)M * 4, 16) + (size_t)M * 24;
   L.x = o; o += align_up((size_t)warps * S * 4, 16);
   L.total = o;
   return L;
@@ -71,6 +74,19 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a, const EventLo
   }
   for (int s = tid; s < S; s += T) s_x0[s] = a.m.x0[s];
   for (int i = tid; i < M * 32; i += T) s_depw[i] = depw_entry(a.m.dep_ptr, a.m.dep_idx, ch, i >> 5, i & 31);
+  int32_t* s_modf = reinterpret_cast<int32_t*>(smem + L.mod);
+  double* s_modk = reinterpret_cast<double*>(smem + L.mod + align_up((size_t)M * 4, 16));
+  double* s_modlo = s_modk + M;
+  double* s_modhi = s_modlo + M;
+  const bool has_mod = a.m.mod_f != nullptr;
+  if (has_mod) {
+    for (int j = tid; j < M; j += T) {
+      s_modf[j] = a.m.mod_f[j];
+      s_modk[j] = a.m.mod_k[j];
+      s_modlo[j] = a.m.mod_lo[j];
+      s_modhi[j] = a.m.mod_hi[j];
+    }
+  }
   if (tid < 4) blk[tid] = 0ULL;
   __syncthreads();
 
@@ -86,6 +102,10 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a, const EventLo
   net.grid = a.grid;
   net.D1 = a.D1;
   net.D2 = a.D2;
+  net.mod_f = has_mod ? s_modf : nullptr;
+  net.mod_k = has_mod ? s_modk : nullptr;
+  net.mod_lo = has_mod ? s_modlo : nullptr;
+  net.mod_hi = has_mod ? s_modhi : nullptr;
   net.t_end_bits = obits(a.t_end);
   net.S = S;
   net.M = M;

@@ -66,6 +66,10 @@ struct WarpNet {
   const double* grid;                 // [G]
   unsigned long long* D1;             // [G * S] difference sums
   unsigned long long* D2;
+  const int32_t* mod_f;               // [M] rate modifiers, or null (see DevModel)
+  const double* mod_k;
+  const double* mod_lo;
+  const double* mod_hi;
   long long t_end_bits;
   int S, M, G;
   int grid_uniform;
@@ -215,8 +219,17 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
         if constexpr (F32) {
           af[q] = __fmul_rn(net.c32[j], __ll2float_rn(h));
         } else {
+          unsigned long long cb = net.cbits[j];
+          if (net.mod_f != nullptr) {  // state-dependent rate: clamp(c + k x_f, lo, hi), FP64
+            const int f = net.mod_f[j];
+            if (f >= 0) {
+              const double v = __dadd_rn(__longlong_as_double((long long)cb),
+                                         __dmul_rn(net.mod_k[j], (double)xs[f]));
+              cb = (unsigned long long)obits(fmin(fmax(v, net.mod_lo[j]), net.mod_hi[j]));
+            }
+          }
           unsigned long long ab;
-          if (!propensity_int(net.cbits[j], h, ab)) ab = propensity_fp64(net.cbits[j], h);
+          if (!propensity_int(cb, h, ab)) ab = propensity_fp64(cb, h);
           av[q] = __longlong_as_double((long long)ab);
         }
       }

@@ -173,3 +173,21 @@ def test_batch_arguments_are_refused_before_touching_the_gpu():
         ssa.Batch([m], [10], [1.0], [11], block_threads=96)
     assert e.value.status == binding.SSA_EINVAL
     m.close()
+
+
+def test_rate_modifier_arguments_are_checked_before_touching_the_gpu():
+    m = ssa.Model([[1, 0]], [[0, 0]], [0.5], [4, 3])
+    for args in [(1, 1, 0.1, 0.0, 1.0), (0, 2, 0.1, 0.0, 1.0), (0, 1, float("nan"), 0.0, 1.0),
+                 (0, 1, 0.1, -1.0, 1.0), (0, 1, 0.1, 2.0, 1.0)]:
+        with pytest.raises(ssa.SSAError) as e:
+            m.set_rate_modifier(*args)
+        assert e.value.status == binding.SSA_EINVAL, args
+    m.set_rate_modifier(0, 1, 0.1, 0.0, float("inf"))
+    with pytest.raises(ssa.SSAError) as e:
+        ssa.ensemble_run(m, 10, 1.0, 3, seed=1, schedule="thread")
+    assert e.value.status == binding.SSA_EUNSUPPORTED and "modifier" in str(e.value)
+    with pytest.raises(ssa.SSAError) as e:
+        ssa.ensemble_run(m, 10, 1.0, 3, seed=1, precision="fp32")
+    assert e.value.status == binding.SSA_EUNSUPPORTED
+    m.set_rate_modifier(0, -1, 0.0, 0.0, 0.0)  # removed again
+    m.close()
