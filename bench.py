@@ -58,6 +58,12 @@ WORKLOADS = {
     "grad": {"factory": "workload_hiv_shaped", "name": "hiv_shaped_grad_S4_M10_G3001_T30_loss_V", "n_traj": 1048576,
              "steps": 5, "e2e_steps": 2, "cpu_sample": 2048, "ref_sample": 1024,
              "kernel": "k_ssa_grad", "dram_bytes": 336896},
+    "paper_hiv": {"factory": "workload_paper_hiv", "name": "paper_hiv_S10_M27_G1001_T10_tnf_modifiers",
+                  "n_traj": 4096, "steps": 3, "e2e_steps": 1, "cpu_sample": 48, "ref_sample": 16,
+                  "kernel": "k_ssa_warp", "dram_bytes": None},
+    "avgxy": {"factory": "workload_hiv_shaped", "name": "hiv_shaped_avg_xy_S4_M10_T30_window_N", "n_traj": 65536,
+              "steps": 5, "e2e_steps": 1, "cpu_sample": 16, "ref_sample": 16,
+              "kernel": "k_ssa_warp (logging) + radix sort", "dram_bytes": None},
     "batch": {"factory": None, "name": "batch256_S4-64_M8-512_N1024-65536_G501_T10_fp32", "n_traj": None,
               "steps": 2, "e2e_steps": 1, "cpu_sample": 16, "ref_sample": 16,
               "kernel": "k_ssa_batch", "dram_bytes": 4043520},
@@ -76,8 +82,10 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="hiv_shaped",
-                   help="hiv_shaped: 4 species / 10 reactions, 65,536 trajectories, thread kernel; random: "
-                        "32 species / 128 reactions, 262,144 trajectories, warp kernel")
+                   help="hiv_shaped (headline): 4 species / 10 reactions, 65,536 trajectories, thread kernel; "
+                        "random: 32 x 128, 262,144 trajectories, warp kernel; paper_hiv: the paper's 27-reaction "
+                        "model with TNF-dependent rates; batch: 256 uneven networks in one graph; grad: rate "
+                        "gradient on 1,048,576 trajectories; avgxy: Avg-Y / Avg-XY selective memory")
     p.add_argument("--n-traj", type=int, default=None, help="trajectories per GPU (default per workload)")
     p.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
                    help="fp32: binary32 propensities and selection sums, FP64 a0 and time (one trajectory "
@@ -99,7 +107,7 @@ def parse_args():
     spec = WORKLOADS[args.workload]
     args.steps = spec["steps"] if args.steps is None else args.steps
     args.n_traj = spec["n_traj"] if args.n_traj is None else args.n_traj
-    if args.workload in ("batch", "grad") and args.impl == "reference":
+    if args.workload in ("batch", "grad", "avgxy") and args.impl == "reference":
         p.error("--impl reference times the forward single-network workloads")
     args.e2e_steps = spec["e2e_steps"] if args.e2e_steps is None else args.e2e_steps
     return args
@@ -178,7 +186,7 @@ def oracle_mode(args):
     """(schedule, precision) of the oracle matching the GPU run: the warp
     layout's W32 order for the random network, FP32 when asked."""
     import oracle
-    schedule = oracle.SCHEDULE_W32 if args.workload == "random" else oracle.SCHEDULE_L
+    schedule = oracle.SCHEDULE_W32 if args.workload in ("random", "paper_hiv") else oracle.SCHEDULE_L
     precision = oracle.PRECISION_FP32 if getattr(args, "precision", "fp64") == "fp32" else oracle.PRECISION_FP64
     return schedule, precision
 
@@ -589,6 +597,77 @@ def ssa_events_estimate(events_total, steps):
     return events_total / 2 / steps
 
 
+def run_avgxy(args):
+    """Selective memory along the time axis on the HIV-shaped model: one step
+    is one ssa_ensemble_avg_xy call (the ensemble run to size the event log,
+    the logging run, the radix sort of ~1e8 event records by time, union
+    indices, window sums) with window k = N, outputs copied to the host."""
+    import numpy as np
+    import torch
+
+    import paper_1007_1768_gb300 as ssa
+    import workloads as W
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    spec = WORKLOADS["avgxy"]
+    n = args.n_traj
+    w = W.workload_hiv_shaped(n)
+    model = ssa.Model.from_network(w.net)
+    M = w.net.n_reactions
+    for i in range(args.warmup):
+        ssa.ensemble_avg_xy(model, n, w.t_end, 1 + i, n, traj_offset=rank * n)
+    r = ssa.ensemble_run(model, n, w.t_end, 2, 1, schedule="warp", traj_offset=rank * n)
+    events_per_run = r.events
+    stream = torch.cuda.current_stream()
+    K = args.steps
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    ms = []
+    info = None
+    for i in range(K):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t, m, q, U = ssa.ensemble_avg_xy(model, n, w.t_end, 1000 + i, n, traj_offset=rank * n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        info = (len(t), U)
+    clk = clocks.stop()
+    total_ms = sum(ms)
+    value = world * events_per_run * K / (total_ms * 1e-3)
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    peak = FP64_OPS_PER_SM_CLK * SMS_GB300 * sm_mhz * 1e6 * 1e-9
+    achieved = 2 * (2 * M + 2) * events_per_run / (total_ms / K * 1e-3) * 1e-9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": spec["name"], "n_traj_per_gpu": n, "t_end": w.t_end, "window": n,
+                       "windows": info[0], "union_points": info[1],
+                       "events": "events of one ensemble (the call simulates it twice: sizing and logging)",
+                       "parallelism": f"replicas x{world} (trajectory-id shards)"},
+            "roofline": {"bound": "alu", "kernel": spec["kernel"], "achieved": achieved, "peak": peak,
+                         "unit": "GFLOP/s (FP64 ops)", "frac": achieved / peak, "traffic": None,
+                         "ops_per_event": "2 x (2M + 2): two simulation passes",
+                         "peak_basis": "2 FP64 ops/clk/SM x 152 SMs x median SM clock"},
+            "cpu_baseline": None,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": int(info[0] * (1 + 2 * w.net.n_species) * 8),
+                    "note": "the timed call is the host API: outputs copied back inside the timed region"},
+            "gpu_launches": None,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    model.close()
+    return 0
+
+
 def run_batch(args):
     """The uneven batch of 256 random networks in one graph replay per step
     (FP32 propensities, FP64 time): persistent kernels per register bucket,
@@ -791,6 +870,8 @@ def main():
         return run_batch(args)
     if args.workload == "grad":
         return run_grad(args)
+    if args.workload == "avgxy":
+        return run_avgxy(args)
     return run_ours(args)
 
 

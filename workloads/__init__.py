@@ -210,6 +210,12 @@ def paper_hiv() -> Network:
     return net
 
 
+def workload_paper_hiv(n_traj: int = 4096, seed: int = 1) -> Workload:
+    """The paper's HIV model over 10 days (about 3.8e5 events per trajectory),
+    1001-point grid."""
+    return Workload(paper_hiv(), n_traj, 10.0, 1001, seed)
+
+
 def hiv_target_rates(seed: int = 2) -> np.ndarray:
     """Rates of the HIV-shaped model each scaled by exp(U(-0.2, 0.2)), seeded:
     the parameters whose ensemble mean of V is the gradient workload's target."""
