@@ -178,21 +178,6 @@ SF_HD uint64_t div_pos(uint64_t nb, uint64_t db, bool& ok) {
   return r;
 }
 
-// (float)v for 0 <= v < 2^63, round to nearest even, as binary32 bits
-// (integer operations only): the 24-bit significand below the leading one,
-// a guard bit and a sticky bit.
-SF_HD uint32_t u63_to_f32(uint64_t v) {
-  const int lz = clz64(v | 1ULL);
-  const uint64_t top = v << lz;                       // leading one at bit 63 (v > 0)
-  uint32_t mant = (uint32_t)(top >> 40);              // 24 bits with the leading one
-  const uint32_t rbit = (uint32_t)(top >> 39) & 1u;
-  const uint32_t st = ((top & ((1ULL << 39) - 1)) != 0) ? 1u : 0u;
-  mant += rbit & (st | (mant & 1u));                  // a carry out moves into the exponent
-  // biased exponent 127 + 63 - lz; the significand's leading one adds 1 to the field
-  const uint32_t bits = ((uint32_t)(189 - lz) << 23) + mant;
-  return (v == 0) ? 0u : bits;
-}
-
 // Exact widening of a non-negative binary32 value (zero, subnormal, normal
 // or +inf, given by its bits) to binary64, returned as bits.  Normal values
 // rebias the exponent (127 -> 1023) and move the significand up 29 bits;
