@@ -117,6 +117,12 @@ typedef struct ssa_run_opts {
    * after the simulation kernel (for timing it alone); NULL to skip. */
   void* sim_event_begin;
   void* sim_event_end;
+  /* ssa_ensemble_avg_xy only: capacity of the event log in records; 0 = the
+   * records per trajectory of an earlier call on the same model (same t_end,
+   * precision, max_events) scaled with a margin, else the event count of a
+   * pilot of up to 4,096 trajectories scaled with a quarter to spare.  Too
+   * small a value costs one more logging run. */
+  int64_t log_records;
 } ssa_run_opts;
 
 /* Totals of one run (host struct). */
@@ -133,6 +139,11 @@ const char* ssa_status_string(ssa_status status);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* ssa_last_error(void);
+
+/* Returns the device memory that the library keeps between calls (its
+ * stream-ordered pools hold the workspaces of finished calls for reuse) to
+ * the driver.  Call when no library work is in flight.  Errors: SSA_ECUDA. */
+ssa_status ssa_release_cached_memory(void);
 
 /* Fills *opts with the defaults: FP64, AUTO schedule and reduction, host
  * memory, default max_events, offset 0, stream id 0, default CUDA stream,
@@ -245,8 +256,11 @@ ssa_status ssa_ensemble_grad(const ssa_model* model, int64_t n_traj, double t_en
  * happen).
  *
  * Union points T_0 = 0 < T_1 < ... < T_{U-1} are 0 and the distinct event
- * times of all n_traj trajectories (ids traj_offset + i, warp schedule,
- * opts->precision); S1_m[s] and S2_m[s] are the sums over trajectories of
+ * times of all n_traj trajectories (ids traj_offset + i, opts->precision);
+ * the trajectories are ssa_ensemble_run's under the same opts->schedule
+ * (AUTO: the thread schedule for FP64 networks of at most 16 reactions and
+ * species without rate modifiers, else the warp schedule).
+ * S1_m[s] and S2_m[s] are the sums over trajectories of
  * x_s(T_m) and x_s(T_m)^2 (right-continuous states).  Window p covers union
  * points [p k, min(U, (p + 1) k)) with n_p points, k = window (0: n_traj):
  *   t_out[p]         = (T_pk + ... ) / n_p      (FP64, ascending order)
@@ -256,10 +270,15 @@ ssa_status ssa_ensemble_grad(const ssa_model* model, int64_t n_traj, double t_en
  * mean and msq) in opts->memory's space; *n_points receives the number of
  * windows P (only min(P, max_points) are written; max_points = 0 only
  * counts) and *n_union (may be NULL) the number of union points U.
- * Runs the ensemble twice (once to size the event log, once writing it:
- * about 48 bytes of device memory per (event, species changed)); synchronous.
- * Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA, SSA_EUNSUPPORTED (thread
- * schedule, networks beyond the warp schedule, more than 2^31 log records),
+ * The event log takes about 48 bytes of device memory per (event, species
+ * changed); opts->log_records sizes it (0: an earlier call's count, else a
+ * pilot of up to 4,096 trajectories, estimates it).  Should the log run out,
+ * the logging run is repeated once with the exact record count it reports.
+ * Workspaces come from the library's pool (ssa_release_cached_memory).
+ * Synchronous.
+ * Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA, SSA_EUNSUPPORTED (the thread
+ * schedule for a network or mode it does not take, networks beyond the warp
+ * schedule, more than 2^31 log records),
  * SSA_EOVERFLOW (n_traj * max_x^2 * window could leave int64).
  */
 ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj, double t_end, uint64_t seed,

@@ -30,7 +30,7 @@ EXPORTS = [
     "ssa_model_info", "ssa_ensemble_workspace_size", "ssa_ensemble_run", "ssa_ensemble_run_noalloc",
     "ssa_batch_create", "ssa_batch_tune", "ssa_batch_launch", "ssa_batch_result", "ssa_batch_network_stats",
     "ssa_batch_destroy", "ssa_batch_run", "ssa_ensemble_grad", "ssa_ensemble_avg_xy",
-    "ssa_model_set_rate_modifier",
+    "ssa_model_set_rate_modifier", "ssa_release_cached_memory",
 ]
 
 
@@ -48,6 +48,7 @@ class RunOpts(ctypes.Structure):
         ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
         ("traj_events", ctypes.c_void_p), ("traj_hash", ctypes.c_void_p), ("traj_flags", ctypes.c_void_p),
         ("device_totals", ctypes.c_void_p), ("sim_event_begin", ctypes.c_void_p), ("sim_event_end", ctypes.c_void_p),
+        ("log_records", ctypes.c_int64),
     ]
 
 
@@ -115,6 +116,8 @@ def lib():
         L.ssa_ensemble_avg_xy.argtypes = [vp, i64, f64, u64, ctypes.POINTER(RunOpts), i64, i64, vp, vp, vp,
                                           ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.ssa_ensemble_avg_xy.restype = ctypes.c_int
+        L.ssa_release_cached_memory.argtypes = []
+        L.ssa_release_cached_memory.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -188,7 +191,7 @@ class EnsembleResult:
 
 def make_opts(precision="fp64", schedule="auto", reduce="auto", memory=MEM_HOST, max_events=0, traj_offset=0,
               stream_id=0, block_threads=0, grid_blocks=0, cuda_stream=None, workspace=None, workspace_bytes=0,
-              device_totals=None, sim_event_begin=None, sim_event_end=None):
+              device_totals=None, sim_event_begin=None, sim_event_end=None, log_records=0):
     o = RunOpts()
     lib().ssa_run_opts_init(ctypes.byref(o))
     o.precision = PREC[precision]
@@ -206,6 +209,7 @@ def make_opts(precision="fp64", schedule="auto", reduce="auto", memory=MEM_HOST,
     o.device_totals = device_totals
     o.sim_event_begin = sim_event_begin
     o.sim_event_end = sim_event_end
+    o.log_records = int(log_records)
     return o
 
 
@@ -311,26 +315,33 @@ def ensemble_avg_xy(model: Model, n_traj: int, t_end: float, seed: int, window: 
                     **opt_kw):
     """ssa_ensemble_avg_xy with host outputs: (t [P], mean [P, S], mean of
     x^2 [P, S], number of union points U).  window 0 means n_traj; window 1
-    gives Avg-Y on the union of event times."""
+    gives Avg-Y on the union of event times.  Without max_points, room for
+    65,536 windows is offered first and the call is repeated only when there
+    are more."""
     L = lib()
     S = model.n_species
     P = ctypes.c_int64()
     U = ctypes.c_int64()
-    cap = max_points
-    if cap is None:  # count first
+    cap = 65536 if max_points is None else int(max_points)
+    while True:
+        t = np.empty(max(cap, 1))
+        mean = np.empty((max(cap, 1), S))
+        msq = np.empty((max(cap, 1), S))
         opts = make_opts(memory=MEM_HOST, **opt_kw)
         _check(L.ssa_ensemble_avg_xy(model.handle, int(n_traj), float(t_end), int(seed), ctypes.byref(opts),
-                                     int(window), 0, None, None, None, ctypes.byref(P), ctypes.byref(U)))
+                                     int(window), int(cap), t.ctypes.data, mean.ctypes.data, msq.ctypes.data,
+                                     ctypes.byref(P), ctypes.byref(U)))
+        if max_points is not None or int(P.value) <= cap:
+            break
         cap = int(P.value)
-    t = np.empty(max(cap, 1))
-    mean = np.empty((max(cap, 1), S))
-    msq = np.empty((max(cap, 1), S))
-    opts = make_opts(memory=MEM_HOST, **opt_kw)
-    _check(L.ssa_ensemble_avg_xy(model.handle, int(n_traj), float(t_end), int(seed), ctypes.byref(opts),
-                                 int(window), int(cap), t.ctypes.data, mean.ctypes.data, msq.ctypes.data,
-                                 ctypes.byref(P), ctypes.byref(U)))
     n = min(int(P.value), int(cap))
     return t[:n], mean[:n], msq[:n], int(U.value)
+
+
+def release_cached_memory() -> None:
+    """ssa_release_cached_memory: return the workspaces the library keeps
+    between calls to the driver."""
+    _check(lib().ssa_release_cached_memory())
 
 
 def _ptr_array(ptrs):

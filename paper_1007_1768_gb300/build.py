@@ -18,7 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libssa.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["ssa_api.cu", "ssa_kernels.cu", "ssa_noalloc.cu", "ssa_thread_s4.cu", "ssa_thread_s8.cu",
-           "ssa_thread_s16.cu", "ssa_warp_kernel.cu",
+           "ssa_thread_s16.cu", "ssa_thread_log_s4.cu", "ssa_thread_log_s8.cu", "ssa_thread_log_s16.cu",
+           "ssa_warp_kernel.cu",
            "ssa_batch.cu", "ssa_grad.cu", "ssa_avgxy.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "-I" + INCLUDE]

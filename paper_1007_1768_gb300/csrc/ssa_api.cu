@@ -45,6 +45,9 @@ struct DeviceInfo {
 };
 std::mutex g_dev_mutex;
 DeviceInfo g_dev[kMaxDevices];
+// Library-owned stream-ordered pools (one per device, made on first use) that
+// keep freed memory for the next call instead of returning it to the driver.
+cudaMemPool_t g_pool[kMaxDevices] = {};
 
 ssa_status device_info(int dev, DeviceInfo* out) {
   if (dev < 0 || dev >= kMaxDevices) return fail(SSA_EUNSUPPORTED, "device index %d out of range", dev);
@@ -82,6 +85,9 @@ struct ssa_model {
   size_t off_mod_f = 0, off_mod_k = 0, off_mod_lo = 0, off_mod_hi = 0;
   std::mutex mu;
   void* dev_image[kMaxDevices] = {};
+  // event-log records per trajectory seen by earlier ssa_ensemble_avg_xy
+  // calls, by (t_end, precision, schedule, max_events); guarded by mu
+  std::vector<LogSize> log_sizes;
 };
 
 namespace {
@@ -359,6 +365,7 @@ ssa_status ssa_model_set_rate_modifier(ssa_model* m, int32_t reaction, int32_t s
   m->mod_k[reaction] = slope;
   m->mod_lo[reaction] = lo;
   m->mod_hi[reaction] = hi;
+  m->log_sizes.clear();
   m->has_mod = false;
   for (int j = 0; j < m->M; ++j)
     if (m->mod_f[j] >= 0) m->has_mod = true;
@@ -380,6 +387,15 @@ ssa_status ssa_model_set_rate_modifier(ssa_model* m, int32_t reaction, int32_t s
   }
   if (prev >= 0) cudaSetDevice(prev);
   plan_model(m);
+  return SSA_OK;
+}
+
+ssa_status ssa_release_cached_memory(void) {
+  g_last_error.clear();
+  std::lock_guard<std::mutex> lk(g_dev_mutex);
+  for (int d = 0; d < kMaxDevices; ++d) {
+    if (g_pool[d]) SSA_CUDA_TRY(cudaMemPoolTrimTo(g_pool[d], 0));
+  }
   return SSA_OK;
 }
 
@@ -490,8 +506,8 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
     if (o.workspace_bytes < wl.total)
       return fail(SSA_EINVAL, "workspace of %zu bytes is smaller than the %zu needed", o.workspace_bytes, wl.total);
   } else {
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), wl.total, stream);
-    if (e != cudaSuccess) return fail(SSA_ENOMEM, "cudaMallocAsync(workspace): %s", cudaGetErrorString(e));
+    cudaError_t e = pool_malloc(reinterpret_cast<void**>(&ws), wl.total, stream);
+    if (e != cudaSuccess) return fail(SSA_ENOMEM, "workspace allocation: %s", cudaGetErrorString(e));
     own_ws = true;
   }
   auto release = [&]() {
@@ -619,6 +635,62 @@ int model_device_tables(const ssa_model* m, int dev, DevModel* out) {
 }
 
 const double* model_rates(const ssa_model* m) { return m->c.data(); }
+
+bool model_log_size_get(const ssa_model* m, const LogSize& key, double* per_traj) {
+  ssa_model* mm = const_cast<ssa_model*>(m);
+  std::lock_guard<std::mutex> lk(mm->mu);
+  for (const LogSize& e : mm->log_sizes) {
+    if (e.t_end == key.t_end && e.precision == key.precision && e.schedule == key.schedule &&
+        e.max_events == key.max_events) {
+      *per_traj = e.per_traj;
+      return true;
+    }
+  }
+  return false;
+}
+
+void model_log_size_put(const ssa_model* m, const LogSize& v) {
+  ssa_model* mm = const_cast<ssa_model*>(m);
+  std::lock_guard<std::mutex> lk(mm->mu);
+  for (LogSize& e : mm->log_sizes) {
+    if (e.t_end == v.t_end && e.precision == v.precision && e.schedule == v.schedule &&
+        e.max_events == v.max_events) {
+      e.per_traj = v.per_traj;
+      return;
+    }
+  }
+  if (mm->log_sizes.size() >= 16) mm->log_sizes.erase(mm->log_sizes.begin());
+  mm->log_sizes.push_back(v);
+}
+
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lk(g_dev_mutex);
+    if (!g_pool[dev]) {
+      cudaMemPoolProps props;
+      std::memset(&props, 0, sizeof props);
+      props.allocType = cudaMemAllocationTypePinned;
+      props.handleTypes = cudaMemHandleTypeNone;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaMemPool_t np;
+      if ((e = cudaMemPoolCreate(&np, &props)) != cudaSuccess) return e;
+      unsigned long long keep = ~0ULL;
+      if ((e = cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+        cudaMemPoolDestroy(np);
+        return e;
+      }
+      g_pool[dev] = np;
+    }
+    pool = g_pool[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
 
 void clear_error() { g_last_error.clear(); }
 

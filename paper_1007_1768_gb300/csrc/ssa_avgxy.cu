@@ -11,10 +11,17 @@
 //   mean_p = sum_m S1_m / (N n_p),  msq_p = sum_m S2_m / (N n_p).
 //
 // Pipeline:
-//   1. the warp kernel runs the ensemble once to count events and the
-//      largest count (capacity and overflow bounds), then again writing the
-//      event log: one record per (event, species changed) with the event
-//      time's bits, the species, v and (2 x_old + v) v;
+//   1. the event log is sized by the records per trajectory that an earlier
+//      call on the model saw (same t_end, precision, schedule, max_events),
+//      else by a pilot of up to 4,096 trajectories (its event count scaled
+//      to the ensemble, a quarter to spare); the thread kernel (FP64 networks
+//      of at most 16 reactions and species without rate modifiers, unless
+//      the warp schedule is asked for) or the warp kernel then runs the
+//      ensemble writing the log: one record per (event, species changed)
+//      with the event time's bits, the species, v and (2 x_old + v) v (one
+//      record with v = 0 for an event changing nothing).  Should the
+//      estimate fall short, the run is repeated once with the exact record
+//      count it reports;
 //   2. a stable least-significant-digit radix sort of the 64-bit time keys
 //      (8-bit digits; digits that are equal across all keys are skipped),
 //      carrying each record's index;
@@ -335,8 +342,6 @@ extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj
   if (max_points < 0 || (max_points > 0 && (!t_out || !mean_out || !msq_out)))
     return (ssa_status)set_error(SSA_EINVAL, "outputs of max_points entries are required");
   if (o.memory != SSA_MEM_HOST && o.memory != SSA_MEM_DEVICE) return (ssa_status)set_error(SSA_EINVAL, "bad memory kind");
-  if (o.schedule == SSA_SCHED_THREAD)
-    return (ssa_status)set_error(SSA_EUNSUPPORTED, "the event log runs on the warp schedule");
   {
     ModelImageView mv0;
     if (model_image_view(model, &mv0) && mv0.has_mod && o.precision == SSA_PREC_FP32)
@@ -347,7 +352,18 @@ extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj
   ModelImageView mv;
   if (!model_image_view(model, &mv)) return (ssa_status)set_error(SSA_EINVAL, "bad model");
   const int S = mv.S, M = mv.M;
-  if (warp_max_chunk(M) == 0) return (ssa_status)set_error(SSA_EUNSUPPORTED, "the warp schedule takes at most 512 reactions");
+  // one trajectory per thread when the network fits the thread kernel (FP64,
+  // at most 16 reactions and species, no rate modifiers), else one per warp
+  const bool fp32 = o.precision == SSA_PREC_FP32;
+  const bool thread_ok = mv.small != nullptr && !fp32;
+  if (o.schedule == SSA_SCHED_THREAD && !thread_ok)
+    return (ssa_status)set_error(SSA_EUNSUPPORTED,
+                                 "the thread schedule takes FP64 networks of at most 16 reactions and 16 species "
+                                 "without rate modifiers");
+  const bool use_thread = o.schedule == SSA_SCHED_THREAD || (o.schedule == SSA_SCHED_AUTO && thread_ok);
+  const int32_t sched = use_thread ? SSA_SCHED_THREAD : SSA_SCHED_WARP;
+  if (!use_thread && warp_max_chunk(M) == 0)
+    return (ssa_status)set_error(SSA_EUNSUPPORTED, "the warp schedule takes at most 512 reactions");
   // the largest number of species one reaction changes (records per event)
   const int32_t* nu_ptr = reinterpret_cast<const int32_t*>(mv.image + mv.off_nu_ptr);
   int max_nnz = 1;
@@ -356,10 +372,11 @@ extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj
     return (ssa_status)set_error(SSA_EUNSUPPORTED, "a reaction changes more species than an event-log chunk holds");
   cudaStream_t st = static_cast<cudaStream_t>(o.cuda_stream);
 
-  // pass 1: event count and largest count (warp schedule, one grid point)
+  // pilot: the event count of up to 4,096 of the trajectories sizes the log
+  const long long n_pilot = std::min<long long>(n_traj, 4096);
   ssa_run_opts o1 = o;
   o1.memory = SSA_MEM_DEVICE;
-  o1.schedule = SSA_SCHED_WARP;
+  o1.schedule = sched;
   o1.traj_events = nullptr;
   o1.traj_hash = nullptr;
   o1.traj_flags = nullptr;
@@ -367,17 +384,23 @@ extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj
   o1.workspace_bytes = 0;
   o1.device_totals = nullptr;
   o1.sim_event_begin = o1.sim_event_end = nullptr;
-  double* d_small = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_small), 16 * (size_t)S + 16, st);
-  if (e != cudaSuccess) return (ssa_status)set_error(SSA_ENOMEM, cudaGetErrorString(e));
+  if (o.log_records < 0) return (ssa_status)set_error(SSA_EINVAL, "opts->log_records must be >= 0");
   ssa_run_stats st1;
-  ssa_status rs = ssa_ensemble_run(model, n_traj, t_end, 1, nullptr, seed, &o1, d_small, d_small + S, nullptr, nullptr,
-                                   &st1);
-  cudaFreeAsync(d_small, st);
-  if (rs != SSA_OK) return rs;
-  const long double mx = (long double)st1.max_x;
-  if ((long double)n_traj * mx * mx * (long double)k >= 4.6e18L)
-    return (ssa_status)set_error(SSA_EOVERFLOW, "window sums of x^2 could leave int64 (N * max_x^2 * window)");
+  std::memset(&st1, 0, sizeof st1);
+  cudaError_t e = cudaSuccess;
+  // records per trajectory of an earlier call with the same model and key
+  LogSize lkey{t_end, o.precision, sched, o.max_events, 0.0};
+  double seen_per_traj = 0.0;
+  const bool seen = o.log_records == 0 && model_log_size_get(model, lkey, &seen_per_traj);
+  if (o.log_records == 0 && !seen) {
+    double* d_small = nullptr;
+    e = pool_malloc(reinterpret_cast<void**>(&d_small), 16 * (size_t)S + 16, st);
+    if (e != cudaSuccess) return (ssa_status)set_error(SSA_ENOMEM, cudaGetErrorString(e));
+    ssa_status rs = ssa_ensemble_run(model, n_pilot, t_end, 1, nullptr, seed, &o1, d_small, d_small + S, nullptr,
+                                     nullptr, &st1);
+    cudaFreeAsync(d_small, st);
+    if (rs != SSA_OK) return rs;
+  }
 
   int dev = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (ssa_status)set_error(SSA_ECUDA, cudaGetErrorString(e));
@@ -386,43 +409,53 @@ extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj
   DevModel dm;
   int mst = model_device_tables(model, dev, &dm);
   if (mst != SSA_OK) return (ssa_status)mst;
-  const int threads = 256;
-  const size_t smem = warp_kernel_smem(M, S, dm.nnz, threads);
-  if (smem > prop.sharedMemPerBlockOptin) return (ssa_status)set_error(SSA_EUNSUPPORTED, "network too large for shared memory");
-  int per_sm = 0;
-  const bool fp32 = o.precision == SSA_PREC_FP32;
-  if ((e = warp_log_kernel_prepare(M, fp32, smem, threads, &per_sm)) != cudaSuccess)
-    return (ssa_status)set_error(SSA_ECUDA, cudaGetErrorString(e));
-  if (per_sm < 1) return (ssa_status)set_error(SSA_EUNSUPPORTED, "the logging kernel cannot be resident");
-  const long long want = (n_traj + threads / 32 - 1) / (threads / 32);
-  const long long capb = (long long)prop.multiProcessorCount * per_sm;
-  const int blocks = (int)(want < capb ? want : capb);
-  const unsigned long long cap =
-      (unsigned long long)st1.events * (unsigned long long)max_nnz +
-      (unsigned long long)(blocks * (threads / 32) + 1) * (unsigned long long)kLogChunk * 2ULL;
-  if (cap >= (1ULL << 31))
-    return (ssa_status)set_error(SSA_EUNSUPPORTED, "the event log would exceed 2^31 records; use fewer trajectories");
+  int threads, blocks;
+  size_t smem;
+  unsigned long long slack;  // room for every writer's open chunk, twice
+  if (use_thread) {
+    LaunchPlan plan;
+    if (const char* msg = plan_thread_launch(S, M, 0, n_traj, prop.multiProcessorCount, prop.sharedMemPerBlockOptin,
+                                             SSA_REDUCE_GLOBAL, o.block_threads, o.grid_blocks, &plan))
+      return (ssa_status)set_error(SSA_EINVAL, msg);
+    threads = plan.threads;
+    blocks = plan.blocks;
+    smem = plan.smem;
+    if ((e = thread_log_kernel_set_smem(M, S, smem)) != cudaSuccess)
+      return (ssa_status)set_error(SSA_ECUDA, cudaGetErrorString(e));
+    slack = ((unsigned long long)blocks * (unsigned long long)threads + 1ULL) * (unsigned long long)kThreadLogChunk * 2ULL;
+  } else {
+    threads = 256;
+    smem = warp_kernel_smem(M, S, dm.nnz, threads);
+    if (smem > prop.sharedMemPerBlockOptin)
+      return (ssa_status)set_error(SSA_EUNSUPPORTED, "network too large for shared memory");
+    int per_sm = 0;
+    if ((e = warp_log_kernel_prepare(M, fp32, smem, threads, &per_sm)) != cudaSuccess)
+      return (ssa_status)set_error(SSA_ECUDA, cudaGetErrorString(e));
+    if (per_sm < 1) return (ssa_status)set_error(SSA_EUNSUPPORTED, "the logging kernel cannot be resident");
+    const long long want = (n_traj + threads / 32 - 1) / (threads / 32);
+    const long long capb = (long long)prop.multiProcessorCount * per_sm;
+    blocks = (int)(want < capb ? want : capb);
+    slack = (unsigned long long)(blocks * (threads / 32) + 1) * (unsigned long long)kLogChunk * 2ULL;
+  }
+  // capacity: the caller's; else the records per trajectory an earlier call
+  // saw, scaled, with a quarter plus 4 / sqrt(N) to spare; else the pilot's
+  // events scaled to all trajectories, with a quarter to spare (exact when
+  // the pilot is the whole ensemble)
+  unsigned long long cap;
+  if (o.log_records > 0) {
+    cap = (unsigned long long)o.log_records;
+  } else if (seen) {
+    const long double margin = 1.25L + 4.0L / std::sqrt((long double)n_traj);
+    cap = (unsigned long long)((long double)seen_per_traj * (long double)n_traj * margin) + slack;
+  } else {
+    const long double est = (long double)st1.events * (long double)n_traj / (long double)n_pilot;
+    cap = (unsigned long long)(est * (n_pilot == n_traj ? 1.0L : 1.25L)) * (unsigned long long)max_nnz + slack;
+  }
 
-  // device memory: one allocation
-  const long long ntiles = (long long)((cap + kSortTile - 1) / kSortTile);
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    const size_t at = off;
-    off = align_up(off + bytes, 256);
-    return at;
-  };
-  const size_t o_key = take(8 * cap), o_key2 = take(8 * cap), o_sp = take(4 * cap), o_ch = take(4 * cap),
-               o_d2 = take(8 * cap), o_perm = take(4 * cap), o_perm2 = take(4 * cap), o_head = take(4 * cap),
-               o_uidx = take(4 * cap), o_T = take(8 * (cap + 1)),
-               o_th = take(4 * (size_t)(256 * ntiles)), o_sc32 = take(4 * scan_scratch_elems<unsigned>(256 * ntiles + cap)),
-               o_hist = take(8 * 8 * 256), o_cnt = take(8 * 4), o_grid = take(8), o_d = take(16 * (size_t)S),
-               o_stats = take(8 * kStatCount), o_counter = take(8);
   unsigned char* ws = nullptr;
-  if ((e = cudaMallocAsync(reinterpret_cast<void**>(&ws), off, st)) != cudaSuccess)
-    return (ssa_status)set_error(SSA_ENOMEM, cudaGetErrorString(e));
   unsigned char* ws2 = nullptr;  // window arrays, sized after the union is known
   auto fail = [&](int status, const char* msg) {
-    cudaFreeAsync(ws, st);
+    if (ws) cudaFreeAsync(ws, st);
     if (ws2) cudaFreeAsync(ws2, st);
     return (ssa_status)set_error(status, msg);
   };
@@ -431,50 +464,94 @@ extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj
     const cudaError_t e_ = (expr);                                \
     if (e_ != cudaSuccess) return fail(SSA_ECUDA, cudaGetErrorString(e_)); \
   } while (0)
-  u64* key = reinterpret_cast<u64*>(ws + o_key);
+  size_t o_key = 0, o_key2 = 0, o_sp = 0, o_ch = 0, o_d2 = 0, o_perm = 0, o_perm2 = 0, o_head = 0, o_uidx = 0, o_T = 0,
+         o_th = 0, o_sc32 = 0, o_hist = 0, o_cnt = 0, o_grid = 0, o_d = 0, o_stats = 0, o_counter = 0;
+  long long ntiles = 0;
+  EventLog lg;
+  unsigned long long hc[5];
+  for (int attempt = 0;; ++attempt) {
+    if (cap >= (1ULL << 31))
+      return fail(SSA_EUNSUPPORTED, "the event log would exceed 2^31 records; use fewer trajectories");
+    // device memory: one allocation
+    ntiles = (long long)((cap + kSortTile - 1) / kSortTile);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+      const size_t at = off;
+      off = align_up(off + bytes, 256);
+      return at;
+    };
+    o_key = take(8 * cap); o_key2 = take(8 * cap); o_sp = take(4 * cap); o_ch = take(4 * cap);
+    o_d2 = take(8 * cap); o_perm = take(4 * cap); o_perm2 = take(4 * cap); o_head = take(4 * cap);
+    o_uidx = take(4 * cap); o_T = take(8 * (cap + 1));
+    o_th = take(4 * (size_t)(256 * ntiles)); o_sc32 = take(4 * scan_scratch_elems<unsigned>(256 * ntiles + cap));
+    o_hist = take(8 * 8 * 256); o_cnt = take(8 * 5); o_grid = take(8); o_d = take(16 * (size_t)S);
+    o_stats = take(8 * kStatCount); o_counter = take(8);
+    if ((e = pool_malloc(reinterpret_cast<void**>(&ws), off, st)) != cudaSuccess)
+      return fail(SSA_ENOMEM, cudaGetErrorString(e));
+    SSA_A_TRY(cudaMemsetAsync(ws + o_cnt, 0, 8 * 5, st));
+    SSA_A_TRY(cudaMemsetAsync(ws + o_d, 0, 16 * (size_t)S, st));
+    SSA_A_TRY(cudaMemsetAsync(ws + o_stats, 0, 8 * kStatCount, st));
+    SSA_A_TRY(cudaMemsetAsync(ws + o_counter, 0, 8, st));
+    SSA_A_TRY(cudaMemsetAsync(ws + o_hist, 0, 8 * 8 * 256, st));
+    k_fill_f64<<<1, 1, 0, st>>>(reinterpret_cast<double*>(ws + o_grid), t_end);
+    SSA_A_TRY(cudaGetLastError());
+    // the trajectories, writing the event log
+    RunArgs a;
+    std::memset(&a, 0, sizeof a);
+    if (use_thread) a.sm = *mv.small;
+    a.m = dm;
+    a.G = 0;  // no grid: the window sums come from the log
+    a.N = n_traj;
+    a.traj_offset = o.traj_offset;
+    a.seed = seed;
+    a.stream_id = o.stream_id;
+    a.max_events = o.max_events;
+    a.t_end = t_end;
+    a.grid = reinterpret_cast<const double*>(ws + o_grid);
+    a.D1 = reinterpret_cast<unsigned long long*>(ws + o_d);
+    a.D2 = a.D1 + S;
+    a.counter = reinterpret_cast<unsigned long long*>(ws + o_counter);
+    a.stats = reinterpret_cast<unsigned long long*>(ws + o_stats);
+    a.grid_uniform = 0;
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ws + o_cnt);  // counter, padded, overflow, -, needed
+    lg.key = reinterpret_cast<u64*>(ws + o_key);
+    lg.species = reinterpret_cast<int32_t*>(ws + o_sp);
+    lg.change = reinterpret_cast<int32_t*>(ws + o_ch);
+    lg.d2 = reinterpret_cast<long long*>(ws + o_d2);
+    lg.counter = cnt;
+    lg.padded = cnt + 1;
+    lg.overflow = cnt + 2;
+    lg.needed = cnt + 4;
+    lg.capacity = cap;
+    if (use_thread)
+      SSA_A_TRY(launch_thread_log_kernel(a, lg, blocks, threads, smem, st));
+    else
+      SSA_A_TRY(launch_warp_log_kernel(a, lg, fp32, blocks, threads, smem, st));
+    SSA_A_TRY(cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, st));
+    unsigned long long hstats[kStatCount];
+    SSA_A_TRY(cudaMemcpyAsync(hstats, ws + o_stats, sizeof hstats, cudaMemcpyDeviceToHost, st));
+    SSA_A_TRY(cudaStreamSynchronize(st));
+    if (hc[2] == 0) {
+      lkey.per_traj = (double)hc[4] / (double)n_traj;
+      model_log_size_put(model, lkey);
+      const long double mx = (long double)hstats[kStatMaxX];
+      if ((long double)n_traj * mx * mx * (long double)k >= 4.6e18L)
+        return fail(SSA_EOVERFLOW, "window sums of x^2 could leave int64 (N * max_x^2 * window)");
+      break;
+    }
+    if (attempt > 0) return fail(SSA_ECUDA, "the event log overflowed its capacity");
+    // the estimate was short: again with the exact record count, plus the
+    // padding bound (a chunk of C slots holds at least C - max_nnz + 1
+    // records before it is closed, losing at most max_nnz - 1 slots)
+    cudaFreeAsync(ws, st);
+    ws = nullptr;
+    const unsigned long long per = (unsigned long long)((use_thread ? kThreadLogChunk : kLogChunk) - max_nnz + 1);
+    cap = hc[4] + (hc[4] / per + 1) * (unsigned long long)(max_nnz - 1) + slack;
+  }
+  u64* key = lg.key;
   u64* key2 = reinterpret_cast<u64*>(ws + o_key2);
   unsigned int* perm = reinterpret_cast<unsigned int*>(ws + o_perm);
   unsigned int* perm2 = reinterpret_cast<unsigned int*>(ws + o_perm2);
-  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ws + o_cnt);  // counter, padded, overflow
-  SSA_A_TRY(cudaMemsetAsync(ws + o_cnt, 0, 8 * 4, st));
-  SSA_A_TRY(cudaMemsetAsync(ws + o_d, 0, 16 * (size_t)S, st));
-  SSA_A_TRY(cudaMemsetAsync(ws + o_stats, 0, 8 * kStatCount, st));
-  SSA_A_TRY(cudaMemsetAsync(ws + o_counter, 0, 8, st));
-  SSA_A_TRY(cudaMemsetAsync(ws + o_hist, 0, 8 * 8 * 256, st));
-  k_fill_f64<<<1, 1, 0, st>>>(reinterpret_cast<double*>(ws + o_grid), t_end);
-  SSA_A_TRY(cudaGetLastError());
-
-  // pass 2: the same trajectories, writing the event log
-  RunArgs a;
-  std::memset(&a, 0, sizeof a);
-  a.m = dm;
-  a.G = 1;
-  a.N = n_traj;
-  a.traj_offset = o.traj_offset;
-  a.seed = seed;
-  a.stream_id = o.stream_id;
-  a.max_events = o.max_events;
-  a.t_end = t_end;
-  a.grid = reinterpret_cast<const double*>(ws + o_grid);
-  a.D1 = reinterpret_cast<unsigned long long*>(ws + o_d);
-  a.D2 = a.D1 + S;
-  a.counter = reinterpret_cast<unsigned long long*>(ws + o_counter);
-  a.stats = reinterpret_cast<unsigned long long*>(ws + o_stats);
-  a.grid_uniform = 0;
-  EventLog lg;
-  lg.key = key;
-  lg.species = reinterpret_cast<int32_t*>(ws + o_sp);
-  lg.change = reinterpret_cast<int32_t*>(ws + o_ch);
-  lg.d2 = reinterpret_cast<long long*>(ws + o_d2);
-  lg.counter = cnt;
-  lg.padded = cnt + 1;
-  lg.overflow = cnt + 2;
-  lg.capacity = cap;
-  SSA_A_TRY(launch_warp_log_kernel(a, lg, fp32, blocks, threads, smem, st));
-  unsigned long long hc[4];
-  SSA_A_TRY(cudaMemcpyAsync(hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, st));
-  SSA_A_TRY(cudaStreamSynchronize(st));
-  if (hc[2]) return fail(SSA_ECUDA, "the event log overflowed its capacity");
   const long long n_all = (long long)std::min<unsigned long long>(hc[0], cap);
   const long long nv = n_all - (long long)hc[1];  // valid records; sentinels sort last
 
@@ -515,7 +592,7 @@ extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj
     k_heads<<<(unsigned)((nv + thr - 1) / thr), thr, 0, st>>>(key, nv, head);
     SSA_A_TRY(cudaGetLastError());
     SSA_A_TRY(cudaMemcpyAsync(uidx, head, 4 * (size_t)nv, cudaMemcpyDeviceToDevice, st));
-    unsigned int* dtot = reinterpret_cast<unsigned int*>(ws + o_cnt + 24);
+    unsigned int* dtot = reinterpret_cast<unsigned int*>(ws + o_cnt + 24);  // slot 3 of the counters
     SSA_A_TRY(device_exclusive_scan<unsigned int>(uidx, nv, sc, dtot, st));
     unsigned int heads = 0;
     SSA_A_TRY(cudaMemcpyAsync(&heads, dtot, 4, cudaMemcpyDeviceToHost, st));
@@ -545,7 +622,7 @@ extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj
   const size_t o_W1 = take2(8 * PS), o_A1 = take2(8 * PS), o_W2 = take2(8 * PS), o_A2 = take2(8 * PS),
                o_sc64 = take2(8 * scan_scratch_elems<long long>((long long)P) + 8), o_x0 = take2(4 * (size_t)S),
                o_t = take2(8 * (size_t)P), o_mean = take2(8 * PS), o_msq = take2(8 * PS);
-  if ((e = cudaMallocAsync(reinterpret_cast<void**>(&ws2), off2, st)) != cudaSuccess)
+  if ((e = pool_malloc(reinterpret_cast<void**>(&ws2), off2, st)) != cudaSuccess)
     return fail(SSA_ENOMEM, cudaGetErrorString(e));
   long long* W1 = reinterpret_cast<long long*>(ws2 + o_W1);
   long long* A1 = reinterpret_cast<long long*>(ws2 + o_A1);

@@ -129,6 +129,21 @@ cudaError_t launch_thread_s16(const RunArgs& a, int blocks, int threads, bool sh
 cudaError_t set_smem_s4(int M, bool shared_d, size_t smem);
 cudaError_t set_smem_s8(int M, bool shared_d, size_t smem);
 cudaError_t set_smem_s16(int M, bool shared_d, size_t smem);
+// logging variants for the Avg-XY pipeline (ssa_thread_log_s{4,8,16}.cu)
+struct EventLog;
+cudaError_t launch_thread_log_s4(const RunArgs& a, const EventLog& lg, int blocks, int threads, size_t smem,
+                                 cudaStream_t st);
+cudaError_t launch_thread_log_s8(const RunArgs& a, const EventLog& lg, int blocks, int threads, size_t smem,
+                                 cudaStream_t st);
+cudaError_t launch_thread_log_s16(const RunArgs& a, const EventLog& lg, int blocks, int threads, size_t smem,
+                                  cudaStream_t st);
+cudaError_t set_smem_log_s4(int M, size_t smem);
+cudaError_t set_smem_log_s8(int M, size_t smem);
+cudaError_t set_smem_log_s16(int M, size_t smem);
+// by S bucket (ssa_kernels.cu)
+cudaError_t launch_thread_log_kernel(const RunArgs& a, const EventLog& lg, int blocks, int threads, size_t smem,
+                                     cudaStream_t stream);
+cudaError_t thread_log_kernel_set_smem(int M, int S, size_t smem);
 cudaError_t launch_finalize(const unsigned long long* D1, const unsigned long long* D2, int G, int S,
                             int64_t N, const int32_t* x0, double* mean, double* var, int64_t* sum1,
                             int64_t* sum2, cudaStream_t stream);
@@ -156,7 +171,8 @@ cudaError_t thread_kernel_set_smem(int M, int S, bool shared_d, size_t smem_byte
 
 // Event log of the warp kernel (selective memory along the time axis): one
 // record per (kept event, species it changes), handed out in per-warp chunks.
-constexpr int kLogChunk = 256;
+constexpr int kLogChunk = 256;       // slots a warp of the warp kernel takes at a time
+constexpr int kThreadLogChunk = 32;  // slots a lane of the thread kernel takes at a time
 constexpr unsigned long long kLogSentinel = 0xFFFFFFFFFFFFFFFFULL;  // key of an unused slot
 struct EventLog {
   unsigned long long* key;       // [capacity] bits of the event time
@@ -166,6 +182,7 @@ struct EventLog {
   unsigned long long* counter;   // slots handed out (in chunks)
   unsigned long long* padded;    // unused slots (sentinel keys)
   unsigned long long* overflow;  // nonzero when the capacity ran out
+  unsigned long long* needed;    // records of every event, written or not (sized a retry)
   unsigned long long capacity;
 };
 
@@ -252,7 +269,20 @@ inline const char* plan_thread_launch(int S, int M, int G, int64_t N, int sms, s
 struct ssa_model;
 
 namespace ssa_impl {
+// Event-log records per trajectory of an earlier Avg-XY call, by its key.
+struct LogSize {
+  double t_end;
+  int32_t precision, schedule;
+  int64_t max_events;
+  double per_traj;
+};
 // Accessors implemented in ssa_api.cu.
+bool model_log_size_get(const ssa_model* m, const LogSize& key, double* per_traj);
+void model_log_size_put(const ssa_model* m, const LogSize& v);
+// Stream-ordered allocation from the library's pool on the current device
+// (freed memory stays in the pool for the next call; cudaFreeAsync frees,
+// ssa_release_cached_memory returns it to the driver).
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st);
 bool model_image_view(const ssa_model* m, ModelImageView* v);
 // The model's device tables on `dev` (copied there on first use); returns
 // SSA_OK or an error status with the thread's message set.

@@ -148,6 +148,23 @@ cudaError_t thread_kernel_set_smem(int M, int S, bool shared_d, size_t smem) {
   }
 }
 
+cudaError_t launch_thread_log_kernel(const RunArgs& a, const EventLog& lg, int blocks, int threads, size_t smem,
+                                     cudaStream_t stream) {
+  switch (bucket_s(a.m.S)) {
+    case 4: return launch_thread_log_s4(a, lg, blocks, threads, smem, stream);
+    case 8: return launch_thread_log_s8(a, lg, blocks, threads, smem, stream);
+    default: return launch_thread_log_s16(a, lg, blocks, threads, smem, stream);
+  }
+}
+
+cudaError_t thread_log_kernel_set_smem(int M, int S, size_t smem) {
+  switch (bucket_s(S)) {
+    case 4: return set_smem_log_s4(M, smem);
+    case 8: return set_smem_log_s8(M, smem);
+    default: return set_smem_log_s16(M, smem);
+  }
+}
+
 cudaError_t launch_finalize(const unsigned long long* D1, const unsigned long long* D2, int G, int S, int64_t N,
                             const int32_t* x0, double* mean, double* var, int64_t* sum1, int64_t* sum2,
                             cudaStream_t stream) {

@@ -21,6 +21,10 @@
 //     (2 x_old + v) v to the difference sums D1 / D2 at the first grid index
 //     with g_k >= t, for every species it changes by v; the finalize kernel
 //     scans them along the grid.
+//   * LOG (the Avg-Y / Avg-XY pipeline): a kept event also writes one record
+//     (time bits, species, v, (2 x_old + v) v) per species it changes -- one
+//     record with v = 0 when it changes none -- into the lane's current
+//     chunk of kThreadLogChunk slots of the event log.
 //
 // Three per-warp regimes give the same bits:
 //   * full warp (more than 8 trajectories): the products c_j h_j and the
@@ -135,6 +139,78 @@ __device__ __forceinline__ int grid_index(const RunArgs& a, long long tb, int k)
   return k;
 }
 
+// Per-lane position in the event log.
+struct ThreadLog {
+  unsigned long long base;    // first slot of the lane's chunk, or kLogSentinel when none
+  int fill;
+  bool failed;                // the capacity ran out: nothing more is written
+  unsigned long long total;   // records of this lane's events (written or not)
+  unsigned long long padded;  // sentinel slots this lane wrote
+};
+
+// Makes room for `cnt` (<= kThreadLogChunk) records: pads the old chunk's
+// tail with sentinels and takes a new chunk when it is full.  Returns false
+// when the capacity is exhausted.
+__device__ __forceinline__ bool thread_log_reserve(const EventLog& lg, ThreadLog& tl, int cnt) {
+  tl.total += (unsigned long long)cnt;
+  if (tl.failed) return false;
+  if (tl.base != kLogSentinel && tl.fill + cnt <= kThreadLogChunk) return true;
+  if (tl.base != kLogSentinel) {
+    for (int q = tl.fill; q < kThreadLogChunk; ++q) lg.key[tl.base + q] = kLogSentinel;
+    tl.padded += (unsigned long long)(kThreadLogChunk - tl.fill);
+  }
+  const unsigned long long b = atomicAdd(lg.counter, (unsigned long long)kThreadLogChunk);
+  if (b + kThreadLogChunk > lg.capacity) {
+    atomicExch(lg.overflow, 1ULL);
+    tl.base = kLogSentinel;
+    tl.failed = true;
+    return false;
+  }
+  tl.base = b;
+  tl.fill = 0;
+  return true;
+}
+
+// The records of a kept event at time bits tb; x is the state after it and
+// pv its change.
+template <int MAXS>
+__device__ __forceinline__ void thread_log_event(const EventLog& lg, ThreadLog& tl, long long tb,
+                                                 const int (&x)[MAXS], const int (&pv)[MAXS]) {
+  int nrec = 0;
+#pragma unroll
+  for (int s = 0; s < MAXS; ++s) nrec += (pv[s] != 0) ? 1 : 0;
+  const bool none = nrec == 0;
+  nrec = none ? 1 : nrec;
+  if (!thread_log_reserve(lg, tl, nrec)) return;
+  unsigned long long slot = tl.base + (unsigned long long)tl.fill;
+  if (none) {
+    lg.key[slot] = (unsigned long long)tb;
+    lg.species[slot] = 0;
+    lg.change[slot] = 0;
+    lg.d2[slot] = 0;
+  }
+#pragma unroll
+  for (int s = 0; s < MAXS; ++s) {
+    if (pv[s] != 0) {
+      const long long xo = (long long)x[s] - pv[s];
+      lg.key[slot] = (unsigned long long)tb;
+      lg.species[slot] = s;
+      lg.change[slot] = pv[s];
+      lg.d2[slot] = (2 * xo + pv[s]) * (long long)pv[s];
+      ++slot;
+    }
+  }
+  tl.fill += nrec;
+}
+
+// Pads the tail of the lane's last chunk (once, when the lane is done).
+__device__ __forceinline__ void thread_log_close(const EventLog& lg, ThreadLog& tl) {
+  if (tl.base == kLogSentinel) return;
+  for (int q = tl.fill; q < kThreadLogChunk; ++q) lg.key[tl.base + q] = kLogSentinel;
+  tl.padded += (unsigned long long)(kThreadLogChunk - tl.fill);
+  tl.base = kLogSentinel;
+}
+
 // Random numbers of event n of a trajectory: E = -ln(r1) and r2 = q2 2^-53,
 // both as double bit patterns.
 struct EventRandom {
@@ -239,11 +315,12 @@ __device__ __forceinline__ double prefix_sums(int M, Traj<MAXM, MAXS>& q) {
 }
 
 // Settle the pending event, whose waiting time is tau: keep it (grid index,
-// difference sums when `emit`, time, count, hash) or, past t_end, undo it.
+// difference sums and, LOG, the event-log records when `emit`, time, count,
+// hash) or, past t_end, undo it.
 // Returns true when the trajectory ends (flags set).
-template <int MAXM, int MAXS>
+template <bool LOG, int MAXM, int MAXS>
 __device__ __forceinline__ bool settle(const RunArgs& a, const StepEnv& e, Traj<MAXM, MAXS>& q, double tau,
-                                       bool emit) {
+                                       bool emit, const EventLog& lg, ThreadLog& tl) {
   const double t_next = __dadd_rn(q.t, tau);
   const long long tb = obits(t_next);
   const bool beyond = q.pend && tb > e.t_end_bits;  // not fired: undo
@@ -262,6 +339,9 @@ __device__ __forceinline__ bool settle(const RunArgs& a, const StepEnv& e, Traj<
       atomicAdd(e.d1 + (size_t)q.k * e.S + s, (unsigned long long)(long long)q.pv[s]);
       atomicAdd(e.d2 + (size_t)q.k * e.S + s, (unsigned long long)((2 * xo + q.pv[s]) * (long long)q.pv[s]));
     }
+  }
+  if constexpr (LOG) {
+    if (emit && keep) thread_log_event<MAXS>(lg, tl, tb, q.x, q.pv);
   }
   q.t = keep ? t_next : q.t;
   q.n += keep ? 1u : 0u;
@@ -315,8 +395,9 @@ __device__ __forceinline__ void draw(const StepEnv& e, Traj<MAXM, MAXS>& q, doub
 }
 
 // One thread-mode iteration.  Returns true when the trajectory has ended.
-template <bool DENSE, int MAXM, int MAXS>
-__device__ __forceinline__ bool thread_step(const RunArgs& a, const StepEnv& e, Traj<MAXM, MAXS>& q) {
+template <bool DENSE, bool LOG, int MAXM, int MAXS>
+__device__ __forceinline__ bool thread_step(const RunArgs& a, const StepEnv& e, Traj<MAXM, MAXS>& q,
+                                            const EventLog& lg, ThreadLog& tl) {
   // propensities the last event touched
   if (DENSE) {
     bool all_ok = true;
@@ -352,7 +433,7 @@ __device__ __forceinline__ bool thread_step(const RunArgs& a, const StepEnv& e, 
   const double a0 = prefix_sums(e.M, q);
   const EventRandom r_after = event_random(q.n + (q.pend ? 2u : 1u), q.traj_id, e.sid, e.key0, e.key1, e.s_inv,
                                            e.s_lnf);
-  const bool done = settle(a, e, q, tau, true);
+  const bool done = settle<LOG>(a, e, q, tau, true, lg, tl);
   const EventRandom r = q.rnd;
   q.rnd = r_after;
   draw(e, q, a0, r, done);
@@ -381,9 +462,9 @@ __device__ __forceinline__ T shfl_all(T v, int src, int width = 32) {
 // takes the g-th remaining trajectory: its state is copied to every lane of
 // the group, which then runs it event by event with the work split as
 // described at the top of this file.
-template <int MAXM, int MAXS>
+template <bool LOG, int MAXM, int MAXS>
 __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Traj<MAXM, MAXS>& q, unsigned act,
-                                         unsigned long long* blk) {
+                                         unsigned long long* blk, const EventLog& lg, ThreadLog& tl) {
   const int lane = threadIdx.x & 31;
   const int grp = lane / kCoopGroup;
   const int gl = lane % kCoopGroup;
@@ -468,7 +549,7 @@ __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Tra
     }
     const double tau = quotient(q.pend_E, q.pend_a0);
     const double a0 = prefix_sums(e.M, q);
-    const bool done = settle(a, e, q, tau, gl == 0) && q.have;
+    const bool done = settle<LOG>(a, e, q, tau, gl == 0, lg, tl) && q.have;
     // this event's random numbers, from the lane that holds them
     const int slot = (int)(q.n - base) & (kCoopGroup - 1);
     EventRandom r;
@@ -483,10 +564,10 @@ __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Tra
   }
 }
 
-template <int MAXM, int MAXS, bool SHARED_D>
-__global__ void __launch_bounds__(512) k_ssa_thread(const RunArgs a) {
+template <int MAXM, int MAXS, bool SHARED_D, bool LOG>
+__global__ void __launch_bounds__(512) k_ssa_thread(const RunArgs a, const EventLog lg) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long blk[4];  // events, truncated, overflowed, max x
+  __shared__ unsigned long long blk[6];  // events, truncated, overflowed, max x, log records, log padding
   const int S = a.m.S, M = a.m.M, G = a.G, T = blockDim.x, tid = threadIdx.x;
   const ThreadSmem L = thread_smem_layout(MAXM, MAXS, S, G, SHARED_D);
   uint64_t* s_inv = reinterpret_cast<uint64_t*>(smem + L.log_inv);
@@ -511,7 +592,7 @@ __global__ void __launch_bounds__(512) k_ssa_thread(const RunArgs a) {
       d2[i] = 0ULL;
     }
   }
-  if (tid < 4) blk[tid] = 0ULL;
+  if (tid < 6) blk[tid] = 0ULL;
   __syncthreads();
 
   StepEnv e;
@@ -557,6 +638,7 @@ __global__ void __launch_bounds__(512) k_ssa_thread(const RunArgs a) {
   q.pend_a0 = 0.0;
   q.rnd = EventRandom{0ULL, 0ULL};
   bool exhausted = false;  // this lane saw the work counter run out
+  ThreadLog tl{kLogSentinel, 0, false, 0ULL, 0ULL};
 
   // Every lane of the warp stays in this loop until the warp has no work, so
   // warp-wide votes see all 32 lanes.
@@ -574,11 +656,12 @@ __global__ void __launch_bounds__(512) k_ssa_thread(const RunArgs a) {
     if (act == 0u) break;
     const int nact = __popc(act);
     if (nact <= kCoopMaxTraj && __any_sync(kFullMask, exhausted)) {
-      coop_run(a, e, q, act, blk);
+      coop_run<LOG>(a, e, q, act, blk, lg, tl);
       break;
     }
     if (q.have) {
-      const bool done = (nact > kDenseLanes) ? thread_step<true>(a, e, q) : thread_step<false>(a, e, q);
+      const bool done = (nact > kDenseLanes) ? thread_step<true, LOG>(a, e, q, lg, tl)
+                                             : thread_step<false, LOG>(a, e, q, lg, tl);
       if (done) {
         finish_trajectory(a, q, blk);
         q.have = false;
@@ -586,6 +669,11 @@ __global__ void __launch_bounds__(512) k_ssa_thread(const RunArgs a) {
     }
   }
 
+  if constexpr (LOG) {
+    thread_log_close(lg, tl);
+    if (tl.total) atomicAdd(&blk[4], tl.total);
+    if (tl.padded) atomicAdd(&blk[5], tl.padded);
+  }
   __syncthreads();
   if (SHARED_D) {
     for (int i = tid; i < G * S; i += T) {
@@ -599,6 +687,10 @@ __global__ void __launch_bounds__(512) k_ssa_thread(const RunArgs a) {
     atomicAdd(a.stats + kStatTruncated, blk[1]);
     atomicAdd(a.stats + kStatOverflowed, blk[2]);
     atomicMax(a.stats + kStatMaxX, blk[3]);
+    if constexpr (LOG) {
+      if (blk[4]) atomicAdd(lg.needed, blk[4]);
+      if (blk[5]) atomicAdd(lg.padded, blk[5]);
+    }
     if (a.device_totals) {
       atomicAdd(a.device_totals + 0, blk[0]);
       atomicAdd(a.device_totals + 1, blk[1]);
@@ -608,54 +700,81 @@ __global__ void __launch_bounds__(512) k_ssa_thread(const RunArgs a) {
   }
 }
 
+#ifndef SSA_THREAD_LOG_ONLY
 template <int MAXM, int MAXS>
 cudaError_t launch_bucket(const RunArgs& a, int blocks, int threads, bool shared_d, size_t smem, cudaStream_t st) {
+  const EventLog none{};
   if (shared_d)
-    k_ssa_thread<MAXM, MAXS, true><<<blocks, threads, smem, st>>>(a);
+    k_ssa_thread<MAXM, MAXS, true, false><<<blocks, threads, smem, st>>>(a, none);
   else
-    k_ssa_thread<MAXM, MAXS, false><<<blocks, threads, smem, st>>>(a);
+    k_ssa_thread<MAXM, MAXS, false, false><<<blocks, threads, smem, st>>>(a, none);
   return cudaGetLastError();
 }
 
 template <int MAXM, int MAXS>
 cudaError_t set_smem_bucket(bool shared_d, size_t smem) {
   if (shared_d)
-    return cudaFuncSetAttribute(k_ssa_thread<MAXM, MAXS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_ssa_thread<MAXM, MAXS, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
-  return cudaFuncSetAttribute(k_ssa_thread<MAXM, MAXS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_ssa_thread<MAXM, MAXS, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem);
 }
+#else
+// The logging variants (difference sums in global memory; the Avg-XY
+// pipeline runs them with G = 0, so none are formed).
+template <int MAXM, int MAXS>
+cudaError_t launch_bucket(const RunArgs& a, const EventLog& lg, int blocks, int threads, size_t smem,
+                          cudaStream_t st) {
+  k_ssa_thread<MAXM, MAXS, false, true><<<blocks, threads, smem, st>>>(a, lg);
+  return cudaGetLastError();
+}
 
-// Dispatch on the M bucket for one S bucket.
+template <int MAXM, int MAXS>
+cudaError_t set_smem_bucket(size_t smem) {
+  return cudaFuncSetAttribute(k_ssa_thread<MAXM, MAXS, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+#endif
+
+// Dispatch on the M bucket for one S bucket (ARGS: the launch arguments).
+#define SSA_M_BUCKETS(FN, ...)                    \
+  switch (bucket_m(M)) {                          \
+    case 2: return FN<2, MAXS>(__VA_ARGS__);      \
+    case 4: return FN<4, MAXS>(__VA_ARGS__);      \
+    case 6: return FN<6, MAXS>(__VA_ARGS__);      \
+    case 8: return FN<8, MAXS>(__VA_ARGS__);      \
+    case 10: return FN<10, MAXS>(__VA_ARGS__);    \
+    case 12: return FN<12, MAXS>(__VA_ARGS__);    \
+    case 14: return FN<14, MAXS>(__VA_ARGS__);    \
+    case 16: return FN<16, MAXS>(__VA_ARGS__);    \
+    default: return cudaErrorInvalidValue;        \
+  }
+
+#ifndef SSA_THREAD_LOG_ONLY
 template <int MAXS>
 cudaError_t launch_for_s(const RunArgs& a, int blocks, int threads, bool shared_d, size_t smem, cudaStream_t st) {
-  switch (bucket_m(a.m.M)) {
-    case 2: return launch_bucket<2, MAXS>(a, blocks, threads, shared_d, smem, st);
-    case 4: return launch_bucket<4, MAXS>(a, blocks, threads, shared_d, smem, st);
-    case 6: return launch_bucket<6, MAXS>(a, blocks, threads, shared_d, smem, st);
-    case 8: return launch_bucket<8, MAXS>(a, blocks, threads, shared_d, smem, st);
-    case 10: return launch_bucket<10, MAXS>(a, blocks, threads, shared_d, smem, st);
-    case 12: return launch_bucket<12, MAXS>(a, blocks, threads, shared_d, smem, st);
-    case 14: return launch_bucket<14, MAXS>(a, blocks, threads, shared_d, smem, st);
-    case 16: return launch_bucket<16, MAXS>(a, blocks, threads, shared_d, smem, st);
-    default: return cudaErrorInvalidValue;
-  }
+  const int M = a.m.M;
+  SSA_M_BUCKETS(launch_bucket, a, blocks, threads, shared_d, smem, st)
 }
 
 template <int MAXS>
 cudaError_t set_smem_for_s(int M, bool shared_d, size_t smem) {
-  switch (bucket_m(M)) {
-    case 2: return set_smem_bucket<2, MAXS>(shared_d, smem);
-    case 4: return set_smem_bucket<4, MAXS>(shared_d, smem);
-    case 6: return set_smem_bucket<6, MAXS>(shared_d, smem);
-    case 8: return set_smem_bucket<8, MAXS>(shared_d, smem);
-    case 10: return set_smem_bucket<10, MAXS>(shared_d, smem);
-    case 12: return set_smem_bucket<12, MAXS>(shared_d, smem);
-    case 14: return set_smem_bucket<14, MAXS>(shared_d, smem);
-    case 16: return set_smem_bucket<16, MAXS>(shared_d, smem);
-    default: return cudaErrorInvalidValue;
-  }
+  SSA_M_BUCKETS(set_smem_bucket, shared_d, smem)
 }
+#else
+template <int MAXS>
+cudaError_t launch_log_for_s(const RunArgs& a, const EventLog& lg, int blocks, int threads, size_t smem,
+                             cudaStream_t st) {
+  const int M = a.m.M;
+  SSA_M_BUCKETS(launch_bucket, a, lg, blocks, threads, smem, st)
+}
+
+template <int MAXS>
+cudaError_t set_smem_log_for_s(int M, size_t smem) {
+  SSA_M_BUCKETS(set_smem_bucket, smem)
+}
+#endif
+#undef SSA_M_BUCKETS
 
 }  // namespace
 }  // namespace ssa_impl

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a, const EventLo
   net.grid_margin = a.grid_margin;
   net.sid = (uint32_t)a.stream_id;
   const uint32_t key0 = (uint32_t)a.seed, key1 = (uint32_t)(a.seed >> 32);
-  WarpLogState lst{kLogSentinel, 0};
+  WarpLogState lst{kLogSentinel, 0, false, 0ULL};
 
   for (;;) {
     unsigned long long next = 0;

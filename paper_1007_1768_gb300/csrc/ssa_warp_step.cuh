@@ -126,8 +126,10 @@ __host__ __device__ inline uint16_t depw_entry(const int32_t* dep_ptr, const int
 
 // Per-warp position in the current chunk (identical on every lane).
 struct WarpLogState {
-  unsigned long long base;  // first slot of the chunk, or kLogSentinel when none
+  unsigned long long base;   // first slot of the chunk, or kLogSentinel when none
   int fill;
+  bool failed;               // the capacity ran out: nothing more is written
+  unsigned long long total;  // records of this warp's events (written or not)
 };
 
 // Makes room for `cnt` (<= kLogChunk) records in this warp's chunk: pads the
@@ -135,6 +137,8 @@ struct WarpLogState {
 // Returns false (every lane) when the capacity is exhausted.
 __device__ __forceinline__ bool log_reserve(const EventLog& lg, WarpLogState& st, int cnt) {
   const int lane = threadIdx.x & 31;
+  st.total += (unsigned long long)cnt;
+  if (st.failed) return false;
   if (st.base != kLogSentinel && st.fill + cnt <= kLogChunk) return true;
   if (st.base != kLogSentinel) {
     for (int q = st.fill + lane; q < kLogChunk; q += 32) lg.key[st.base + q] = kLogSentinel;
@@ -146,6 +150,7 @@ __device__ __forceinline__ bool log_reserve(const EventLog& lg, WarpLogState& st
   if (b + kLogChunk > lg.capacity) {
     if (lane == 0) atomicExch(lg.overflow, 1ULL);
     st.base = kLogSentinel;
+    st.failed = true;
     return false;
   }
   st.base = b;
@@ -156,6 +161,7 @@ __device__ __forceinline__ bool log_reserve(const EventLog& lg, WarpLogState& st
 // Pads the tail of the warp's last chunk (call once, when the warp is done).
 __device__ __forceinline__ void log_close(const EventLog& lg, WarpLogState& st) {
   const int lane = threadIdx.x & 31;
+  if (lane == 0 && st.total) atomicAdd(lg.needed, st.total);
   if (st.base == kLogSentinel) return;
   for (int q = st.fill + lane; q < kLogChunk; q += 32) lg.key[st.base + q] = kLogSentinel;
   if (lane == 0) atomicAdd(lg.padded, (unsigned long long)(kLogChunk - st.fill));

@@ -13,19 +13,27 @@ pytestmark = pytest.mark.gpu
 W32 = oracle.SCHEDULE_W32
 
 
-def test_avg_xy_truncation_and_absorbing_states():
+@pytest.mark.parametrize("sched", ["thread", "warp"])
+def test_avg_xy_truncation_and_absorbing_states(sched):
+    osched = oracle.SCHEDULE_L if sched == "thread" else W32
     net = W.hiv_shaped()
     model = ssa.Model.from_network(net)
-    t, m, q, U = ssa.ensemble_avg_xy(model, 40, 30.0, 3, 7, max_events=25)
-    ot, om, oq, oU = oracle.avg_xy(net, 40, 30.0, 3, 7, max_events=25, schedule=W32)
+    t, m, q, U = ssa.ensemble_avg_xy(model, 40, 30.0, 3, 7, max_events=25, schedule=sched)
+    ot, om, oq, oU = oracle.avg_xy(net, 40, 30.0, 3, 7, max_events=25, schedule=osched)
     assert U == oU <= 40 * 25 + 1 and np.array_equal(t, ot) and np.array_equal(m, om) and np.array_equal(q, oq)
     model.close()
     death = W.Network("death", ["X"], np.array([[1]], np.int32), np.array([[0]], np.int32), np.array([2.0]),
                       np.array([5], np.int32))
     model = ssa.Model.from_network(death)
-    t, m, q, U = ssa.ensemble_avg_xy(model, 33, 50.0, 4, 1)
-    ot, om, oq, oU = oracle.avg_xy(death, 33, 50.0, 4, 1, schedule=W32)
+    t, m, q, U = ssa.ensemble_avg_xy(model, 33, 50.0, 4, 1, schedule=sched)
+    ot, om, oq, oU = oracle.avg_xy(death, 33, 50.0, 4, 1, schedule=osched)
     assert U == oU == 33 * 5 + 1 and np.array_equal(m, om) and m[-1, 0] == 0.0
+    if sched == "thread":  # the thread schedule is FP64 only
+        with pytest.raises(ssa.SSAError) as e:
+            ssa.ensemble_avg_xy(model, 33, 50.0, 4, 5, precision="fp32", schedule="thread")
+        assert e.value.status == ssa.binding.SSA_EUNSUPPORTED
+        model.close()
+        return
     # FP32 mode
     t, m, q, U = ssa.ensemble_avg_xy(model, 33, 50.0, 4, 5, precision="fp32")
     ot, om, oq, oU = oracle.avg_xy(death, 33, 50.0, 4, 5, schedule=W32, precision=oracle.PRECISION_FP32)
