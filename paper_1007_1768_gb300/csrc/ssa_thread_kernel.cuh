@@ -33,11 +33,15 @@
 //   * sparse warp: the hardware products and quotient (fewer instructions,
 //     latency hidden behind the prefix chain);
 //   * cooperative (at most 4 trajectories left and no new work): the warp
-//     splits into groups of 8 lanes, one trajectory per group.  The lanes of
-//     a group share the propensity products and precompute the random numbers
-//     of the next 8 events at once; the prefix chain, selection and update
-//     run replicated in every lane of the group.  This cuts the instructions
-//     per event of the long trajectories that end the run.
+//     splits into groups of 8 lanes, one trajectory per group, and runs it in
+//     batches of 8 events.  The lanes of a group share the propensity
+//     products; the prefix chain, selection and update run replicated and
+//     back to back for the 8 events, with nothing else on that chain.  Once
+//     per batch, lane b forms the random numbers and the waiting time of
+//     event b, the group forms the 8 event times in order and finds where
+//     the trajectory ends (later events of the batch are undone), and lane b
+//     does event b's grid index, difference sums and log records.  This cuts
+//     the cycles per event of the long trajectories that end the run.
 #ifndef SSA_THREAD_KERNEL_CUH_
 #define SSA_THREAD_KERNEL_CUH_
 
@@ -521,51 +525,171 @@ __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Tra
       }
     }
   }
-  // random numbers of events base .. base + 7, one per lane of the group
-  uint32_t base = 0;
-  EventRandom cache = {0ULL, 0ULL};
-  bool filled = false;
-
-  while (__any_sync(kFullMask, q.have)) {
-    // refresh every group's cache at once when any group may draw past its
-    // 8 (the groups advance in step, so they run out together); the next
-    // draw index is n or n + 1
-    const bool want = q.have && (!filled || q.n + 1u >= base + (uint32_t)kCoopGroup);
-    if (__any_sync(kFullMask, want)) {
-      base = q.n;
-      cache = event_random(base + (uint32_t)gl, q.traj_id, e.sid, e.key0, e.key1, e.s_inv, e.s_lnf);
-      filled = true;
-    }
-    // propensities: lane gl computes j = gl + 8 i when dirty
-#pragma unroll
-    for (int i = 0; i < kSlots; ++i) {
-      const int j = gl + kCoopGroup * i;
-      if (j < e.M && ((q.dirty >> j) & 1u)) mine[i] = propensity_fp64(mine_c[i], mass_action_h<MAXS>(mine_w[i], q.x));
-    }
-    // every propensity into every lane of the group
-#pragma unroll
-    for (int j = 0; j < MAXM; ++j) {
-      if (j < e.M) q.av[j] = shfl_all(mine[j / kCoopGroup], j % kCoopGroup, kCoopGroup);
-    }
+  // the pending event carried over from thread mode
+  {
     const double tau = quotient(q.pend_E, q.pend_a0);
-    const double a0 = prefix_sums(e.M, q);
     const bool done = settle<LOG>(a, e, q, tau, gl == 0, lg, tl) && q.have;
-    // this event's random numbers, from the lane that holds them
-    const int slot = (int)(q.n - base) & (kCoopGroup - 1);
-    EventRandom r;
-    r.E = shfl_all(cache.E, slot, kCoopGroup);
-    r.u2 = shfl_all(cache.u2, slot, kCoopGroup);
-    draw(e, q, a0, r, done || !q.have);
     if (done) {
       if (gl == 0) finish_trajectory(a, q, blk);
       q.have = false;
-      q.pend = false;
+    }
+    q.pend = false;
+  }
+
+  // Batches of kCoopGroup events.  The draws run back to back (selection and
+  // state update only); lane b keeps what event base + b needs afterwards
+  // (a0, the reaction, the state before it).  Then the waiting times (one
+  // quotient per lane), the event times in order, the end of the trajectory
+  // (past t_end, overflow or max_events: later events of the batch are
+  // undone) and the bookkeeping of the kept events (lane b: grid index,
+  // difference sums, log records, largest count).  Every group of a warp
+  // runs every step, so the shuffles see all 32 lanes.
+  while (__any_sync(kFullMask, q.have)) {
+    const uint32_t base = q.n;
+    const EventRandom rr = event_random(base + (uint32_t)gl, q.traj_id, e.sid, e.key0, e.key1, e.s_inv, e.s_lnf);
+    bool alive = q.have;  // the batch's events so far were applied
+    int nb = kCoopGroup;  // index of the first event that would overflow, else kCoopGroup
+    double my_a0 = 0.0;
+    int my_j = 0;
+#pragma unroll 1
+    for (int b = 0; b < kCoopGroup; ++b) {
+      // propensities: lane gl computes j = gl + 8 i when dirty
+#pragma unroll
+      for (int i = 0; i < kSlots; ++i) {
+        const int j = gl + kCoopGroup * i;
+        if (j < e.M && ((q.dirty >> j) & 1u))
+          mine[i] = propensity_fp64(mine_c[i], mass_action_h<MAXS>(mine_w[i], q.x));
+      }
+#pragma unroll
+      for (int j = 0; j < MAXM; ++j) {
+        if (j < e.M) q.av[j] = shfl_all(mine[j / kCoopGroup], j % kCoopGroup, kCoopGroup);
+      }
+      const double a0 = prefix_sums(e.M, q);
+      const unsigned long long u2 = shfl_all(rr.u2, b, kCoopGroup);
+      const long long gb = obits(__dmul_rn(__longlong_as_double((long long)u2), a0));
+      // first j with prefix_j > target, else the last j with a_j > 0
+      int cnt = 0;
+#pragma unroll
+      for (int j = 0; j < MAXM; ++j) {
+        if (j < e.M) cnt += (obits(q.pre[j]) <= gb) ? 1 : 0;
+      }
+      int jsel = cnt;
+      if (cnt >= e.M) {
+        jsel = 0;
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j) {
+          if (j < e.M && q.av[j] != 0ULL) jsel = j;
+        }
+      }
+      const int* row = e.s_nu + jsel * MAXS;
+      int rv[MAXS];
+      bool over = false;
+#pragma unroll
+      for (int s = 0; s < MAXS; ++s) {
+        rv[s] = row[s];
+        over |= (long long)q.x[s] + (long long)rv[s] > kStateMax;
+      }
+      if (gl == b) {
+        my_a0 = a0;
+        my_j = jsel;
+      }
+      const bool apply = alive && !over;
+      if (alive && over) nb = b;
+#pragma unroll
+      for (int s = 0; s < MAXS; ++s) q.x[s] += apply ? rv[s] : 0;
+      q.dirty = apply ? e.s_depmask[jsel] : 0u;
+      alive = apply;
+    }
+
+    // waiting times (lane b: event base + b), then the times in order
+    const double my_tau = quotient(rr.E, my_a0);
+    double tt = q.t;
+    unsigned long long h = q.hash;
+    int K = 0;      // events kept
+    int endf = -1;  // the trajectory ends: 0 past t_end, 1 max_events, 2 overflow
+    long long my_tb = 0;
+    int jb[kCoopGroup];
+#pragma unroll
+    for (int b = 0; b < kCoopGroup; ++b) {
+      const double tau_b = shfl_all(my_tau, b, kCoopGroup);
+      jb[b] = shfl_all(my_j, b, kCoopGroup);
+      const double t_b = __dadd_rn(tt, tau_b);
+      const long long tb_b = obits(t_b);
+      if (gl == b) my_tb = tb_b;
+      if (endf < 0) {
+        if (tb_b > e.t_end_bits) {
+          endf = 0;
+        } else if (b == nb) {
+          endf = 2;
+        } else {
+          K = b + 1;
+          tt = t_b;
+          const unsigned long long h1 = (h ^ (unsigned long long)jb[b]) * kFnvPrime;
+          h = (h1 ^ (unsigned long long)tb_b) * kFnvPrime;
+          if ((long long)base + K == a.max_events) endf = 1;
+        }
+      }
+    }
+    // undo the applied events that were not kept
+#pragma unroll
+    for (int b = 0; b < kCoopGroup; ++b) {
+      const bool undo = b >= K && b < nb;
+      const int* row = e.s_nu + jb[b] * MAXS;
+#pragma unroll
+      for (int s = 0; s < MAXS; ++s) q.x[s] -= undo ? row[s] : 0;
+    }
+    // bookkeeping of the kept events, lane b for event base + b
+    const bool mine_kept = q.have && gl < K;
+    int my_k = q.k;
+    int mx = 0;
+    if (mine_kept) {
+      my_k = grid_index(a, my_tb, q.k);
+      // the state after this lane's event: the state after the kept events
+      // less the changes of the later kept ones
+      int xa[MAXS], pv[MAXS];
+#pragma unroll
+      for (int s = 0; s < MAXS; ++s) xa[s] = q.x[s];
+#pragma unroll
+      for (int b = 1; b < kCoopGroup; ++b) {
+        if (b > gl && b < K) {
+          const int* rowb = e.s_nu + jb[b] * MAXS;
+#pragma unroll
+          for (int s = 0; s < MAXS; ++s) xa[s] -= rowb[s];
+        }
+      }
+      const int* row = e.s_nu + my_j * MAXS;
+#pragma unroll
+      for (int s = 0; s < MAXS; ++s) {
+        pv[s] = row[s];
+        if (pv[s] != 0) mx = max(mx, xa[s]);
+        if (pv[s] != 0 && my_k < e.G) {
+          const long long xo = (long long)xa[s] - pv[s];
+          atomicAdd(e.d1 + (size_t)my_k * e.S + s, (unsigned long long)(long long)pv[s]);
+          atomicAdd(e.d2 + (size_t)my_k * e.S + s, (unsigned long long)((2 * xo + pv[s]) * (long long)pv[s]));
+        }
+      }
+      if constexpr (LOG) thread_log_event<MAXS>(lg, tl, my_tb, xa, pv);
+    }
+#pragma unroll
+    for (int off = kCoopGroup / 2; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(kFullMask, mx, off, kCoopGroup));
+    const int k_last = shfl_all(my_k, K > 0 ? K - 1 : 0, kCoopGroup);
+    if (q.have) {
+      q.maxx = max(q.maxx, mx);
+      if (K > 0) q.k = k_last;
+      q.t = tt;
+      q.n = base + (uint32_t)K;
+      q.hash = h;
+      if (endf >= 0) {
+        q.flags = (endf == 1) ? 1 : ((endf == 2) ? 2 : 0);
+        if (gl == 0) finish_trajectory(a, q, blk);
+        q.have = false;
+      }
     }
   }
 }
 
 template <int MAXM, int MAXS, bool SHARED_D, bool LOG>
-__global__ void __launch_bounds__(512) k_ssa_thread(const RunArgs a, const EventLog lg) {
+__global__ void __launch_bounds__(512, 1) k_ssa_thread(const RunArgs a, const EventLog lg) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long blk[6];  // events, truncated, overflowed, max x, log records, log padding
   const int S = a.m.S, M = a.m.M, G = a.G, T = blockDim.x, tid = threadIdx.x;
