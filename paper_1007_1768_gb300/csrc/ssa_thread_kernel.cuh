@@ -310,10 +310,15 @@ __device__ __forceinline__ double quotient(unsigned long long Eb, double a0) {
 template <int MAXM, int MAXS>
 __device__ __forceinline__ double prefix_sums(int M, Traj<MAXM, MAXS>& q) {
   q.pre[0] = __longlong_as_double((long long)q.av[0]);
+  if (M == MAXM) {  // the bucket's own size: a plain chain
 #pragma unroll
-  for (int j = 1; j < MAXM; ++j) {
-    if (j < M) q.pre[j] = __dadd_rn(q.pre[j - 1], __longlong_as_double((long long)q.av[j]));
-    else q.pre[j] = q.pre[j - 1];
+    for (int j = 1; j < MAXM; ++j) q.pre[j] = __dadd_rn(q.pre[j - 1], __longlong_as_double((long long)q.av[j]));
+  } else {
+#pragma unroll
+    for (int j = 1; j < MAXM; ++j) {
+      if (j < M) q.pre[j] = __dadd_rn(q.pre[j - 1], __longlong_as_double((long long)q.av[j]));
+      else q.pre[j] = q.pre[j - 1];
+    }
   }
   return q.pre[MAXM - 1];
 }
@@ -560,9 +565,15 @@ __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Tra
         if (j < e.M && ((q.dirty >> j) & 1u))
           mine[i] = propensity_fp64(mine_c[i], mass_action_h<MAXS>(mine_w[i], q.x));
       }
+      // the changed ones into every lane of the group: one shuffle per
+      // reaction that any group of the warp recomputed
+      for (unsigned dm = __reduce_or_sync(kFullMask, q.dirty); dm != 0u; dm &= dm - 1u) {
+        const int j = __ffs((int)dm) - 1;
+        const unsigned long long v = shfl_all(j < kCoopGroup ? mine[0] : mine[kSlots - 1], j % kCoopGroup,
+                                              kCoopGroup);
+        const bool mine_changed = (q.dirty >> j) & 1u;
 #pragma unroll
-      for (int j = 0; j < MAXM; ++j) {
-        if (j < e.M) q.av[j] = shfl_all(mine[j / kCoopGroup], j % kCoopGroup, kCoopGroup);
+        for (int jj = 0; jj < MAXM; ++jj) q.av[jj] = (jj == j && mine_changed) ? v : q.av[jj];
       }
       const double a0 = prefix_sums(e.M, q);
       const unsigned long long u2 = shfl_all(rr.u2, b, kCoopGroup);
