@@ -43,7 +43,7 @@ SMS_GB300 = 152
 # DRAM read + write bytes of one k_ssa_thread launch (ncu capture summarised in
 # profiles/k_ssa_thread_hiv_shaped.md: tables, grid and parameters; the
 # difference sums stay in L2), independent of the number of trajectories.
-SIM_KERNEL_DRAM_BYTES = 841728
+SIM_KERNEL_DRAM_BYTES = 717824
 # Bench workloads: the HIV-shaped model (the headline line) and the random
 # 32-species / 128-reaction network (one trajectory per warp).
 WORKLOADS = {
@@ -101,6 +101,9 @@ def parse_args():
     p.add_argument("--scan", action="store_true",
                    help="time one ensemble per trajectory count (32 .. 1,048,576) and print, per count, the "
                         "cycles per event of its longest trajectory (the serial floor of the step)")
+    p.add_argument("--solo", type=int, default=None, metavar="ID",
+                   help="run trajectory ID of the HIV-shaped workload alone (seed 1000) and print its "
+                        "kernel time and cycles per event")
     p.add_argument("--probe", choices=["pipes", "latency", "step"],
                    help="build and run one of the pipe / latency / step-part probes in csrc/probes")
     args = p.parse_args()
@@ -849,6 +852,22 @@ def run_scan():
     return 0
 
 
+def run_solo(traj_id: int):
+    """One trajectory of the HIV-shaped workload (seed 1000) alone: with one
+    lane group of one warp busy, its kernel time is the serial chain of its
+    events (the cooperative mode from the first event)."""
+    import paper_1007_1768_gb300 as ssa
+    import workloads as W
+    w = W.workload_hiv_shaped()
+    model = ssa.Model.from_network(w.net)
+    for rep in range(3):
+        r = ssa.ensemble_run(model, 1, w.t_end, w.n_grid, 1000, traj_offset=traj_id, per_traj=True)
+        ev = int(r.traj_events[0])
+        print(json.dumps({"traj_id": traj_id, "events": ev, "kernel_ms": round(r.kernel_ms, 3),
+                          "cycles_per_event_at_2070MHz": round(r.kernel_ms * 2.07e6 / max(ev, 1), 1)}), flush=True)
+    return 0
+
+
 def run_probe(name: str):
     """Builds csrc/probes/probe_<name>.cu with nvcc for sm_103a and runs it."""
     from paper_1007_1768_gb300 import build as libbuild
@@ -866,6 +885,8 @@ def main():
         return run_scan()
     if args.probe:
         return run_probe(args.probe)
+    if args.solo is not None:
+        return run_solo(args.solo)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":

@@ -9,7 +9,8 @@
 
 constexpr int CHAIN = 2048;
 
-// mode: 0 dadd, 1 dmul, 2 ddiv, 3 iadd32, 4 imad32, 5 umul64hi, 6 dfma
+// mode: 0 dadd, 1 dmul, 2 ddiv, 3 iadd32, 4 imad32, 5 umul64hi, 6 dfma,
+// 7 two independent dadd chains (cycles per pair)
 template <int MODE>
 __device__ __forceinline__ void chain(double& d, unsigned long long& u, unsigned& w) {
   if (MODE == 0) { d = __dadd_rn(d, 1.0000000001); }
@@ -19,12 +20,18 @@ __device__ __forceinline__ void chain(double& d, unsigned long long& u, unsigned
   if (MODE == 4) { w = w * 2654435761u + 1u; }
   if (MODE == 5) { u = __umul64hi(u, 0x9E3779B97F4A7C15ull) + u; }
   if (MODE == 6) { d = __fma_rn(d, 0.9999999, 1e-9); }
+  if (MODE == 7) {
+    d = __dadd_rn(d, 1.0000000001);
+    u = (unsigned long long)__double_as_longlong(__dadd_rn(__longlong_as_double((long long)u), 1.5));
+  }
 }
 
 template <int MODE>
 __global__ void k_lat(long long* cycles, double* out, int active_lanes) {
   const int lane = threadIdx.x & 31;
-  double d = 1.0 + lane; unsigned long long u = 12345 + lane; unsigned w = 777 + lane;
+  double d = 1.0 + lane;
+  unsigned long long u = (MODE == 7) ? (unsigned long long)__double_as_longlong(2.0 + lane) : 12345ULL + lane;
+  unsigned w = 777 + lane;
   long long t0 = 0, t1 = 0;
   if (lane < active_lanes) {
     t0 = clock64();
@@ -89,6 +96,7 @@ int main() {
   if (run<0>("DADD", sms, d_cyc, d_out, e0, e1)) return 1;
   if (run<1>("DMUL", sms, d_cyc, d_out, e0, e1)) return 1;
   if (run<6>("DFMA", sms, d_cyc, d_out, e0, e1)) return 1;
+  if (run<7>("2xDADD", sms, d_cyc, d_out, e0, e1)) return 1;
   if (run<2>("DDIV", sms, d_cyc, d_out, e0, e1)) return 1;
   if (run<3>("IADD+SHF", sms, d_cyc, d_out, e0, e1)) return 1;
   if (run<4>("IMAD", sms, d_cyc, d_out, e0, e1)) return 1;
