@@ -26,12 +26,12 @@
 //     record with v = 0 when it changes none -- into the lane's current
 //     chunk of kThreadLogChunk slots of the event log.
 //
-// Three per-warp regimes give the same bits:
-//   * full warp (more than 8 trajectories): the products c_j h_j and the
-//     quotient E / a0 run as exact integer arithmetic (ssa_softfloat.cuh),
-//     since the SM's FP64 unit, shared by all its warps, is the bottleneck;
-//   * sparse warp: the hardware products and quotient (fewer instructions,
-//     latency hidden behind the prefix chain);
+// The products c_j h_j run on the FP64 unit, only for the reactions the last
+// event touched; the quotient E / a0 runs as exact integer arithmetic
+// (ssa_softfloat.cuh).  (Integer products for every reaction in full warps
+// were measured slower: with them the integer ALU pipe, not the FP64 unit,
+// bounds a full GPU.)  Two per-warp regimes give the same bits:
+//   * one trajectory per lane;
 //   * cooperative (at most 4 trajectories left and no new work): the warp
 //     splits into groups of 8 lanes, one trajectory per group, and runs it in
 //     batches of 8 events.  The lanes of a group share the propensity
@@ -65,7 +65,6 @@ constexpr long long kStateMax = 2147483647LL;
 constexpr unsigned kFullMask = 0xFFFFFFFFu;
 constexpr int kCoopGroup = 8;      // lanes per trajectory in cooperative mode
 constexpr int kCoopMaxTraj = 4;    // trajectories per warp in cooperative mode
-constexpr int kDenseLanes = 8;     // a warp with more trajectories runs the integer forms
 
 // x[s] for a runtime species index s < MAXS (select chain over registers).
 template <int MAXS>
@@ -404,35 +403,15 @@ __device__ __forceinline__ void draw(const StepEnv& e, Traj<MAXM, MAXS>& q, doub
 }
 
 // One thread-mode iteration.  Returns true when the trajectory has ended.
-template <bool DENSE, bool LOG, int MAXM, int MAXS>
+template <bool LOG, int MAXM, int MAXS>
 __device__ __forceinline__ bool thread_step(const RunArgs& a, const StepEnv& e, Traj<MAXM, MAXS>& q,
                                             const EventLog& lg, ThreadLog& tl) {
-  // propensities the last event touched
-  if (DENSE) {
-    bool all_ok = true;
+  // propensities the last event touched (hardware products: a warp runs the
+  // product of reaction j only when one of its lanes needs it)
 #pragma unroll
-    for (int j = 0; j < MAXM; ++j) {
-      if (j < e.M) {
-        unsigned long long r;
-        const bool ok = propensity_int(a.sm.cbits[j], mass_action_h<MAXS>(a.sm.rinfo[j], q.x), r);
-        const bool d = (q.dirty >> j) & 1u;
-        all_ok &= ok | !d;
-        q.av[j] = (d && ok) ? r : q.av[j];
-      }
-    }
-    if (!all_ok) {  // rare: redo the failed ones on the FP64 unit
-#pragma unroll
-      for (int j = 0; j < MAXM; ++j) {
-        if (j < e.M && ((q.dirty >> j) & 1u))
-          q.av[j] = propensity_fp64(a.sm.cbits[j], mass_action_h<MAXS>(a.sm.rinfo[j], q.x));
-      }
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < MAXM; ++j) {
-      if (j < e.M && ((q.dirty >> j) & 1u))
-        q.av[j] = propensity_fp64(a.sm.cbits[j], mass_action_h<MAXS>(a.sm.rinfo[j], q.x));
-    }
+  for (int j = 0; j < MAXM; ++j) {
+    if (j < e.M && ((q.dirty >> j) & 1u))
+      q.av[j] = propensity_fp64(a.sm.cbits[j], mass_action_h<MAXS>(a.sm.rinfo[j], q.x));
   }
   // one straight-line block of independent chains: the pending event's
   // quotient, the prefix sums of the new state, and the random numbers of
@@ -795,8 +774,7 @@ __global__ void __launch_bounds__(512, 1) k_ssa_thread(const RunArgs a, const Ev
       break;
     }
     if (q.have) {
-      const bool done = (nact > kDenseLanes) ? thread_step<true, LOG>(a, e, q, lg, tl)
-                                             : thread_step<false, LOG>(a, e, q, lg, tl);
+      const bool done = thread_step<LOG>(a, e, q, lg, tl);
       if (done) {
         finish_trajectory(a, q, blk);
         q.have = false;
