@@ -43,7 +43,7 @@ SMS_GB300 = 152
 # DRAM read + write bytes of one k_ssa_thread launch (ncu capture summarised in
 # profiles/k_ssa_thread_hiv_shaped.md: tables, grid and parameters; the
 # difference sums stay in L2), independent of the number of trajectories.
-SIM_KERNEL_DRAM_BYTES = 717824
+SIM_KERNEL_DRAM_BYTES = 689920
 # Bench workloads: the HIV-shaped model (the headline line) and the random
 # 32-species / 128-reaction network (one trajectory per warp).
 WORKLOADS = {
