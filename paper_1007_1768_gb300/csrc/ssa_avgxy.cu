@@ -294,13 +294,32 @@ __global__ void __launch_bounds__(kWinThreads) k_window_sums(
   }
 }
 
-// One thread per window: the times of its union points summed in ascending order.
+// One thread per window: the times of its union points summed in ascending
+// order.  The loads run a chunk of kTimeChunk ahead of the additions (the
+// sum is a serial chain of FP64 additions; without the prefetch every load's
+// latency would sit on it).
+constexpr int kTimeChunk = 16;
 __global__ void k_window_times(const double* T, long long U, long long k, long long P, double* t_out) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   const long long a = p * k, b = min(U, a + k);
   double sum = 0.0;
-  for (long long q = a; q < b; ++q) sum = __dadd_rn(sum, T[q]);
+  double cur[kTimeChunk], nxt[kTimeChunk];
+  long long q = a;
+#pragma unroll
+  for (int i = 0; i < kTimeChunk; ++i) cur[i] = (q + i < b) ? T[q + i] : 0.0;
+  while (q < b) {
+    const long long qn = q + kTimeChunk;
+#pragma unroll
+    for (int i = 0; i < kTimeChunk; ++i) nxt[i] = (qn + i < b) ? T[qn + i] : 0.0;
+#pragma unroll
+    for (int i = 0; i < kTimeChunk; ++i) {
+      if (q + i < b) sum = __dadd_rn(sum, cur[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < kTimeChunk; ++i) cur[i] = nxt[i];
+    q = qn;
+  }
   t_out[p] = __ddiv_rn(sum, (double)(b - a));
 }
 
@@ -644,7 +663,12 @@ extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj
   double* dt = reinterpret_cast<double*>(ws2 + o_t);
   double* dmean = reinterpret_cast<double*>(ws2 + o_mean);
   double* dmsq = reinterpret_cast<double*>(ws2 + o_msq);
-  k_window_times<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(T, U, k, P, dt);
+  {
+    // few long windows: one warp per block spreads them over the SMs (each
+    // SM's FP64 unit serves the additions of its warps in turn)
+    const int tpb = (P <= 32LL * prop.multiProcessorCount) ? 32 : 128;
+    k_window_times<<<(unsigned)((P + tpb - 1) / tpb), tpb, 0, st>>>(T, U, k, P, dt);
+  }
   SSA_A_TRY(cudaGetLastError());
   k_window_final<<<(unsigned)((PS + 255) / 256), 256, 0, st>>>(W1, A1, W2, A2, x0d, n_traj, U, k, S, P, dmean, dmsq);
   SSA_A_TRY(cudaGetLastError());
