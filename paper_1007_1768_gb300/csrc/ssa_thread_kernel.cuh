@@ -1,6 +1,9 @@
 // The simulation kernel for small networks (at most 16 reactions and 16
-// species).  Included by ssa_thread_s{4,8,16}.cu, each of which instantiates
-// it for one species bucket so the builds run in parallel.
+// species).  Included by ssa_thread_s{4,8,16}.cu and, for the logging
+// variants, ssa_thread_log_s{4,8,16}.cu, each of which instantiates it for one
+// species bucket so the builds run in parallel; the warp kernel, the batch
+// kernel and the gradient replay include it for its helpers (propensity
+// products, random numbers, quotient, grid index).
 //
 // Gillespie's direct method (Sec. 2), one trajectory per lane; lanes take
 // trajectory ids from a global work counter.
