@@ -179,17 +179,42 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_hist(const u64* keys, lon
   tile_hist[(long long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// Stable scatter of one tile: items are taken in index order (round r holds
-// indices r * 256 + tid of the tile); within a round, lanes of a warp with
-// the same digit are ranked by __match_any_sync, warps in order by a
-// per-round count table, rounds by running digit counts.
+// Stable scatter of one tile.  Items are ranked in index order (round r
+// holds indices r * 256 + tid of the tile; within a round, lanes of a warp
+// with the same digit are ranked by __match_any_sync, warps in order by a
+// per-round count table, rounds by running digit counts) into the tile's own
+// digit order in shared memory; the tile then leaves in that order, so each
+// digit's items go out as one contiguous run.
 __global__ void __launch_bounds__(kSortThreads) k_tile_scatter(const u64* kin, const unsigned int* vin, u64* kout,
                                                                unsigned int* vout, long long n, int shift,
                                                                const unsigned int* offs, long long ntiles) {
-  __shared__ unsigned int base[256];
+  __shared__ unsigned int base[256];   // next local slot of each digit
+  __shared__ unsigned int lbase[256];  // first local slot of each digit
+  __shared__ unsigned int gbase[256];  // first global slot of each digit (this tile)
   __shared__ unsigned int wcnt[kSortThreads / 32][256];
+  __shared__ u64 skey[kSortTile];
+  __shared__ unsigned int sval[kSortTile];
+  __shared__ unsigned int wsum[kSortThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  base[tid] = offs[(long long)tid * ntiles + blockIdx.x];
+  // local digit offsets: exclusive scan of this tile's digit counts (a count
+  // is the step of the digit-major exclusive scan to the next entry)
+  {
+    const long long idx = (long long)tid * ntiles + blockIdx.x;
+    const unsigned c = (idx + 1 < 256 * ntiles) ? offs[idx + 1] - offs[idx] : (unsigned)n - offs[idx];
+    unsigned x = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+      if (lane >= off) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    unsigned pre = 0;
+    for (int ww = 0; ww < w; ++ww) pre += wsum[ww];
+    lbase[tid] = pre + x - c;
+    base[tid] = pre + x - c;
+    gbase[tid] = offs[(long long)tid * ntiles + blockIdx.x];
+  }
   const long long t0 = (long long)blockIdx.x * kSortTile;
   const unsigned lt = (1u << lane) - 1u;
   for (int r = 0; r < kSortItems; ++r) {
@@ -206,15 +231,24 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_scatter(const u64* kin, c
     if (valid) {
       unsigned before = 0;
       for (int ww = 0; ww < w; ++ww) before += wcnt[ww][dig];
-      const unsigned pos = base[dig] + before + rank;
-      kout[pos] = key;
-      vout[pos] = vin[i];
+      const unsigned lpos = base[dig] + before + rank;
+      skey[lpos] = key;
+      sval[lpos] = vin[i];
     }
     __syncthreads();
     unsigned add = 0;
     for (int ww = 0; ww < kSortThreads / 32; ++ww) add += wcnt[ww][tid];
     base[tid] += add;
     __syncthreads();  // every thread has read this round's counts before they are cleared
+  }
+  // out in local order: slot j of digit d goes to gbase[d] + (j - lbase[d])
+  const long long cnt = min((long long)kSortTile, n - t0);
+  for (int j = tid; j < cnt; j += kSortThreads) {
+    const u64 key = skey[j];
+    const unsigned d = (unsigned)((key >> shift) & 255);
+    const unsigned pos = gbase[d] + ((unsigned)j - lbase[d]);
+    kout[pos] = key;
+    vout[pos] = sval[j];
   }
 }
 
