@@ -328,33 +328,63 @@ __global__ void __launch_bounds__(kWinThreads) k_window_sums(
   }
 }
 
-// One thread per window: the times of its union points summed in ascending
-// order.  The loads run a chunk of kTimeChunk ahead of the additions (the
-// sum is a serial chain of FP64 additions; without the prefetch every load's
-// latency would sit on it).
-constexpr int kTimeChunk = 16;
-__global__ void k_window_times(const double* T, long long U, long long k, long long P, double* t_out) {
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  const long long a = p * k, b = min(U, a + k);
-  double sum = 0.0;
-  double cur[kTimeChunk], nxt[kTimeChunk];
-  long long q = a;
-#pragma unroll
-  for (int i = 0; i < kTimeChunk; ++i) cur[i] = (q + i < b) ? T[q + i] : 0.0;
-  while (q < b) {
-    const long long qn = q + kTimeChunk;
-#pragma unroll
-    for (int i = 0; i < kTimeChunk; ++i) nxt[i] = (qn + i < b) ? T[qn + i] : 0.0;
-#pragma unroll
-    for (int i = 0; i < kTimeChunk; ++i) {
-      if (q + i < b) sum = __dadd_rn(sum, cur[i]);
+// The times of each window's union points summed in ascending order (a
+// serial chain of FP64 additions per window).  A block of 64 threads serves
+// 32 consecutive windows: warp 0 (lane l for window 32 blockIdx.x + l) runs
+// the chains from shared memory while warp 1 loads the next kTimeChunk times
+// of every window into the other buffer, so no load latency sits on a chain.
+constexpr int kTimeChunk = 64;
+constexpr int kTimeStride = kTimeChunk + 1;  // odd stride: lanes hit distinct banks
+__global__ void __launch_bounds__(64) k_window_times(const double* T, long long U, long long k, long long P,
+                                                     double* t_out) {
+  __shared__ double buf[2][32 * kTimeStride];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long p0 = (long long)blockIdx.x * 32;
+  const long long p = p0 + lane;
+  const long long a = p * k;
+  const long long b = (p < P) ? min(U, a + k) : a;
+  // the longest window of the block sets the number of chunks
+  const long long span = min(U, (p0 + 32) * k) - p0 * k;
+  const long long nchunk = (min(span, k) + kTimeChunk - 1) / kTimeChunk;
+  // the producer fills buffer c & 1 with chunk c of all 32 windows by
+  // asynchronous 8-byte copies (zero fill past a window's end), then waits
+  // for them before the block's barrier
+  auto load = [&](long long c) {
+    double* dst = buf[c & 1];
+    for (int wi = 0; wi < 32; ++wi) {
+      const long long wa = (p0 + wi) * k, wb = (p0 + wi < P) ? min(U, wa + k) : wa;
+      for (int i = lane; i < kTimeChunk; i += 32) {
+        const long long q = wa + c * kTimeChunk + i;
+        const unsigned sdst = (unsigned)__cvta_generic_to_shared(dst + wi * kTimeStride + i);
+        const double* src = (q < wb) ? T + q : T;
+        const int nbytes = (q < wb) ? 8 : 0;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sdst), "l"(src), "r"(nbytes) : "memory");
+      }
     }
-#pragma unroll
-    for (int i = 0; i < kTimeChunk; ++i) cur[i] = nxt[i];
-    q = qn;
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  if (warp == 1 && nchunk > 0) {
+    load(0);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   }
-  t_out[p] = __ddiv_rn(sum, (double)(b - a));
+  __syncthreads();
+  double sum = 0.0;
+  for (long long c = 0; c < nchunk; ++c) {
+    if (warp == 1) {
+      if (c + 1 < nchunk) {
+        load(c + 1);
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      }
+    } else {
+      const double* src = buf[c & 1] + lane * kTimeStride;
+      const long long q0 = a + c * kTimeChunk;
+      for (int i = 0; i < kTimeChunk; ++i) {
+        if (q0 + i < b) sum = __dadd_rn(sum, src[i]);
+      }
+    }
+    __syncthreads();
+  }
+  if (warp == 0 && p < P) t_out[p] = __ddiv_rn(sum, (double)(b - a));
 }
 
 // mean and msq per (window, species); CW* hold the exclusive scans of W* along p.
@@ -697,12 +727,7 @@ extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj
   double* dt = reinterpret_cast<double*>(ws2 + o_t);
   double* dmean = reinterpret_cast<double*>(ws2 + o_mean);
   double* dmsq = reinterpret_cast<double*>(ws2 + o_msq);
-  {
-    // few long windows: one warp per block spreads them over the SMs (each
-    // SM's FP64 unit serves the additions of its warps in turn)
-    const int tpb = (P <= 32LL * prop.multiProcessorCount) ? 32 : 128;
-    k_window_times<<<(unsigned)((P + tpb - 1) / tpb), tpb, 0, st>>>(T, U, k, P, dt);
-  }
+  k_window_times<<<(unsigned)((P + 31) / 32), 64, 0, st>>>(T, U, k, P, dt);
   SSA_A_TRY(cudaGetLastError());
   k_window_final<<<(unsigned)((PS + 255) / 256), 256, 0, st>>>(W1, A1, W2, A2, x0d, n_traj, U, k, S, P, dmean, dmsq);
   SSA_A_TRY(cudaGetLastError());
