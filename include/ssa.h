@@ -270,7 +270,7 @@ ssa_status ssa_ensemble_grad(const ssa_model* model, int64_t n_traj, double t_en
  * mean and msq) in opts->memory's space; *n_points receives the number of
  * windows P (only min(P, max_points) are written; max_points = 0 only
  * counts) and *n_union (may be NULL) the number of union points U.
- * The event log takes about 48 bytes of device memory per (event, species
+ * The event log takes about 57 bytes of device memory per (event, species
  * changed); opts->log_records sizes it (0: an earlier call's count, else a
  * pilot of up to 4,096 trajectories, estimates it).  Should the log run out,
  * the logging run is repeated once with the exact record count it reports.

@@ -281,8 +281,8 @@ constexpr int kWinRecords = 4096;
 constexpr int kWinSlots = 512;
 
 __global__ void __launch_bounds__(kWinThreads) k_window_sums(
-    const unsigned int* head, const unsigned int* uidx, const unsigned int* perm, const int32_t* species,
-    const int32_t* change, const long long* d2, long long nv, long long U, long long k, int S, long long P,
+    const unsigned int* head, const unsigned int* uidx, const unsigned int* perm, const LogRec* rec,
+    long long nv, long long U, long long k, int S, long long P,
     long long* W1, long long* A1, long long* W2, long long* A2) {
   __shared__ long long sW1[kWinSlots], sA1[kWinSlots], sW2[kWinSlots], sA2[kWinSlots];
   const long long r0 = (long long)blockIdx.x * kWinRecords;
@@ -297,8 +297,9 @@ __global__ void __launch_bounds__(kWinThreads) k_window_sums(
     const long long p = u / k;
     const long long b = min(U, (p + 1) * k);
     const unsigned int q = perm[r];
-    const int s = species[q];
-    const long long v = change[q], dd = d2[q], wt = b - u;
+    const LogRec rq = rec[q];
+    const int s = rq.species;
+    const long long v = rq.change, dd = rq.d2, wt = b - u;
     if (local) {
       const int slot = (int)((p - p_lo) * S + s);
       atomicAdd(reinterpret_cast<unsigned long long*>(&sW1[slot]), (unsigned long long)v);
@@ -547,7 +548,7 @@ extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj
     const cudaError_t e_ = (expr);                                \
     if (e_ != cudaSuccess) return fail(SSA_ECUDA, cudaGetErrorString(e_)); \
   } while (0)
-  size_t o_key = 0, o_key2 = 0, o_sp = 0, o_ch = 0, o_d2 = 0, o_perm = 0, o_perm2 = 0, o_head = 0, o_uidx = 0, o_T = 0,
+  size_t o_key = 0, o_key2 = 0, o_rec = 0, o_perm = 0, o_perm2 = 0, o_head = 0, o_uidx = 0, o_T = 0,
          o_th = 0, o_sc32 = 0, o_hist = 0, o_cnt = 0, o_grid = 0, o_d = 0, o_stats = 0, o_counter = 0;
   long long ntiles = 0;
   EventLog lg;
@@ -563,8 +564,8 @@ extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj
       off = align_up(off + bytes, 256);
       return at;
     };
-    o_key = take(8 * cap); o_key2 = take(8 * cap); o_sp = take(4 * cap); o_ch = take(4 * cap);
-    o_d2 = take(8 * cap); o_perm = take(4 * cap); o_perm2 = take(4 * cap); o_head = take(4 * cap);
+    o_key = take(8 * cap); o_key2 = take(8 * cap); o_rec = take(sizeof(LogRec) * cap);
+    o_perm = take(4 * cap); o_perm2 = take(4 * cap); o_head = take(4 * cap);
     o_uidx = take(4 * cap); o_T = take(8 * (cap + 1));
     o_th = take(4 * (size_t)(256 * ntiles)); o_sc32 = take(4 * scan_scratch_elems<unsigned>(256 * ntiles + cap));
     o_hist = take(8 * 8 * 256); o_cnt = take(8 * 5); o_grid = take(8); o_d = take(16 * (size_t)S);
@@ -598,9 +599,7 @@ extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj
     a.grid_uniform = 0;
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ws + o_cnt);  // counter, padded, overflow, -, needed
     lg.key = reinterpret_cast<u64*>(ws + o_key);
-    lg.species = reinterpret_cast<int32_t*>(ws + o_sp);
-    lg.change = reinterpret_cast<int32_t*>(ws + o_ch);
-    lg.d2 = reinterpret_cast<long long*>(ws + o_d2);
+    lg.rec = reinterpret_cast<LogRec*>(ws + o_rec);
     lg.counter = cnt;
     lg.padded = cnt + 1;
     lg.overflow = cnt + 2;
@@ -714,7 +713,7 @@ extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj
   SSA_A_TRY(cudaMemsetAsync(ws2, 0, o_sc64, st));
   if (nv > 0) {
     k_window_sums<<<(unsigned)((nv + kWinRecords - 1) / kWinRecords), kWinThreads, 0, st>>>(
-        head, uidx, perm, lg.species, lg.change, lg.d2, nv, U, k, S, P, W1, A1, W2, A2);
+        head, uidx, perm, lg.rec, nv, U, k, S, P, W1, A1, W2, A2);
     SSA_A_TRY(cudaGetLastError());
   }
   long long* sc64 = reinterpret_cast<long long*>(ws2 + o_sc64);

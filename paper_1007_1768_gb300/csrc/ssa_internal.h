@@ -174,11 +174,15 @@ cudaError_t thread_kernel_set_smem(int M, int S, bool shared_d, size_t smem_byte
 constexpr int kLogChunk = 256;       // slots a warp of the warp kernel takes at a time
 constexpr int kThreadLogChunk = 32;  // slots a lane of the thread kernel takes at a time
 constexpr unsigned long long kLogSentinel = 0xFFFFFFFFFFFFFFFFULL;  // key of an unused slot
+// What a record carries besides its time key (16 bytes: one load).
+struct __align__(16) LogRec {
+  int32_t species;
+  int32_t change;  // v
+  long long d2;    // (2 x_old + v) v
+};
 struct EventLog {
   unsigned long long* key;       // [capacity] bits of the event time
-  int32_t* species;              // [capacity]
-  int32_t* change;               // [capacity] v
-  long long* d2;                 // [capacity] (2 x_old + v) v
+  LogRec* rec;                   // [capacity]
   unsigned long long* counter;   // slots handed out (in chunks)
   unsigned long long* padded;    // unused slots (sentinel keys)
   unsigned long long* overflow;  // nonzero when the capacity ran out

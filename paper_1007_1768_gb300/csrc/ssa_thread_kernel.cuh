@@ -191,18 +191,14 @@ __device__ __forceinline__ void thread_log_event(const EventLog& lg, ThreadLog& 
   unsigned long long slot = tl.base + (unsigned long long)tl.fill;
   if (none) {
     lg.key[slot] = (unsigned long long)tb;
-    lg.species[slot] = 0;
-    lg.change[slot] = 0;
-    lg.d2[slot] = 0;
+    lg.rec[slot] = LogRec{0, 0, 0};
   }
 #pragma unroll
   for (int s = 0; s < MAXS; ++s) {
     if (pv[s] != 0) {
       const long long xo = (long long)x[s] - pv[s];
       lg.key[slot] = (unsigned long long)tb;
-      lg.species[slot] = s;
-      lg.change[slot] = pv[s];
-      lg.d2[slot] = (2 * xo + pv[s]) * (long long)pv[s];
+      lg.rec[slot] = LogRec{s, pv[s], (2 * xo + pv[s]) * (long long)pv[s]};
       ++slot;
     }
   }

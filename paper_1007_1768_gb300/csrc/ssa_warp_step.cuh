@@ -379,9 +379,7 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
       if (logged && q1 == q0 && lane == 0) {
         const unsigned long long slot = lst->base + (unsigned long long)lst->fill;
         lg->key[slot] = (unsigned long long)tb;
-        lg->species[slot] = 0;
-        lg->change[slot] = 0;
-        lg->d2[slot] = 0;
+        lg->rec[slot] = LogRec{0, 0, 0};
       }
     }
     for (int e = q0 + lane; e < q1; e += 32) {
@@ -400,9 +398,7 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
         if (logged) {
           const unsigned long long slot = lst->base + (unsigned long long)(lst->fill + (e - q0));
           lg->key[slot] = (unsigned long long)tb;
-          lg->species[slot] = s;
-          lg->change[slot] = vv;
-          lg->d2[slot] = d2;
+          lg->rec[slot] = LogRec{s, vv, d2};
         }
       }
     }
