@@ -194,3 +194,33 @@ def test_shards_finalised_on_the_host_match_one_run():
     mean, var = finalize_sums(s1, s2, n)
     assert np.array_equal(mean.view(np.int64), full["mean"].view(np.int64))
     assert np.array_equal(var.view(np.int64), full["var"].view(np.int64))
+
+
+def test_cooperative_batches_ending_inside_a_batch():
+    """A warp holding at most 4 trajectories runs them cooperatively, 8 events
+    per batch, from the first event (1, 3 or 4 trajectories here): truncation
+    at max_events, an absorbing state and the int32 overflow land at various
+    places inside a batch, and the later events of that batch are undone."""
+    net = W.hiv_shaped()
+    for n in (1, 3, 4):
+        for me in (1, 8, 13, 21, 100):
+            g = _gpu(net, n, 30.0, 301, 5, max_events=me)
+            r, mean, var = _oracle(net, n, 30.0, 301, 5, max_events=me)
+            _assert_same(g, r, mean, var)
+    death = W.Network("death", ["X"], np.array([[1]], np.int32), np.array([[0]], np.int32), np.array([2.0]),
+                      np.array([11], np.int32))
+    g = _gpu(death, 3, 50.0, 51, 3)
+    r, mean, var = _oracle(death, 3, 50.0, 51, 3)
+    _assert_same(g, r, mean, var)
+    assert np.all(g["traj_events"] == 11)
+    # births from 2^31 - 1 - 20: the 21st would leave int32 (device buffers,
+    # no stats: the call does not wait, so no status for the overflow; two
+    # trajectories keep the sums of x^2 inside int64)
+    grow = W.Network("grow", ["X"], np.array([[0]], np.int32), np.array([[1]], np.int32), np.array([5.0]),
+                     np.array([2147483647 - 20], np.int32))
+    g = _gpu(grow, 2, 100.0, 11, 4, stats=False)
+    r, mean, var = _oracle(grow, 2, 100.0, 11, 4)
+    for key, want in (("sum1", r.S1), ("sum2", r.S2), ("traj_events", r.traj_events), ("traj_hash", r.traj_hash),
+                      ("traj_flags", r.traj_flags)):
+        assert np.array_equal(g[key], want), key
+    assert np.all(r.traj_events == 20) and np.all(r.traj_flags == ssa.binding.TRAJ_OVERFLOW)
