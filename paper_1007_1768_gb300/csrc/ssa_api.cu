@@ -554,7 +554,8 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
   a.traj_hash = host ? (o.traj_hash ? reinterpret_cast<uint64_t*>(ws + wl.thash) : nullptr) : o.traj_hash;
   a.traj_flags = host ? (o.traj_flags ? reinterpret_cast<int32_t*>(ws + wl.tflags) : nullptr) : o.traj_flags;
   a.device_totals = reinterpret_cast<unsigned long long*>(o.device_totals);
-  a.grid_uniform = (!grid && G >= 2 && G <= (1 << 20) && t_end < 1e30) ? 1 : 0;
+  const bool uniform = !grid || (host && host_grid_is_uniform(grid, G, t_end));
+  a.grid_uniform = (uniform && G >= 2 && G <= (1 << 20) && t_end < 1e30) ? 1 : 0;
   a.grid_scale = (float)((double)(G - 1) / t_end);
   a.grid_margin = (float)((double)G * 0x1p-21);
 

@@ -503,7 +503,8 @@ ssa_status ssa_batch_create(int32_t n_models, const ssa_model* const* models, co
     w.S = b->S[i];
     w.M = b->M[i];
     w.G = b->G[i];
-    w.grid_uniform = (!gr && b->G[i] >= 2 && b->G[i] <= (1 << 20) && te < 1e30) ? 1 : 0;
+    const bool uniform = !gr || host_grid_is_uniform(gr, b->G[i], te);
+    w.grid_uniform = (uniform && b->G[i] >= 2 && b->G[i] <= (1 << 20) && te < 1e30) ? 1 : 0;
     w.grid_scale = (float)((double)(b->G[i] - 1) / te);
     w.grid_margin = (float)((double)b->G[i] * 0x1p-21);
     w.sid = (uint32_t)(o.stream_id + (uint64_t)i);

@@ -449,7 +449,8 @@ extern "C" ssa_status ssa_ensemble_grad(const ssa_model* model, int64_t n_traj, 
   a.Pgc = Pgc;
   a.gtraj = reinterpret_cast<double*>(ws + o_gtraj);
   a.counter = reinterpret_cast<unsigned long long*>(ws + o_counter);
-  a.grid_uniform = (!grid && G >= 2 && G <= (1 << 20) && t_end < 1e30) ? 1 : 0;
+  const bool uniform = !grid || (host && host_grid_is_uniform(grid, G, t_end));
+  a.grid_uniform = (uniform && G >= 2 && G <= (1 << 20) && t_end < 1e30) ? 1 : 0;
   a.grid_scale = (float)((double)(G - 1) / t_end);
   a.grid_margin = (float)((double)G * 0x1p-21);
   const long long want = (n_traj + 127) / 128;

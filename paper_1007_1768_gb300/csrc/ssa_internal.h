@@ -115,6 +115,18 @@ __host__ __device__ inline ThreadSmem thread_smem_layout(int maxm, int maxs, int
   return L;
 }
 
+// True when a host grid is the uniform grid bit for bit,
+// g_k = RN(RN(k t_end) / (G - 1)) (what k_uniform_grid writes), so the
+// kernels may locate grid cells by the estimate of the uniform case.
+inline bool host_grid_is_uniform(const double* g, int G, double t_end) {
+  if (G < 2) return false;
+  for (int k = 0; k < G; ++k) {
+    const double v = ((double)k * t_end) / (double)(G - 1);
+    if (!(g[k] == v)) return false;
+  }
+  return true;
+}
+
 // Template buckets of the thread kernel: M rounded up to an even number, S to 4, 8 or 16.
 __host__ __device__ inline int bucket_m(int M) { return (M + 1) / 2 * 2; }
 __host__ __device__ inline int bucket_s(int S) { return S <= 4 ? 4 : (S <= 8 ? 8 : 16); }

@@ -224,3 +224,23 @@ def test_cooperative_batches_ending_inside_a_batch():
                       ("traj_flags", r.traj_flags)):
         assert np.array_equal(g[key], want), key
     assert np.all(r.traj_events == 20) and np.all(r.traj_flags == ssa.binding.TRAJ_OVERFLOW)
+
+
+def test_explicit_uniform_grid_takes_the_same_path():
+    """A host grid equal to the uniform grid bit for bit locates grid cells by
+    the uniform estimate; the results are those of the implicit grid and of
+    the oracle with the explicit grid (and a grid off by one ulp at one point
+    still matches the oracle through the general path)."""
+    net = W.hiv_shaped()
+    grid = (np.arange(301, dtype=np.float64) * 30.0) / 300.0
+    a = _gpu(net, 600, 30.0, 301, 3)
+    b = _gpu(net, 600, 30.0, 0, 3, grid=grid, device=False)
+    for key in ("sum1", "sum2", "traj_hash", "traj_events"):
+        assert np.array_equal(a[key], b[key]), key
+    r, mean, var = _oracle(net, 600, 30.0, 0, 3, grid=grid)
+    _assert_same(b, r, mean, var)
+    g2 = grid.copy()
+    g2[150] = np.nextafter(g2[150], 0.0)
+    c = _gpu(net, 600, 30.0, 0, 3, grid=g2, device=False)
+    r2, mean2, var2 = _oracle(net, 600, 30.0, 0, 3, grid=g2)
+    _assert_same(c, r2, mean2, var2)
