@@ -107,3 +107,14 @@ def test_log_capacity_pilot_hint_and_retry():
     with pytest.raises(ssa.SSAError) as e:
         _gpu(net, 16, T, 4, 1, log_records=-1)
     assert e.value.status == ssa.binding.SSA_EINVAL
+
+
+@pytest.mark.parametrize("sched", ["thread", "warp"])
+def test_wide_small_network_both_schedules(sched):
+    """12 species and 15 reactions: the thread kernel's widest template
+    bucket (16 x 16) for the thread schedule, and the warp schedule."""
+    net = W.random_network(21, n_species=12, n_reactions=15, x0_hi=30)
+    for k in (1, 5, 200):
+        t, m, q, U = _gpu(net, 200, 3.0, 3, k, schedule=sched, max_events=200000)
+        ot, om, oq, oU = oracle.avg_xy(net, 200, 3.0, 3, k, schedule=SCHED[sched], max_events=200000)
+        assert U == oU and np.array_equal(t, ot) and np.array_equal(m, om) and np.array_equal(q, oq), (sched, k)

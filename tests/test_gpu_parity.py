@@ -244,3 +244,14 @@ def test_explicit_uniform_grid_takes_the_same_path():
     c = _gpu(net, 600, 30.0, 0, 3, grid=g2, device=False)
     r2, mean2, var2 = _oracle(net, 600, 30.0, 0, 3, grid=g2)
     _assert_same(c, r2, mean2, var2)
+
+
+@pytest.mark.parametrize("n", [3, 200, 1000])
+def test_wide_small_network_thread_kernel(n):
+    """The thread kernel's widest template bucket (12 species, 15 reactions
+    run as 16 x 16), with cooperative mode from the first event (3
+    trajectories) and at the end of a fuller launch."""
+    net = W.random_network(21, n_species=12, n_reactions=15, x0_hi=30)
+    g = _gpu(net, n, 3.0, 31, 9, schedule="thread", max_events=200000)
+    r, mean, var = _oracle(net, n, 3.0, 31, 9, max_events=200000)
+    _assert_same(g, r, mean, var)
