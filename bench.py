@@ -490,14 +490,16 @@ def run_grad(args):
     ke = torch.cuda.Event(enable_timing=True)
 
     def step(seed, timed=False):
-        r = ssa.ensemble_run(model, n, w.t_end, G, seed, device=dev, want_sums=False, traj_offset=rank * n)
+        r = ssa.ensemble_run(model, n, w.t_end, G, seed, device=dev, want_sums=False, traj_offset=rank * n,
+                             per_traj=True)
         wgt = torch.zeros((G, S), dtype=torch.float64, device=dev)
         wgt[:, 2] = 2.0 * (r.mean[:, 2] - target)
         opt = {}
         if timed:
             opt = {"sim_event_begin": kb.cuda_event, "sim_event_end": ke.cuda_event}
+        # the forward's event counts let the replay start the longest trajectories first
         g, se, _ = ssa.ensemble_grad(model, n, w.t_end, G, seed, wgt, r.mean, device=dev, traj_offset=rank * n,
-                                     **opt)
+                                     traj_events=r.traj_events, **opt)
         return r.events, g, se
 
     if args.profile_small:

@@ -19,10 +19,12 @@ class SSAEnsembleFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, rates, reactants, products, x0, n_traj, t_end, n_grid, seed, device, opt_kw):
         model = _b.Model(reactants, products, rates.detach().to("cpu", torch.float64).numpy(), x0)
-        r = _b.ensemble_run(model, n_traj, t_end, n_grid, seed, device=device, want_sums=False, **opt_kw)
+        r = _b.ensemble_run(model, n_traj, t_end, n_grid, seed, device=device, want_sums=False, per_traj=True,
+                            **opt_kw)
         ctx.model = model
         ctx.call = (n_traj, t_end, n_grid, seed, device, opt_kw)
         ctx.rates_meta = (rates.device, rates.dtype)
+        ctx.traj_events = r.traj_events  # the backward replays the longest trajectories first
         ctx.save_for_backward(r.mean)
         ctx.last_se = None
         return r.mean, r.var
@@ -36,7 +38,7 @@ class SSAEnsembleFunction(torch.autograd.Function):
         if grad_mean is None:
             grad_mean = torch.zeros_like(mean)
         g, se, _ = _b.ensemble_grad(ctx.model, n_traj, t_end, n_grid, seed, grad_mean.contiguous(), mean,
-                                    device=device, **opt_kw)
+                                    device=device, traj_events=ctx.traj_events, **opt_kw)
         ctx.model.close()
         dev, dt = ctx.rates_meta
         SSAEnsembleFunction.last_standard_error = se.to(dev, dt)

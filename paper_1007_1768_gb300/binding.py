@@ -273,10 +273,12 @@ def ensemble_run(model: Model, n_traj: int, t_end: float, n_grid: int, seed: int
 
 
 def ensemble_grad(model: Model, n_traj: int, t_end: float, n_grid: int, seed: int, dL_dmean, mean, grid=None, *,
-                  device=None, per_traj: bool = False, **opt_kw):
+                  device=None, per_traj: bool = False, traj_events=None, **opt_kw):
     """ssa_ensemble_grad: (dL/drates [M], standard errors [M], per-trajectory
     contributions [M, N] or None).  ``device=None``: numpy in and out;
-    a torch device: torch tensors on that device (torch's current stream)."""
+    a torch device: torch tensors on that device (torch's current stream).
+    ``traj_events``: the forward's per-trajectory event counts (int64 [N],
+    same memory space), to replay the longest trajectories first."""
     L = lib()
     M = model.n_reactions
     G = int(n_grid if grid is None else len(grid))
@@ -289,6 +291,10 @@ def ensemble_grad(model: Model, n_traj: int, t_end: float, n_grid: int, seed: in
         traj = np.empty((M, int(n_traj))) if per_traj else None
         opts = make_opts(memory=MEM_HOST, workspace=None if traj is None else traj.ctypes.data,
                          workspace_bytes=0 if traj is None else traj.nbytes, **opt_kw)
+        if traj_events is not None:
+            tev = np.ascontiguousarray(traj_events, dtype=np.int64)
+            assert tev.shape == (int(n_traj),)
+            opts.traj_events = tev.ctypes.data
         _check(L.ssa_ensemble_grad(model.handle, int(n_traj), float(t_end), G,
                                    None if g is None else g.ctypes.data, int(seed), ctypes.byref(opts),
                                    w.ctypes.data, mu.ctypes.data, out.ctypes.data, se.ctypes.data))
@@ -305,6 +311,10 @@ def ensemble_grad(model: Model, n_traj: int, t_end: float, n_grid: int, seed: in
     opts = make_opts(memory=MEM_DEVICE, cuda_stream=stream.cuda_stream,
                      workspace=None if traj is None else traj.data_ptr(),
                      workspace_bytes=0 if traj is None else traj.numel() * 8, **opt_kw)
+    if traj_events is not None:
+        tev = torch.as_tensor(traj_events, device=dev).to(torch.int64).contiguous()
+        assert tev.shape == (int(n_traj),)
+        opts.traj_events = tev.data_ptr()
     _check(L.ssa_ensemble_grad(model.handle, int(n_traj), float(t_end), G, None if g is None else g.data_ptr(),
                                int(seed), ctypes.byref(opts), w.data_ptr(), mu.data_ptr(), out.data_ptr(),
                                se.data_ptr()))

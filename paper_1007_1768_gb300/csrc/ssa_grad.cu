@@ -27,6 +27,7 @@
 //
 // The trajectory itself is the thread kernel's: FP64 propensities, schedule
 // L prefix sums, the same random numbers, selection and stopping rules.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -54,6 +55,7 @@ struct GradArgs {
   const double* Pc;         // [G + 1] ... of c_k = sum_s w[k][s] m[k][s]
   const double* Pgc;        // [G + 1] ... of g_k c_k
   double* gtraj;            // [M x N] per-trajectory contributions (column r at r * N)
+  const unsigned int* order;  // [N] trajectory taken at each work index, or null (index order)
   unsigned long long* counter;
   int32_t grid_uniform;
   float grid_scale, grid_margin;
@@ -120,8 +122,9 @@ __global__ void __launch_bounds__(kGradThreads) k_ssa_grad(const GradArgs a) {
   const int S = a.S, M = a.M, G = a.G;
   const uint32_t key0 = (uint32_t)a.seed, key1 = (uint32_t)(a.seed >> 32), sid = (uint32_t)a.stream_id;
   for (;;) {
-    const unsigned long long li = atomicAdd(a.counter, 1ULL);
-    if (li >= (unsigned long long)a.N) break;
+    const unsigned long long wi = atomicAdd(a.counter, 1ULL);
+    if (wi >= (unsigned long long)a.N) break;
+    const unsigned long long li = a.order ? (unsigned long long)a.order[wi] : wi;  // trajectory index
     const unsigned long long traj_id = a.traj_offset + li;
     int x[MAXS];
 #pragma unroll
@@ -306,6 +309,47 @@ __global__ void __launch_bounds__(1024) k_grad_reduce(const double* gtraj, long 
   }
 }
 
+// Work order, longest trajectories first, from the forward's event counts:
+// buckets of 1/12 of a doubling of the count, in descending order; within a
+// bucket, any order.  Only the schedule depends on it: each trajectory's
+// contribution lands at its own index and the reduction runs in index order.
+__device__ __forceinline__ int order_bucket(long long ev) {
+  const float l = log2f((float)(ev < 0 ? 0 : ev) + 1.0f) * 12.0f;
+  return 255 - min(255, (int)l);
+}
+
+__global__ void k_order_hist(const long long* ev, long long n, unsigned int* hist) {
+  __shared__ unsigned int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    atomicAdd(&h[order_bucket(ev[i])], 1u);
+  __syncthreads();
+  if (h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+// In place: exclusive scan of the 256 bucket counts (one block of 256).
+__global__ void k_order_scan(unsigned int* hist) {
+  __shared__ unsigned int v[256];
+  v[threadIdx.x] = hist[threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int run = 0;
+    for (int i = 0; i < 256; ++i) {
+      const unsigned int c = v[i];
+      v[i] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  hist[threadIdx.x] = v[threadIdx.x];
+}
+
+__global__ void k_order_scatter(const long long* ev, long long n, unsigned int* next, unsigned int* order) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) order[atomicAdd(&next[order_bucket(ev[i])], 1u)] = (unsigned int)i;
+}
+
 template <int MAXM, int MAXS>
 cudaError_t launch_grad_t(const GradArgs& a, int blocks, cudaStream_t st) {
   const size_t smem = (size_t)kLogCells * 16 + (size_t)4 * MAXM * kGradThreads * 8 + (size_t)MAXM * MAXS * 4 +
@@ -394,8 +438,14 @@ extern "C" ssa_status ssa_ensemble_grad(const ssa_model* model, int64_t n_traj, 
                o_Pw = take(8 * (gs + S)), o_Pgw = take(8 * (gs + S)), o_Pc = take(8 * ((size_t)G + 1)),
                o_Pgc = take(8 * ((size_t)G + 1)), o_out = take(16 * (size_t)M),
                o_gtraj = take(8 * (size_t)M * (size_t)n_traj);
+  // optional work order from the forward's event counts (opts->traj_events)
+  const bool ordered = o.traj_events != nullptr;
+  if (ordered && n_traj > (int64_t)0xFFFFFFFFLL)
+    return (ssa_status)set_error(SSA_EINVAL, "a work order takes at most 2^32 - 1 trajectories");
+  const size_t o_order = ordered ? take(4 * (size_t)n_traj) : 0, o_hist = ordered ? take(4 * 256) : 0,
+               o_ev = (ordered && host) ? take(8 * (size_t)n_traj) : 0;
   unsigned char* ws = nullptr;
-  if ((e = cudaMallocAsync(reinterpret_cast<void**>(&ws), off, st)) != cudaSuccess)
+  if ((e = pool_malloc(reinterpret_cast<void**>(&ws), off, st)) != cudaSuccess)
     return (ssa_status)set_error(SSA_ENOMEM, cudaGetErrorString(e));
   auto fail_cuda = [&](cudaError_t err) {
     cudaFreeAsync(ws, st);
@@ -448,6 +498,25 @@ extern "C" ssa_status ssa_ensemble_grad(const ssa_model* model, int64_t n_traj, 
   a.Pc = Pc;
   a.Pgc = Pgc;
   a.gtraj = reinterpret_cast<double*>(ws + o_gtraj);
+  a.order = nullptr;
+  if (ordered) {
+    const long long* ev = reinterpret_cast<const long long*>(o.traj_events);
+    if (host) {
+      SSA_G_TRY(cudaMemcpyAsync(ws + o_ev, o.traj_events, 8 * (size_t)n_traj, cudaMemcpyHostToDevice, st));
+      ev = reinterpret_cast<const long long*>(ws + o_ev);
+    }
+    unsigned int* hist = reinterpret_cast<unsigned int*>(ws + o_hist);
+    unsigned int* order = reinterpret_cast<unsigned int*>(ws + o_order);
+    SSA_G_TRY(cudaMemsetAsync(hist, 0, 4 * 256, st));
+    const int hb = (int)std::min<long long>((n_traj + 255) / 256, 4LL * prop.multiProcessorCount);
+    k_order_hist<<<hb, 256, 0, st>>>(ev, n_traj, hist);
+    SSA_G_TRY(cudaGetLastError());
+    k_order_scan<<<1, 256, 0, st>>>(hist);
+    SSA_G_TRY(cudaGetLastError());
+    k_order_scatter<<<(unsigned)((n_traj + 255) / 256), 256, 0, st>>>(ev, n_traj, hist, order);
+    SSA_G_TRY(cudaGetLastError());
+    a.order = order;
+  }
   a.counter = reinterpret_cast<unsigned long long*>(ws + o_counter);
   const bool uniform = !grid || (host && host_grid_is_uniform(grid, G, t_end));
   a.grid_uniform = (uniform && G >= 2 && G <= (1 << 20) && t_end < 1e30) ? 1 : 0;

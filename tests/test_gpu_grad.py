@@ -80,6 +80,31 @@ def test_parity_explicit_grid_truncation_and_absorbing():
     _parity(death, 64, 50.0, 51, 3)
 
 
+def test_work_order_from_event_counts_changes_nothing():
+    """The forward's event counts only reorder the replay (longest first):
+    the gradient, its standard error and every per-trajectory contribution
+    are the same bits, with host and with device buffers, also for a
+    nonsense order hint."""
+    import torch
+    net = W.hiv_shaped()
+    n, G = 3000, 301
+    model = ssa.Model.from_network(net)
+    try:
+        f = ssa.ensemble_run(model, n, 30.0, G, 5, per_traj=True)
+        w = np.zeros((G, 4))
+        w[:, 2] = 1e-2
+        g0, se0, t0 = ssa.ensemble_grad(model, n, 30.0, G, 5, w, f.mean, per_traj=True)
+        g1, se1, t1 = ssa.ensemble_grad(model, n, 30.0, G, 5, w, f.mean, per_traj=True, traj_events=f.traj_events)
+        rev = np.arange(n, dtype=np.int64)[::-1].copy()
+        g2, se2, t2 = ssa.ensemble_grad(model, n, 30.0, G, 5, w, f.mean, per_traj=True, traj_events=rev)
+        gd, sed, td = ssa.ensemble_grad(model, n, 30.0, G, 5, torch.as_tensor(w), torch.as_tensor(f.mean),
+                                        device="cuda:0", per_traj=True, traj_events=torch.as_tensor(f.traj_events))
+        for g, se, t in ((g1, se1, t1), (g2, se2, t2), (gd.cpu().numpy(), sed.cpu().numpy(), td.cpu().numpy())):
+            assert np.array_equal(g, g0) and np.array_equal(se, se0) and np.array_equal(t, t0)
+    finally:
+        model.close()
+
+
 def test_repeatable_and_refusals():
     net = W.hiv_shaped()
     f = _forward(net, 2000, 30.0, 301, 7)
