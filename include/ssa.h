@@ -242,10 +242,11 @@ ssa_status ssa_ensemble_run(const ssa_model* model, int64_t n_traj, double t_end
  * opts->workspace, when non-NULL, receives the per-trajectory contributions
  * g (M x N, column r at r * N, same memory space; workspace_bytes >= 8 M N).
  * opts->traj_events, when non-NULL, is an input here: the forward's
- * per-trajectory event counts [N] (same memory space).  The replay then
- * starts the longest trajectories first; the results do not depend on it
- * (each contribution is kept at its trajectory's index and reduced in index
- * order), only the time the replay's last trajectories take.
+ * per-trajectory event counts [N] (same memory space).  When N is several
+ * times the GPU's resident threads, the replay then starts the longest
+ * trajectories first; the results do not depend on it (each contribution is
+ * kept at its trajectory's index and reduced in index order), only the time
+ * the replay's last trajectories take.
  * Host memory: synchronous.  Device memory: enqueued on opts->cuda_stream.
  * Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA, SSA_EUNSUPPORTED (FP32 mode, the
  * warp schedule, larger networks, a zero rate).

@@ -350,30 +350,34 @@ __global__ void k_order_scatter(const long long* ev, long long n, unsigned int* 
   if (i < n) order[atomicAdd(&next[order_bucket(ev[i])], 1u)] = (unsigned int)i;
 }
 
+// launch = false: only set the shared-memory size and report the blocks one
+// SM holds (*per_sm).
 template <int MAXM, int MAXS>
-cudaError_t launch_grad_t(const GradArgs& a, int blocks, cudaStream_t st) {
+cudaError_t launch_grad_t(const GradArgs& a, int blocks, cudaStream_t st, bool launch, int* per_sm) {
   const size_t smem = (size_t)kLogCells * 16 + (size_t)4 * MAXM * kGradThreads * 8 + (size_t)MAXM * MAXS * 4 +
                       (size_t)MAXM * 4;
   cudaError_t e = cudaFuncSetAttribute(k_ssa_grad<MAXM, MAXS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  if (!launch)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_ssa_grad<MAXM, MAXS>, kGradThreads, smem);
   k_ssa_grad<MAXM, MAXS><<<blocks, kGradThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <int MAXM>
-cudaError_t launch_grad_m(const GradArgs& a, int blocks, cudaStream_t st) {
+cudaError_t launch_grad_m(const GradArgs& a, int blocks, cudaStream_t st, bool launch, int* per_sm) {
   switch (bucket_s(a.S)) {
-    case 4: return launch_grad_t<MAXM, 4>(a, blocks, st);
-    case 8: return launch_grad_t<MAXM, 8>(a, blocks, st);
-    default: return launch_grad_t<MAXM, 16>(a, blocks, st);
+    case 4: return launch_grad_t<MAXM, 4>(a, blocks, st, launch, per_sm);
+    case 8: return launch_grad_t<MAXM, 8>(a, blocks, st, launch, per_sm);
+    default: return launch_grad_t<MAXM, 16>(a, blocks, st, launch, per_sm);
   }
 }
 
-cudaError_t launch_grad(const GradArgs& a, int blocks, cudaStream_t st) {
-  if (a.M <= 4) return launch_grad_m<4>(a, blocks, st);
-  if (a.M <= 8) return launch_grad_m<8>(a, blocks, st);
-  if (a.M <= 12) return launch_grad_m<12>(a, blocks, st);
-  return launch_grad_m<16>(a, blocks, st);
+cudaError_t launch_grad(const GradArgs& a, int blocks, cudaStream_t st, bool launch = true, int* per_sm = nullptr) {
+  if (a.M <= 4) return launch_grad_m<4>(a, blocks, st, launch, per_sm);
+  if (a.M <= 8) return launch_grad_m<8>(a, blocks, st, launch, per_sm);
+  if (a.M <= 12) return launch_grad_m<12>(a, blocks, st, launch, per_sm);
+  return launch_grad_m<16>(a, blocks, st, launch, per_sm);
 }
 
 }  // namespace
@@ -499,7 +503,15 @@ extern "C" ssa_status ssa_ensemble_grad(const ssa_model* model, int64_t n_traj, 
   a.Pgc = Pgc;
   a.gtraj = reinterpret_cast<double*>(ws + o_gtraj);
   a.order = nullptr;
-  if (ordered) {
+  // Longest first pays when lanes take several trajectories each; when every
+  // trajectory has a lane from the start it would only crowd the longest into
+  // the first blocks (and SMs), so the natural order stays.
+  int per_sm = 0;
+  a.M = M;
+  a.S = S;
+  SSA_G_TRY(launch_grad(a, 0, st, false, &per_sm));
+  const long long resident = (long long)std::max(per_sm, 1) * prop.multiProcessorCount * kGradThreads;
+  if (ordered && n_traj >= 4 * resident) {
     const long long* ev = reinterpret_cast<const long long*>(o.traj_events);
     if (host) {
       SSA_G_TRY(cudaMemcpyAsync(ws + o_ev, o.traj_events, 8 * (size_t)n_traj, cudaMemcpyHostToDevice, st));

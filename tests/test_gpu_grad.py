@@ -81,13 +81,15 @@ def test_parity_explicit_grid_truncation_and_absorbing():
 
 
 def test_work_order_from_event_counts_changes_nothing():
-    """The forward's event counts only reorder the replay (longest first):
-    the gradient, its standard error and every per-trajectory contribution
-    are the same bits, with host and with device buffers, also for a
-    nonsense order hint."""
+    """The forward's event counts only reorder the replay (longest first,
+    used when the ensemble is several times the resident threads: 240,000
+    trajectories here): the gradient, its standard error and every
+    per-trajectory contribution are the same bits, with host and with device
+    buffers, also for a nonsense order hint and for an ensemble below the
+    threshold."""
     import torch
     net = W.hiv_shaped()
-    n, G = 3000, 301
+    n, G = 240000, 301
     model = ssa.Model.from_network(net)
     try:
         f = ssa.ensemble_run(model, n, 30.0, G, 5, per_traj=True)
@@ -101,6 +103,10 @@ def test_work_order_from_event_counts_changes_nothing():
                                         device="cuda:0", per_traj=True, traj_events=torch.as_tensor(f.traj_events))
         for g, se, t in ((g1, se1, t1), (g2, se2, t2), (gd.cpu().numpy(), sed.cpu().numpy(), td.cpu().numpy())):
             assert np.array_equal(g, g0) and np.array_equal(se, se0) and np.array_equal(t, t0)
+        f3 = ssa.ensemble_run(model, 3000, 30.0, G, 6, per_traj=True)
+        a3 = ssa.ensemble_grad(model, 3000, 30.0, G, 6, w, f3.mean, per_traj=True)
+        b3 = ssa.ensemble_grad(model, 3000, 30.0, G, 6, w, f3.mean, per_traj=True, traj_events=f3.traj_events)
+        assert all(np.array_equal(x, y) for x, y in zip(a3, b3))
     finally:
         model.close()
 
