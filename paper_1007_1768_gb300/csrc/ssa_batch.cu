@@ -10,8 +10,9 @@
 // after network in launch order; work_begin[p] is the first item of the
 // network at position p.
 //
-// Launches.  Networks are ordered by chunk bucket (ceil(M / 32) rounded to
-// 1, 2, 4, 8, 16), then by descending M.  "Split" grouping runs one
+// Launches.  Networks are ordered by descending chunk bucket (ceil(M / 32)
+// rounded to 1, 2, 4, 8, 16), then by descending M: the costliest steps
+// first.  "Split" grouping runs one
 // persistent kernel per bucket (register use fits the bucket), the kernels
 // on parallel graph branches so that CTAs of one fill the SMs the tail of
 // another frees; "single" grouping runs one kernel for all networks at the
@@ -401,13 +402,15 @@ ssa_status ssa_batch_create(int32_t n_models, const ssa_model* const* models, co
   if (e != cudaSuccess) return bail(set_error(SSA_ECUDA, cudaGetErrorString(e)));
   b->sms = prop.multiProcessorCount;
 
-  // launch order: bucket ascending, then M descending (longer steps first), then index
+  // launch order: bucket descending, then M descending, then index -- the
+  // costliest steps first, so that in one kernel for all networks the
+  // largest networks' trajectories do not start last and end the launch
   const int n = n_models;
   b->order.resize(n);
   for (int i = 0; i < n; ++i) b->order[i] = i;
   std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
     const int bx = bucket_of(b->M[x]), by = bucket_of(b->M[y]);
-    if (bx != by) return bx < by;
+    if (bx != by) return bx > by;
     return b->M[x] > b->M[y];
   });
   b->pos.resize(n);
