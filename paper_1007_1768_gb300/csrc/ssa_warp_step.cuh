@@ -17,8 +17,11 @@
 // overall).  After an event every lane reads its bits of the fired
 // reaction's dependency mask (a per-reaction, per-lane table) and recomputes
 // only those propensities.  The state x lives in shared memory (S counts per
-// warp); the changes of the fired reaction are applied one per lane.  The
-// random numbers of 32 consecutive events are drawn at once, one per lane.
+// warp); the changes of the fired reaction are applied one per lane.  Events
+// run in batches of 32: the random numbers of the batch are drawn at once,
+// one per lane; the draws (selection and state update) run back to back, and
+// the waiting times, event times, end of the trajectory and the bookkeeping
+// of the kept events follow once per batch.
 // Selective memory (Sec. 3.2.1) is the difference-sum scheme of the thread
 // kernel: an event at time t changing x_s by v adds v and (2 x_s + v) v at
 // the first grid index k with g_k >= t.
@@ -202,217 +205,281 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
   int k = 0;
   unsigned long long hash = kFnvOffset;
   int flags = 0;
-  uint32_t base = 0;
-  unsigned long long cE = 0, cU = 0;
-  bool filled = false;
 
+  // Batches of 32 events (lane b holds event base + b's random numbers).  The
+  // draws run back to back: propensities, sums, selection and state update
+  // only.  Then lane b forms event b's waiting time, the warp forms the event
+  // times in order and finds where the trajectory ends (past t_end, overflow,
+  // max_events, an absorbing state), undoes the later applied events, and
+  // books the kept ones: grid indices, hash, and -- walking back through the
+  // batch to recover each event's pre-event counts -- difference sums, log
+  // records and the largest count.
   for (;;) {
-    // propensities of this lane's reactions that the last event touched
-#pragma unroll
-    for (int q = 0; q < MAXCH; ++q) {
-      if (q >= ch) break;
-      if ((dirty >> q) & 1u) {
-        const int j = my0 + q;
-        const int32_t w = net.rinfo[j];
-        const int kind = rinfo_kind(w);
-        const long long xa = xs[rinfo_a(w)];
-        const long long xb = xs[rinfo_b(w)];
-        const long long bi = xa * ((kind == kBi) ? xb : (xa - 1));
-        const long long h =
-            (kind == kOrder0) ? 1LL : ((kind == kUni) ? xa : ((kind == kBi) ? bi : (bi >> 1)));
-        // products on the FP32 pipe (FP32 mode) or as exact integer
-        // arithmetic (FP64 mode: the SM's FP64 unit binds the warp kernel)
-        if constexpr (F32) {
-          af[q] = __fmul_rn(net.c32[j], __ll2float_rn(h));
-        } else {
-          unsigned long long cb = net.cbits[j];
-          if (net.mod_f != nullptr) {  // state-dependent rate: clamp(c + k x_f, lo, hi), FP64
-            const int f = net.mod_f[j];
-            if (f >= 0) {
-              const double v = __dadd_rn(__longlong_as_double((long long)cb),
-                                         __dmul_rn(net.mod_k[j], (double)xs[f]));
-              cb = (unsigned long long)obits(fmin(fmax(v, net.mod_lo[j]), net.mod_hi[j]));
-            }
-          }
-          unsigned long long ab;
-          if (!propensity_int(cb, h, ab)) ab = propensity_fp64(cb, h);
-          av[q] = __longlong_as_double((long long)ab);
-        }
-      }
-    }
-    // schedule W32: running sums inside the chunk, Kogge-Stone scan of the
-    // chunk sums, prefixes excl + inner.  A past-the-end a_j (lanes owning
-    // fewer than ch reactions) is +0 and x + (+0) = x, so the last running
-    // sum is the chunk sum (+0 for an empty lane).
-    double run[MAXCH];   // FP64 mode: running sums
-    float run32[MAXCH];  // FP32 mode: binary32 running sums
-    double a0, excl = 0.0, sel_total;
-    float excl32 = 0.0f;
-    // loops over the chunk stop at ch (warp-uniform), the runtime chunk size
-    if constexpr (F32) {
-      // binary32 selection sums
-      float v32 = af[0];
-      run32[0] = v32;
-#pragma unroll
-      for (int q = 1; q < MAXCH; ++q) {
-        if (q >= ch) break;
-        v32 = __fadd_rn(v32, af[q]);
-        run32[q] = v32;
-      }
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const float u = __shfl_up_sync(kFullMask, v32, off);
-        if (lane >= off) v32 = __fadd_rn(v32, u);
-      }
-      excl32 = __shfl_up_sync(kFullMask, v32, 1);
-      sel_total = widen(__shfl_sync(kFullMask, v32, 31));
-      // a0, formed anew each event: the lane's chunk summed left to right in
-      // binary32 with its rounding errors carried (cascaded TwoSum), the two
-      // parts widened and added in FP64, the lane values scanned in FP64.
-      // A past-the-end a_j = +0 leaves both parts unchanged.
-      float cs = af[0], cerr = 0.0f;
-#pragma unroll
-      for (int q = 1; q < MAXCH; ++q) {
-        if (q >= ch) break;
-        const float x = af[q];
-        const float tt = __fadd_rn(cs, x);
-        const float bp = __fsub_rn(tt, cs);
-        const float d = __fadd_rn(__fsub_rn(cs, __fsub_rn(tt, bp)), __fsub_rn(x, bp));
-        cerr = __fadd_rn(cerr, d);
-        cs = tt;
-      }
-      double r64 = __dadd_rn(widen(cs), widen_signed(cerr));
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const double u = __shfl_up_sync(kFullMask, r64, off);
-        if (lane >= off) r64 = __dadd_rn(r64, u);
-      }
-      a0 = __shfl_sync(kFullMask, r64, 31);
-    } else {
-      double v = av[0];
-      run[0] = v;
-#pragma unroll
-      for (int q = 1; q < MAXCH; ++q) {
-        if (q >= ch) break;
-        v = __dadd_rn(v, av[q]);
-        run[q] = v;
-      }
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const double u = __shfl_up_sync(kFullMask, v, off);
-        if (lane >= off) v = __dadd_rn(v, u);
-      }
-      excl = __shfl_up_sync(kFullMask, v, 1);
-      a0 = __shfl_sync(kFullMask, v, 31);
-      sel_total = a0;
-    }
-    // random numbers of event n: 32 consecutive events drawn at once, one per lane
-    if (!filled || n >= base + 32u) {
-      base = n;
-      const EventRandom r = event_random(base + (uint32_t)lane, traj_id, net.sid, key0, key1, s_inv, s_lnf);
-      cE = r.E;
-      cU = r.u2;
-      filled = true;
-    }
-    const int slot = (int)(n - base);
-    const unsigned long long Eb = __shfl_sync(kFullMask, cE, slot);
-    const unsigned long long Ub = __shfl_sync(kFullMask, cU, slot);
-    const double t_next = __dadd_rn(t, quotient(Eb, a0));  // a0 == 0: +inf
-    const long long tb = obits(t_next);
-    if (tb > net.t_end_bits) break;
-    k = grid_index_net(net, tb, k);
-    // selection: first j with a_j > 0 and prefix_j > r2 * total (FP64
-    // product).  The a_j > 0 test matters at lane boundaries, where the
-    // scan's exclusive value can exceed the previous lane's last prefix by
-    // rounding.  FP32 mode: for a binary32 p and a double T >= 0,
-    // (double)p > T exactly when p > RD32(T), T rounded down to binary32, so
-    // the widened comparison runs on the binary32 bit patterns.
-    const double target = __dmul_rn(__longlong_as_double((long long)Ub), sel_total);
-    const long long gb = obits(target);
-    unsigned gf = 0;
-    if constexpr (F32) gf = __float_as_uint(__double2float_rd(target));
-    int myfirst = -1;
-#pragma unroll
-    for (int q = 0; q < MAXCH; ++q) {
-      if (q >= ch) break;
-      bool hitq;
-      if constexpr (F32) {
-        const float pre = (lane == 0) ? run32[q] : __fadd_rn(excl32, run32[q]);
-        hitq = (__float_as_uint(af[q]) != 0u) && (__float_as_uint(pre) > gf);
-      } else {
-        const double pre = (lane == 0) ? run[q] : __dadd_rn(excl, run[q]);
-        hitq = (obits(av[q]) > 0) && (obits(pre) > gb);
-      }
-      if (hitq && myfirst < 0 && q < mine) myfirst = my0 + q;
-    }
-    const unsigned hit = __ballot_sync(kFullMask, myfirst >= 0);
-    int jsel;
-    if (hit) {
-      jsel = __shfl_sync(kFullMask, myfirst, __ffs(hit) - 1);
-    } else {  // rounding left no j: the last reaction with a_j > 0
-      int mylast = -1;
+    const uint32_t base = n;
+    const EventRandom rr = event_random(base + (uint32_t)lane, traj_id, net.sid, key0, key1, s_inv, s_lnf);
+    double my_a0 = 0.0;  // lane b: a0 of event b
+    int my_j = 0;        // lane b: reaction of event b
+    int nb = 32;         // events applied (base .. base + nb - 1)
+    int nrec = 32;       // events whose time is formed: the applied ones and the one that stopped the draws
+#pragma unroll 1
+    for (int b = 0; b < 32; ++b) {
+      // propensities of this lane's reactions that the last event touched
 #pragma unroll
       for (int q = 0; q < MAXCH; ++q) {
         if (q >= ch) break;
-        const bool pos = F32 ? (__float_as_uint(af[q]) != 0u) : (obits(av[q]) > 0);
-        if (q < mine && pos) mylast = my0 + q;
-      }
-      const unsigned pos = __ballot_sync(kFullMask, mylast >= 0);
-      jsel = __shfl_sync(kFullMask, mylast, 31 - __clz(pos));
-    }
-    // state change of jsel, one nonzero entry per lane
-    const int q0 = net.nu_ptr[jsel], q1 = net.nu_ptr[jsel + 1];
-    bool over = false;
-    for (int e = q0 + lane; e < q1; e += 32)
-      over |= (long long)xs[net.nu_idx[e]] + (long long)net.nu_val[e] > kStateMax;
-    if (__any_sync(kFullMask, over)) {
-      flags |= kWarpFlagOverflow;
-      break;
-    }
-    __syncwarp();
-    bool logged = false;
-    // an event with no net change still adds its time to the union: one
-    // record with v = 0 (species 0, no effect on the sums)
-    const int nrec = (q1 > q0) ? (q1 - q0) : 1;
-    if constexpr (LOG) {
-      logged = log_reserve(*lg, *lst, nrec);
-      if (logged && q1 == q0 && lane == 0) {
-        const unsigned long long slot = lst->base + (unsigned long long)lst->fill;
-        lg->key[slot] = (unsigned long long)tb;
-        lg->rec[slot] = LogRec{0, 0, 0};
-      }
-    }
-    for (int e = q0 + lane; e < q1; e += 32) {
-      const int s = net.nu_idx[e];
-      const int vv = net.nu_val[e];
-      const int xo = xs[s];
-      const int xn = xo + vv;
-      xs[s] = xn;
-      maxx = max(maxx, xn);
-      const long long d2 = (2 * (long long)xo + vv) * (long long)vv;
-      if (k < net.G) {
-        atomicAdd(net.D1 + (size_t)k * S + s, (unsigned long long)(long long)vv);
-        atomicAdd(net.D2 + (size_t)k * S + s, (unsigned long long)d2);
-      }
-      if constexpr (LOG) {
-        if (logged) {
-          const unsigned long long slot = lst->base + (unsigned long long)(lst->fill + (e - q0));
-          lg->key[slot] = (unsigned long long)tb;
-          lg->rec[slot] = LogRec{s, vv, d2};
+        if ((dirty >> q) & 1u) {
+          const int j = my0 + q;
+          const int32_t w = net.rinfo[j];
+          const int kind = rinfo_kind(w);
+          const long long xa = xs[rinfo_a(w)];
+          const long long xb = xs[rinfo_b(w)];
+          const long long bi = xa * ((kind == kBi) ? xb : (xa - 1));
+          const long long h =
+              (kind == kOrder0) ? 1LL : ((kind == kUni) ? xa : ((kind == kBi) ? bi : (bi >> 1)));
+          // products on the FP32 pipe (FP32 mode) or as exact integer
+          // arithmetic (FP64 mode: the SM's FP64 unit binds the warp kernel)
+          if constexpr (F32) {
+            af[q] = __fmul_rn(net.c32[j], __ll2float_rn(h));
+          } else {
+            unsigned long long cb = net.cbits[j];
+            if (net.mod_f != nullptr) {  // state-dependent rate: clamp(c + k x_f, lo, hi), FP64
+              const int f = net.mod_f[j];
+              if (f >= 0) {
+                const double v = __dadd_rn(__longlong_as_double((long long)cb),
+                                           __dmul_rn(net.mod_k[j], (double)xs[f]));
+                cb = (unsigned long long)obits(fmin(fmax(v, net.mod_lo[j]), net.mod_hi[j]));
+              }
+            }
+            unsigned long long ab;
+            if (!propensity_int(cb, h, ab)) ab = propensity_fp64(cb, h);
+            av[q] = __longlong_as_double((long long)ab);
+          }
         }
       }
+      // schedule W32: running sums inside the chunk, Kogge-Stone scan of the
+      // chunk sums, prefixes excl + inner.  A past-the-end a_j (lanes owning
+      // fewer than ch reactions) is +0 and x + (+0) = x, so the last running
+      // sum is the chunk sum (+0 for an empty lane).
+      double run[MAXCH];   // FP64 mode: running sums
+      float run32[MAXCH];  // FP32 mode: binary32 running sums
+      double a0, excl = 0.0, sel_total;
+      float excl32 = 0.0f;
+      // loops over the chunk stop at ch (warp-uniform), the runtime chunk size
+      if constexpr (F32) {
+        // binary32 selection sums
+        float v32 = af[0];
+        run32[0] = v32;
+#pragma unroll
+        for (int q = 1; q < MAXCH; ++q) {
+          if (q >= ch) break;
+          v32 = __fadd_rn(v32, af[q]);
+          run32[q] = v32;
+        }
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const float u = __shfl_up_sync(kFullMask, v32, off);
+          if (lane >= off) v32 = __fadd_rn(v32, u);
+        }
+        excl32 = __shfl_up_sync(kFullMask, v32, 1);
+        sel_total = widen(__shfl_sync(kFullMask, v32, 31));
+        // a0, formed anew each event: the lane's chunk summed left to right in
+        // binary32 with its rounding errors carried (cascaded TwoSum), the two
+        // parts widened and added in FP64, the lane values scanned in FP64.
+        // A past-the-end a_j = +0 leaves both parts unchanged.
+        float cs = af[0], cerr = 0.0f;
+#pragma unroll
+        for (int q = 1; q < MAXCH; ++q) {
+          if (q >= ch) break;
+          const float x = af[q];
+          const float tt = __fadd_rn(cs, x);
+          const float bp = __fsub_rn(tt, cs);
+          const float d = __fadd_rn(__fsub_rn(cs, __fsub_rn(tt, bp)), __fsub_rn(x, bp));
+          cerr = __fadd_rn(cerr, d);
+          cs = tt;
+        }
+        double r64 = __dadd_rn(widen(cs), widen_signed(cerr));
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const double u = __shfl_up_sync(kFullMask, r64, off);
+          if (lane >= off) r64 = __dadd_rn(r64, u);
+        }
+        a0 = __shfl_sync(kFullMask, r64, 31);
+      } else {
+        double v = av[0];
+        run[0] = v;
+#pragma unroll
+        for (int q = 1; q < MAXCH; ++q) {
+          if (q >= ch) break;
+          v = __dadd_rn(v, av[q]);
+          run[q] = v;
+        }
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const double u = __shfl_up_sync(kFullMask, v, off);
+          if (lane >= off) v = __dadd_rn(v, u);
+        }
+        excl = __shfl_up_sync(kFullMask, v, 1);
+        a0 = __shfl_sync(kFullMask, v, 31);
+        sel_total = a0;
+      }
+      if (lane == b) my_a0 = a0;
+      if (obits(a0) == 0) {  // absorbing: the event's time is +inf
+        nb = b;
+        nrec = b + 1;
+        break;
+      }
+      // selection: first j with a_j > 0 and prefix_j > r2 * total (FP64
+      // product).  The a_j > 0 test matters at lane boundaries, where the
+      // scan's exclusive value can exceed the previous lane's last prefix by
+      // rounding.  FP32 mode: for a binary32 p and a double T >= 0,
+      // (double)p > T exactly when p > RD32(T), T rounded down to binary32, so
+      // the widened comparison runs on the binary32 bit patterns.
+      const unsigned long long Ub = __shfl_sync(kFullMask, rr.u2, b);
+      const double target = __dmul_rn(__longlong_as_double((long long)Ub), sel_total);
+      const long long gb = obits(target);
+      unsigned gf = 0;
+      if constexpr (F32) gf = __float_as_uint(__double2float_rd(target));
+      int myfirst = -1;
+#pragma unroll
+      for (int q = 0; q < MAXCH; ++q) {
+        if (q >= ch) break;
+        bool hitq;
+        if constexpr (F32) {
+          const float pre = (lane == 0) ? run32[q] : __fadd_rn(excl32, run32[q]);
+          hitq = (__float_as_uint(af[q]) != 0u) && (__float_as_uint(pre) > gf);
+        } else {
+          const double pre = (lane == 0) ? run[q] : __dadd_rn(excl, run[q]);
+          hitq = (obits(av[q]) > 0) && (obits(pre) > gb);
+        }
+        if (hitq && myfirst < 0 && q < mine) myfirst = my0 + q;
+      }
+      const unsigned hit = __ballot_sync(kFullMask, myfirst >= 0);
+      int jsel;
+      if (hit) {
+        jsel = __shfl_sync(kFullMask, myfirst, __ffs(hit) - 1);
+      } else {  // rounding left no j: the last reaction with a_j > 0
+        int mylast = -1;
+#pragma unroll
+        for (int q = 0; q < MAXCH; ++q) {
+          if (q >= ch) break;
+          const bool pos = F32 ? (__float_as_uint(af[q]) != 0u) : (obits(av[q]) > 0);
+          if (q < mine && pos) mylast = my0 + q;
+        }
+        const unsigned pos = __ballot_sync(kFullMask, mylast >= 0);
+        jsel = __shfl_sync(kFullMask, mylast, 31 - __clz(pos));
+      }
+      if (lane == b) my_j = jsel;
+      // state change of jsel, one nonzero entry per lane
+      const int q0 = net.nu_ptr[jsel], q1 = net.nu_ptr[jsel + 1];
+      bool over = false;
+      for (int e = q0 + lane; e < q1; e += 32)
+        over |= (long long)xs[net.nu_idx[e]] + (long long)net.nu_val[e] > kStateMax;
+      if (__any_sync(kFullMask, over)) {  // not applied: the trajectory ends here unless past t_end
+        nb = b;
+        nrec = b + 1;
+        break;
+      }
+      __syncwarp();
+      for (int e = q0 + lane; e < q1; e += 32) xs[net.nu_idx[e]] += net.nu_val[e];
+      __syncwarp();
+      dirty = net.depw[jsel * 32 + lane];
     }
-    if constexpr (LOG) {
-      if (logged) lst->fill += nrec;
+
+    // the event times in order (lane b: event b's waiting time)
+    const double my_tau = quotient(rr.E, my_a0);  // a0 == 0: +inf
+    double tt = t;
+    long long my_tb = 0;
+    int K = 0;      // events kept
+    int endf = -1;  // the trajectory ends: 0 past t_end, 1 max_events, 2 overflow
+    for (int b = 0; b < nrec && endf < 0; ++b) {
+      const double t_b = __dadd_rn(tt, __shfl_sync(kFullMask, my_tau, b));
+      const long long tb_b = obits(t_b);
+      if (lane == b) my_tb = tb_b;
+      if (tb_b > net.t_end_bits) {
+        endf = 0;
+      } else if (b == nb) {
+        endf = 2;
+      } else {
+        K = b + 1;
+        tt = t_b;
+        if ((long long)base + K == max_events) endf = 1;
+      }
     }
-    __syncwarp();
-    t = t_next;
-    ++n;
-    hash = (hash ^ (unsigned long long)jsel) * kFnvPrime;
-    hash = (hash ^ (unsigned long long)tb) * kFnvPrime;
-    dirty = net.depw[jsel * 32 + lane];
-    if ((long long)n == max_events) {
-      flags |= kWarpFlagTruncated;
+    // the applied events that were not kept, last first
+    for (int b = nb - 1; b >= K; --b) {
+      const int j = __shfl_sync(kFullMask, my_j, b);
+      const int q0 = net.nu_ptr[j], q1 = net.nu_ptr[j + 1];
+      for (int e = q0 + lane; e < q1; e += 32) xs[net.nu_idx[e]] -= net.nu_val[e];
+      __syncwarp();
+    }
+    // grid indices (lane b: event b's) and the sequence hash, in order
+    int my_k = k, kk = k;
+    for (int b = 0; b < K; ++b) {
+      const int j = __shfl_sync(kFullMask, my_j, b);
+      const long long tb_b = __shfl_sync(kFullMask, my_tb, b);
+      kk = grid_index_net(net, tb_b, kk);
+      if (lane == b) my_k = kk;
+      hash = (hash ^ (unsigned long long)j) * kFnvPrime;
+      hash = (hash ^ (unsigned long long)tb_b) * kFnvPrime;
+    }
+    // kept events, last first: the counts before each one (walking the state
+    // back), its difference sums and log records, the largest count
+    for (int b = K - 1; b >= 0; --b) {
+      const int j = __shfl_sync(kFullMask, my_j, b);
+      const long long tb_b = __shfl_sync(kFullMask, my_tb, b);
+      const int kb = __shfl_sync(kFullMask, my_k, b);
+      const int q0 = net.nu_ptr[j], q1 = net.nu_ptr[j + 1];
+      bool logged = false;
+      // an event with no net change still adds its time to the union: one
+      // record with v = 0 (species 0, no effect on the sums)
+      const int nrc = (q1 > q0) ? (q1 - q0) : 1;
+      if constexpr (LOG) {
+        logged = log_reserve(*lg, *lst, nrc);
+        if (logged && q1 == q0 && lane == 0) {
+          const unsigned long long slot = lst->base + (unsigned long long)lst->fill;
+          lg->key[slot] = (unsigned long long)tb_b;
+          lg->rec[slot] = LogRec{0, 0, 0};
+        }
+      }
+      for (int e = q0 + lane; e < q1; e += 32) {
+        const int s = net.nu_idx[e];
+        const int vv = net.nu_val[e];
+        const int xn = xs[s];
+        const int xo = xn - vv;
+        xs[s] = xo;
+        maxx = max(maxx, xn);
+        const long long d2 = (2 * (long long)xo + vv) * (long long)vv;
+        if (kb < net.G) {
+          atomicAdd(net.D1 + (size_t)kb * S + s, (unsigned long long)(long long)vv);
+          atomicAdd(net.D2 + (size_t)kb * S + s, (unsigned long long)d2);
+        }
+        if constexpr (LOG) {
+          if (logged) {
+            const unsigned long long slot = lst->base + (unsigned long long)(lst->fill + (e - q0));
+            lg->key[slot] = (unsigned long long)tb_b;
+            lg->rec[slot] = LogRec{s, vv, d2};
+          }
+        }
+      }
+      if constexpr (LOG) {
+        if (logged) lst->fill += nrc;
+      }
+      __syncwarp();
+    }
+    // and forward again to the state after the kept events
+    for (int b = 0; b < K; ++b) {
+      const int j = __shfl_sync(kFullMask, my_j, b);
+      const int q0 = net.nu_ptr[j], q1 = net.nu_ptr[j + 1];
+      for (int e = q0 + lane; e < q1; e += 32) xs[net.nu_idx[e]] += net.nu_val[e];
+      __syncwarp();
+    }
+    if (K > 0) {
+      t = tt;
+      k = kk;
+    }
+    n += (uint32_t)K;
+    if (endf >= 0) {
+      flags |= (endf == 1) ? kWarpFlagTruncated : ((endf == 2) ? kWarpFlagOverflow : 0);
       break;
     }
   }
