@@ -54,7 +54,7 @@ WORKLOADS = {
     # profiles/ (model tables and grid; independent of the trajectory count)
     "random": {"factory": "workload_random", "name": "random_S32_M128_G1001_T10_netseed3", "n_traj": 262144,
                "steps": 10, "e2e_steps": 3, "cpu_sample": 2048, "ref_sample": 512,
-               "kernel": "k_ssa_warp", "dram_bytes": {"fp64": 592128, "fp32": 588032}},
+               "kernel": "k_ssa_warp", "dram_bytes": {"fp64": 834816, "fp32": 595456}},
     "grad": {"factory": "workload_hiv_shaped", "name": "hiv_shaped_grad_S4_M10_G3001_T30_loss_V", "n_traj": 1048576,
              "steps": 5, "e2e_steps": 2, "cpu_sample": 2048, "ref_sample": 1024,
              "kernel": "k_ssa_grad", "dram_bytes": 256680000},
