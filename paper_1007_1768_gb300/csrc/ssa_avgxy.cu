@@ -279,6 +279,7 @@ __global__ void k_union_times(const u64* keys, long long nv, const unsigned int*
 constexpr int kWinThreads = 256;
 constexpr int kWinRecords = 4096;
 constexpr int kWinSlots = 512;
+constexpr int kWinRegS = 8;  // species summed in registers on the one-window path
 
 __global__ void __launch_bounds__(kWinThreads) k_window_sums(
     const unsigned int* head, const unsigned int* uidx, const unsigned int* perm, const LogRec* rec,
@@ -292,6 +293,52 @@ __global__ void __launch_bounds__(kWinThreads) k_window_sums(
   const bool local = (p_hi - p_lo + 1) * S <= kWinSlots;
   for (int i = threadIdx.x; i < kWinSlots; i += blockDim.x) sW1[i] = sA1[i] = sW2[i] = sA2[i] = 0;
   __syncthreads();
+  if (p_lo == p_hi && S <= kWinRegS) {
+    // one window and few species (the usual case for wide windows): each
+    // thread sums its records per species in registers, a warp adds its
+    // threads' sums by shuffle, and one lane per warp adds them to the
+    // block's slots -- instead of four contended shared atomics per record
+    const long long b = min(U, (p_lo + 1) * k);
+    long long w1[kWinRegS], a1[kWinRegS], w2[kWinRegS], a2[kWinRegS];
+#pragma unroll
+    for (int i = 0; i < kWinRegS; ++i) w1[i] = a1[i] = w2[i] = a2[i] = 0;
+    for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+      const long long u = (long long)uidx[r] + head[r];
+      const LogRec rq = rec[perm[r]];
+      const long long v = rq.change, dd = rq.d2, wt = b - u;
+      const long long vw = v * wt, dw = dd * wt;
+#pragma unroll
+      for (int i = 0; i < kWinRegS; ++i) {
+        const bool m = rq.species == i;
+        w1[i] += m ? v : 0;
+        a1[i] += m ? vw : 0;
+        w2[i] += m ? dd : 0;
+        a2[i] += m ? dw : 0;
+      }
+    }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < kWinRegS; ++i) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        w1[i] += __shfl_xor_sync(0xFFFFFFFFu, w1[i], off);
+        a1[i] += __shfl_xor_sync(0xFFFFFFFFu, a1[i], off);
+        w2[i] += __shfl_xor_sync(0xFFFFFFFFu, w2[i], off);
+        a2[i] += __shfl_xor_sync(0xFFFFFFFFu, a2[i], off);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < kWinRegS; ++i) {
+        if (i < S) {
+          atomicAdd(reinterpret_cast<unsigned long long*>(&sW1[i]), (unsigned long long)w1[i]);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&sA1[i]), (unsigned long long)a1[i]);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&sW2[i]), (unsigned long long)w2[i]);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&sA2[i]), (unsigned long long)a2[i]);
+        }
+      }
+    }
+  } else {
   for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
     const long long u = (long long)uidx[r] + head[r];
     const long long p = u / k;
@@ -313,6 +360,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_sums(
       atomicAdd(reinterpret_cast<unsigned long long*>(W2 + g), (unsigned long long)dd);
       atomicAdd(reinterpret_cast<unsigned long long*>(A2 + g), (unsigned long long)(dd * wt));
     }
+  }
   }
   __syncthreads();
   if (local) {
