@@ -102,10 +102,12 @@ typedef struct ssa_run_opts {
   uint64_t traj_offset;   /* id of the first trajectory; ids are traj_offset .. traj_offset + n_traj - 1 */
   uint64_t stream_id;     /* fourth word of the random counter, < 2^32 (e.g. a network index) */
   void* cuda_stream;      /* cudaStream_t to run on; NULL = the legacy default stream */
-  void* workspace;        /* device scratch of workspace_bytes; NULL = allocated and freed on the stream */
+  void* workspace;        /* device scratch of workspace_bytes; NULL = taken from the library's stream-ordered
+                           * pool and returned to it (ssa_release_cached_memory) */
   size_t workspace_bytes;
   /* Optional per-trajectory outputs, [n_traj] each, in opts->memory's space; NULL to skip:
-   * events fired, a 64-bit hash of the (reaction index, event time bits) sequence, flag bits. */
+   * events fired, a 64-bit hash of the (reaction index, event time bits) sequence, flag bits.
+   * (ssa_ensemble_grad reads traj_events as an input: the forward's counts.) */
   int64_t* traj_events;
   uint64_t* traj_hash;
   int32_t* traj_flags;
