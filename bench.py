@@ -40,9 +40,9 @@ if ROOT not in sys.path:
 METRIC = "SSA reaction events/s incl. grid align+mean/var reduce, 1 GB300, vs plain FP64"
 UNIT = "events/s"
 SMS_GB300 = 152
-# DRAM read + write bytes of one k_ssa_thread launch (ncu capture summarised in
-# profiles/k_ssa_thread_hiv_shaped.md: tables, grid and parameters; the
-# difference sums stay in L2), independent of the number of trajectories.
+# DRAM read + write bytes of one k_ssa_thread launch (from an ncu capture:
+# tables, grid and parameters; the difference sums stay in L2), independent of
+# the number of trajectories.
 SIM_KERNEL_DRAM_BYTES = 689920
 # Bench workloads: the HIV-shaped model (the headline line) and the random
 # 32-species / 128-reaction network (one trajectory per warp).
@@ -50,8 +50,8 @@ WORKLOADS = {
     "hiv_shaped": {"factory": "workload_hiv_shaped", "name": "hiv_shaped_S4_M10_G3001_T30", "n_traj": 65536,
                    "steps": 100, "e2e_steps": 20, "cpu_sample": 16384, "ref_sample": 4096,
                    "kernel": "k_ssa_thread", "dram_bytes": SIM_KERNEL_DRAM_BYTES},
-    # DRAM bytes per launch of the simulation kernel from the ncu captures in
-    # profiles/ (model tables and grid; independent of the trajectory count)
+    # DRAM bytes per launch of the simulation kernel from ncu captures (model
+    # tables and grid; independent of the trajectory count)
     "random": {"factory": "workload_random", "name": "random_S32_M128_G1001_T10_netseed3", "n_traj": 262144,
                "steps": 10, "e2e_steps": 3, "cpu_sample": 2048, "ref_sample": 512,
                "kernel": "k_ssa_warp", "dram_bytes": {"fp64": 834816, "fp32": 595456}},
@@ -98,14 +98,6 @@ def parse_args():
     p.add_argument("--profile-small", action="store_true",
                    help="one small step for an ncu capture (--profile-n trajectories); prints no bench line")
     p.add_argument("--profile-n", type=int, default=16384)
-    p.add_argument("--scan", action="store_true",
-                   help="time one ensemble per trajectory count (32 .. 1,048,576) and print, per count, the "
-                        "cycles per event of its longest trajectory (the serial floor of the step)")
-    p.add_argument("--solo", type=int, default=None, metavar="ID",
-                   help="run trajectory ID of the HIV-shaped workload alone (seed 1000) and print its "
-                        "kernel time and cycles per event")
-    p.add_argument("--probe", choices=["pipes", "latency", "step"],
-                   help="build and run one of the pipe / latency / step-part probes in csrc/probes")
     args = p.parse_args()
     spec = WORKLOADS[args.workload]
     args.steps = spec["steps"] if args.steps is None else args.steps
@@ -832,63 +824,8 @@ def cpu_baseline_batch(ws, per_network: int):
                       f"{dt:.2f} s on {cores} threads"}
 
 
-def run_scan():
-    """Kernel time per trajectory count for the HIV-shaped model; for counts
-    up to 65,536 also the longest trajectory's events, whose serial chain sets
-    the floor of the kernel time."""
-    import paper_1007_1768_gb300 as ssa
-    import workloads as W
-    net = W.hiv_shaped()
-    model = ssa.Model.from_network(net)
-    for n in [32, 128, 1024, 16384, 65536, 262144, 1048576]:
-        best = None
-        for rep in range(3):
-            r = ssa.ensemble_run(model, n, 30.0, 3001, 1000 + rep, per_traj=n <= 65536, want_sums=False)
-            if best is None or r.kernel_ms < best.kernel_ms:
-                best = r
-        mx = int(best.traj_events.max()) if best.traj_events is not None else None
-        line = {"n_traj": n, "kernel_ms": round(best.kernel_ms, 3), "events": best.events,
-                "events_per_s": best.events / best.kernel_ms * 1e3, "max_traj_events": mx,
-                "cycles_per_event_of_longest_at_2070MHz": round(best.kernel_ms * 2.07e6 / mx, 1) if mx else None}
-        print(json.dumps(line), flush=True)
-    return 0
-
-
-def run_solo(traj_id: int):
-    """One trajectory of the HIV-shaped workload (seed 1000) alone: with one
-    lane group of one warp busy, its kernel time is the serial chain of its
-    events (the cooperative mode from the first event)."""
-    import paper_1007_1768_gb300 as ssa
-    import workloads as W
-    w = W.workload_hiv_shaped()
-    model = ssa.Model.from_network(w.net)
-    for rep in range(3):
-        r = ssa.ensemble_run(model, 1, w.t_end, w.n_grid, 1000, traj_offset=traj_id, per_traj=True)
-        ev = int(r.traj_events[0])
-        print(json.dumps({"traj_id": traj_id, "events": ev, "kernel_ms": round(r.kernel_ms, 3),
-                          "cycles_per_event_at_2070MHz": round(r.kernel_ms * 2.07e6 / max(ev, 1), 1)}), flush=True)
-    return 0
-
-
-def run_probe(name: str):
-    """Builds csrc/probes/probe_<name>.cu with nvcc for sm_103a and runs it."""
-    from paper_1007_1768_gb300 import build as libbuild
-    src = os.path.join(ROOT, "paper_1007_1768_gb300", "csrc", "probes", f"probe_{name}.cu")
-    exe = os.path.join(libbuild.BUILD, f"probe_{name}")
-    os.makedirs(libbuild.BUILD, exist_ok=True)
-    subprocess.run([libbuild.nvcc(), "-O3", "-std=c++17", "-fmad=false", "-I", libbuild.INCLUDE, *libbuild.ARCH,
-                    "-o", exe, src], check=True)
-    return subprocess.run([exe]).returncode
-
-
 def main():
     args = parse_args()
-    if args.scan:
-        return run_scan()
-    if args.probe:
-        return run_probe(args.probe)
-    if args.solo is not None:
-        return run_solo(args.solo)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
