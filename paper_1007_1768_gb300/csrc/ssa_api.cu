@@ -695,6 +695,18 @@ cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st) {
 
 void clear_error() { g_last_error.clear(); }
 
+bool model_small_copy(const ssa_model* m, SmallModelCopy* out) {
+  if (!m || !out) return false;
+  ssa_model* mm = const_cast<ssa_model*>(m);
+  std::lock_guard<std::mutex> lk(mm->mu);
+  out->S = m->S;
+  out->M = m->M;
+  out->has_small = m->has_small;
+  out->has_mod = m->has_mod;
+  out->small = m->small;
+  return true;
+}
+
 bool model_image_view(const ssa_model* m, ModelImageView* v) {
   if (!m || !v) return false;
   v->S = m->S;

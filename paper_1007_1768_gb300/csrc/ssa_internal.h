@@ -300,6 +300,14 @@ void model_log_size_put(const ssa_model* m, const LogSize& v);
 // ssa_release_cached_memory returns it to the driver).
 cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st);
 bool model_image_view(const ssa_model* m, ModelImageView* v);
+// A copy of a model's sizes and small tables, taken under the model's lock.
+struct SmallModelCopy {
+  int32_t S, M;
+  bool has_small;  // M <= 16 and S <= 16 and no rate modifiers: `small` is filled
+  bool has_mod;    // rate modifiers present
+  SmallModel small;
+};
+bool model_small_copy(const ssa_model* m, SmallModelCopy* out);
 // The model's device tables on `dev` (copied there on first use); returns
 // SSA_OK or an error status with the thread's message set.
 int model_device_tables(const ssa_model* m, int dev, DevModel* out);

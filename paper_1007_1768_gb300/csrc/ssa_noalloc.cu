@@ -7,7 +7,7 @@
 // real-time loops that must not block on allocation.  This entry point
 // serves them.  It allocates nothing: no cudaMalloc, no cudaMallocAsync, no
 // cudaFree, no allocating library call.  Its scratch memory (work counter,
-// totals, per-grid difference sums, the uniform grid and the model tables)
+// totals, per-grid difference sums, the uniform grid and the initial counts)
 // lives in one file-scope device array of fixed size, kNoAllocScratchBytes,
 // that every GPU loading the library holds until the process exits.  The
 // caller passes every input and output buffer.
@@ -22,6 +22,12 @@
 // The first call on a device looks up the device address of the array with
 // cudaGetSymbolAddress (with that device current) and caches it.  That first
 // call should therefore come before any stream capture on that device.
+//
+// The call moves no data from host memory: the kernel takes the model's
+// small tables by value (kernel parameters), and the one table the
+// finalisation reads from device memory (x0) is written into the scratch by a
+// one-warp kernel from a by-value copy.  The host thread waits only when the
+// caller asks for stats.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -77,6 +83,16 @@ ssa_status scratch_on_device(int dev, unsigned char** out, int* sms, size_t* sme
   return SSA_OK;
 }
 
+// The initial counts, by value, for the one-warp kernel below.
+struct X0Words {
+  int32_t v[kSmallMax];
+};
+
+__global__ void k_put_x0(int32_t* dst, X0Words x0, int S) {
+  const int s = threadIdx.x;
+  if (s < S) dst[s] = x0.v[s];
+}
+
 }  // namespace
 
 extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n_traj, double t_end,
@@ -86,8 +102,10 @@ extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n
   clear_error();
   ssa_run_opts o;
   if (opts) o = *opts; else ssa_run_opts_init(&o);
-  ModelImageView mv;
-  if (!model || !model_image_view(model, &mv)) return record_error(SSA_EINVAL, "model is NULL");
+  // a consistent copy of the model's small tables (taken under the model's
+  // lock, so a concurrent ssa_model_set_rate_modifier cannot tear it)
+  SmallModelCopy mc;
+  if (!model || !model_small_copy(model, &mc)) return record_error(SSA_EINVAL, "model is NULL");
   if (n_traj < 1) return record_error(SSA_EINVAL, "n_traj must be >= 1");
   if (!(t_end > 0.0) || !std::isfinite(t_end)) return record_error(SSA_EINVAL, "t_end must be finite and > 0");
   if (n_grid < 1) return record_error(SSA_EINVAL, "n_grid must be >= 1");
@@ -95,8 +113,13 @@ extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n
   if (o.memory != SSA_MEM_DEVICE)
     return record_error(SSA_EINVAL, "ssa_ensemble_run_noalloc takes device buffers only (memory = SSA_MEM_DEVICE)");
   if (o.precision != SSA_PREC_FP64) return record_error(SSA_EUNSUPPORTED, "this entry point runs SSA_PREC_FP64 only");
-  if (o.schedule == SSA_SCHED_WARP || !mv.small)
+  if (mc.has_mod)
+    return record_error(SSA_EUNSUPPORTED,
+                        "models with rate modifiers run on the warp schedule, which this entry point does not serve");
+  if (o.schedule == SSA_SCHED_WARP || !mc.has_small)
     return record_error(SSA_EUNSUPPORTED, "networks with more than 16 reactions or species are not supported here");
+  if (o.schedule < SSA_SCHED_AUTO || o.schedule > SSA_SCHED_WARP) return record_error(SSA_EINVAL, "bad schedule");
+  if (o.reduce < SSA_REDUCE_AUTO || o.reduce > SSA_REDUCE_GLOBAL) return record_error(SSA_EINVAL, "bad reduce mode");
   if (o.block_threads < 0 || o.block_threads > 512 || (o.block_threads % 32) != 0)
     return record_error(SSA_EINVAL, "block_threads must be 0 or a multiple of 32 up to 512");
   if (o.grid_blocks < 0) return record_error(SSA_EINVAL, "grid_blocks must be >= 0");
@@ -104,21 +127,21 @@ extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n
   if (o.stream_id > 0xFFFFFFFFULL) return record_error(SSA_EINVAL, "stream_id must be below 2^32");
 
   // scratch layout inside the fixed array
-  const size_t gs = (size_t)n_grid * (size_t)mv.S;
+  const size_t gs = (size_t)n_grid * (size_t)mc.S;
   auto up = [](size_t v) { return align_up(v, 256); };
   const size_t off_counter = 0;
   const size_t off_stats = up(off_counter + 8);
   const size_t off_d1 = up(off_stats + 8 * kStatCount);
   const size_t off_d2 = up(off_d1 + 8 * gs);
   const size_t off_grid = up(off_d2 + 8 * gs);
-  const size_t off_model = up(off_grid + 8 * (size_t)n_grid);
-  const size_t need = up(off_model + mv.bytes);
+  const size_t off_x0 = up(off_grid + 8 * (size_t)n_grid);
+  const size_t need = up(off_x0 + 4 * (size_t)kSmallMax);
   if (gs > ((size_t)1 << 31) || need > kNoAllocScratchBytes) {
     char msg[256];
     snprintf(msg, sizeof msg,
              "ssa_ensemble_run_noalloc needs %zu bytes of scratch for n_grid = %d and %d species; its fixed "
              "scratch holds %zu bytes (SSA_NOALLOC_SCRATCH_BYTES)",
-             need, n_grid, mv.S, kNoAllocScratchBytes);
+             need, n_grid, mc.S, kNoAllocScratchBytes);
     return record_error(SSA_EINVAL, msg);
   }
 
@@ -133,7 +156,7 @@ extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n
 
   // launch shape (same rule as ssa_ensemble_run)
   LaunchPlan plan;
-  if (const char* msg = plan_thread_launch(mv.S, mv.M, n_grid, n_traj, sms, smem_optin, o.reduce, o.block_threads,
+  if (const char* msg = plan_thread_launch(mc.S, mc.M, n_grid, n_traj, sms, smem_optin, o.reduce, o.block_threads,
                                            o.grid_blocks, &plan))
     return record_error(SSA_EINVAL, msg);
 
@@ -142,13 +165,17 @@ extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n
     snprintf(msg, sizeof msg, "%s: %s", what, cudaGetErrorString(e));
     return record_error(SSA_ECUDA, msg);
   };
-  cudaError_t e = thread_kernel_set_smem(mv.M, mv.S, plan.shared_d, plan.smem);
+  cudaError_t e = thread_kernel_set_smem(mc.M, mc.S, plan.shared_d, plan.smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   // counter, totals and difference sums start at zero on every call
   e = cudaMemsetAsync(scratch, 0, off_grid, stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(scratch)");
-  e = cudaMemcpyAsync(scratch + off_model, mv.image, mv.bytes, cudaMemcpyHostToDevice, stream);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(model tables)");
+  int32_t* d_x0 = reinterpret_cast<int32_t*>(scratch + off_x0);
+  X0Words x0w = {};
+  for (int s = 0; s < mc.S; ++s) x0w.v[s] = mc.small.x0[s];
+  k_put_x0<<<1, 32, 0, stream>>>(d_x0, x0w, mc.S);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "initial counts kernel");
   const double* d_grid = grid;
   if (!d_grid) {
     double* g = reinterpret_cast<double*>(scratch + off_grid);
@@ -157,23 +184,12 @@ extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n
     d_grid = g;
   }
 
-  const unsigned char* b = scratch + off_model;
   RunArgs a;
-  a.sm = *mv.small;
-  a.m.S = mv.S;
-  a.m.M = mv.M;
-  a.m.nnz = mv.nnz;
-  a.m.ndep = mv.ndep;
-  a.m.c = reinterpret_cast<const double*>(b + mv.off_c);
-  a.m.rinfo = reinterpret_cast<const int32_t*>(b + mv.off_rinfo);
-  a.m.nu_ptr = reinterpret_cast<const int32_t*>(b + mv.off_nu_ptr);
-  a.m.nu_idx = reinterpret_cast<const int32_t*>(b + mv.off_nu_idx);
-  a.m.nu_val = reinterpret_cast<const int32_t*>(b + mv.off_nu_val);
-  a.m.x0 = reinterpret_cast<const int32_t*>(b + mv.off_x0);
-  a.m.dep_ptr = reinterpret_cast<const int32_t*>(b + mv.off_dep_ptr);
-  a.m.dep_idx = reinterpret_cast<const int32_t*>(b + mv.off_dep_idx);
-  a.m.mod_f = nullptr;  // the thread schedule serves plain mass action only
-  a.m.mod_k = a.m.mod_lo = a.m.mod_hi = nullptr;
+  a.sm = mc.small;
+  a.m = DevModel{};  // the thread kernel reads the small tables from its parameters
+  a.m.S = mc.S;
+  a.m.M = mc.M;
+  a.m.x0 = d_x0;
   a.G = n_grid;
   a.N = n_traj;
   a.traj_offset = o.traj_offset;
@@ -194,9 +210,17 @@ extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n
   a.grid_scale = (float)((double)(n_grid - 1) / t_end);
   a.grid_margin = (float)((double)n_grid * 0x1p-21);
 
+  if (o.sim_event_begin) {
+    e = cudaEventRecord(static_cast<cudaEvent_t>(o.sim_event_begin), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(sim_event_begin)");
+  }
   e = launch_thread_kernel(a, plan.blocks, plan.threads, plan.shared_d, plan.smem, stream);
   if (e != cudaSuccess) return cuda_fail(e, "simulation kernel");
-  e = launch_finalize(a.D1, a.D2, n_grid, mv.S, n_traj, a.m.x0, mean, var, sum1, sum2, stream);
+  if (o.sim_event_end) {
+    e = cudaEventRecord(static_cast<cudaEvent_t>(o.sim_event_end), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(sim_event_end)");
+  }
+  e = launch_finalize(a.D1, a.D2, n_grid, mc.S, n_traj, a.m.x0, mean, var, sum1, sum2, stream);
   if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
   if (!stats) return SSA_OK;
 
