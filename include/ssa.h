@@ -147,6 +147,22 @@ const char* ssa_last_error(void);
  * the driver.  Call when no library work is in flight.  Errors: SSA_ECUDA. */
 ssa_status ssa_release_cached_memory(void);
 
+/*
+ * ssa_finalize_sums — the average and variance of Sec. 4 from int64 grid sums
+ * (step A8) on the host, for sums added across shards: trajectories are
+ * fixed by (seed, id, stream id), so runs over contiguous id ranges
+ * (opts->traj_offset) add up to the sums of one run bit for bit.
+ *   sum1, sum2: [n_grid x n_species] row-major host arrays of sum x and
+ *     sum x^2 over n_traj trajectories (sum1, sum2 of ssa_ensemble_run);
+ *   mean, var: [n_grid x n_species] host outputs (caller-owned).
+ * mean = sum1 / N; var = (N sum2 - sum1^2) / (N (N - 1)) with the numerator
+ * exact in 128 bits and rounded once; NaN when N = 1.  The values are
+ * bit-identical to what the device finalisation writes for a single run.
+ * Errors: SSA_EINVAL (n_traj < 1, n_grid < 1, n_species < 1, NULL arrays).
+ */
+ssa_status ssa_finalize_sums(int64_t n_traj, int32_t n_grid, int32_t n_species, const int64_t* sum1,
+                             const int64_t* sum2, double* mean, double* var);
+
 /* Fills *opts with the defaults: FP64, AUTO schedule and reduction, host
  * memory, default max_events, offset 0, stream id 0, default CUDA stream,
  * library-managed workspace, no per-trajectory outputs. */
@@ -308,17 +324,22 @@ ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj, double t_
  * block on an allocation.
  *
  * It calls no cudaMalloc, cudaMallocAsync, cudaFree or other allocating
- * routine.  Its scratch (work counter, totals, per-grid difference sums, the
- * uniform grid and the model's tables) lives in one fixed device array of
- * SSA_NOALLOC_SCRATCH_BYTES per GPU.  The caller passes all inputs and outputs:
+ * routine, and copies nothing from host memory: the model's tables travel as
+ * kernel parameters.  Its scratch (work counter, totals, per-grid difference
+ * sums, the uniform grid and the initial counts) lives in one fixed device
+ * array of SSA_NOALLOC_SCRATCH_BYTES per GPU.  The caller passes all inputs
+ * and outputs:
  *   opts->memory must be SSA_MEM_DEVICE; grid (NULL for the uniform grid),
  *   mean, var [G x S] and the optional sum1, sum2 [G x S] and per-trajectory
  *   outputs are device pointers on the current device.  stats is a host
  *   struct or NULL; when non-NULL the call waits for the stream (kernel_ms is
- *   reported as 0).  opts->workspace is ignored.
- * Limits: 16 * n_grid * n_species + 8 * n_grid + the model's tables (plus
- * alignment) must fit in SSA_NOALLOC_SCRATCH_BYTES, else SSA_EINVAL with a
- * message giving the bytes needed.  Networks with at most 16 reactions, FP64.
+ *   reported as 0); otherwise it only enqueues work.  opts->workspace is
+ *   ignored; opts->sim_event_begin / sim_event_end are recorded around the
+ *   simulation kernel as in ssa_ensemble_run.
+ * Limits: 16 * n_grid * n_species + 8 * n_grid + 64 bytes (plus alignment)
+ * must fit in SSA_NOALLOC_SCRATCH_BYTES, else SSA_EINVAL with a message
+ * giving the bytes needed.  Networks with at most 16 reactions and 16
+ * species, FP64, without rate modifiers (others: SSA_EUNSUPPORTED).
  * Sharing: every call uses the same array and overwrites what the previous
  * call left there; each call clears what must start at zero on its own stream.
  * Calls whose GPU work overlaps (several streams or host threads on one

@@ -30,7 +30,7 @@ EXPORTS = [
     "ssa_model_info", "ssa_ensemble_workspace_size", "ssa_ensemble_run", "ssa_ensemble_run_noalloc",
     "ssa_batch_create", "ssa_batch_tune", "ssa_batch_launch", "ssa_batch_result", "ssa_batch_network_stats",
     "ssa_batch_destroy", "ssa_batch_run", "ssa_ensemble_grad", "ssa_ensemble_avg_xy",
-    "ssa_model_set_rate_modifier", "ssa_release_cached_memory",
+    "ssa_model_set_rate_modifier", "ssa_release_cached_memory", "ssa_finalize_sums",
 ]
 
 
@@ -116,6 +116,8 @@ def lib():
         L.ssa_ensemble_avg_xy.argtypes = [vp, i64, f64, u64, ctypes.POINTER(RunOpts), i64, i64, vp, vp, vp,
                                           ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.ssa_ensemble_avg_xy.restype = ctypes.c_int
+        L.ssa_finalize_sums.argtypes = [i64, i32, i32, vp, vp, vp, vp]
+        L.ssa_finalize_sums.restype = ctypes.c_int
         L.ssa_release_cached_memory.argtypes = []
         L.ssa_release_cached_memory.restype = ctypes.c_int
         _lib = L

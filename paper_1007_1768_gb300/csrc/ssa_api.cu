@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -395,6 +396,28 @@ ssa_status ssa_release_cached_memory(void) {
   std::lock_guard<std::mutex> lk(g_dev_mutex);
   for (int d = 0; d < kMaxDevices; ++d) {
     if (g_pool[d]) SSA_CUDA_TRY(cudaMemPoolTrimTo(g_pool[d], 0));
+  }
+  return SSA_OK;
+}
+
+ssa_status ssa_finalize_sums(int64_t n_traj, int32_t n_grid, int32_t n_species, const int64_t* sum1,
+                             const int64_t* sum2, double* mean, double* var) {
+  g_last_error.clear();
+  if (n_traj < 1) return fail(SSA_EINVAL, "n_traj must be >= 1 (got %lld)", (long long)n_traj);
+  if (n_grid < 1 || n_species < 1) return fail(SSA_EINVAL, "n_grid and n_species must be >= 1");
+  if (!sum1 || !sum2 || !mean || !var) return fail(SSA_EINVAL, "sum1, sum2, mean and var must not be NULL");
+  const size_t n = (size_t)n_grid * (size_t)n_species;
+  const double dN = (double)n_traj;
+  const double den = dN * (double)(n_traj - 1);
+  for (size_t q = 0; q < n; ++q) {
+    mean[q] = (double)sum1[q] / dN;
+    if (n_traj < 2) {
+      var[q] = std::numeric_limits<double>::quiet_NaN();
+    } else {
+      // N sum2 - sum1^2 in 128 bits, one rounding to double, one division
+      const __int128 num = (__int128)n_traj * (__int128)sum2[q] - (__int128)sum1[q] * (__int128)sum1[q];
+      var[q] = (double)num / den;
+    }
   }
   return SSA_OK;
 }

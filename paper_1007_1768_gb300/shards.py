@@ -22,19 +22,16 @@ def shard_range(n_traj: int, rank: int, world: int):
 
 
 def finalize_sums(sum1, sum2, n_traj: int):
-    """mean = sum1 / N and var = (N sum2 - sum1^2) / (N (N - 1)) from int64 sums,
-    with the numerator formed exactly (Python integers) and rounded once --
-    the same values the library's finalisation kernel writes."""
-    s1 = np.asarray(sum1, dtype=np.int64)
-    s2 = np.asarray(sum2, dtype=np.int64)
-    mean = s1.astype(np.float64) / float(n_traj)
+    """mean = sum1 / N and var = (N sum2 - sum1^2) / (N (N - 1)) from int64 sums
+    added across shards: libssa's ssa_finalize_sums (exact 128-bit numerator,
+    one rounding), the same values the device finalisation writes."""
+    from . import binding
+    s1 = np.ascontiguousarray(sum1, dtype=np.int64)
+    s2 = np.ascontiguousarray(sum2, dtype=np.int64)
+    if s1.shape != s2.shape or s1.ndim != 2:
+        raise ValueError("sum1 and sum2 must be [n_grid, n_species] arrays of one shape")
+    mean = np.empty(s1.shape, dtype=np.float64)
     var = np.empty(s1.shape, dtype=np.float64)
-    if n_traj < 2:
-        var[...] = np.nan
-        return mean, var
-    den = float(n_traj) * float(n_traj - 1)
-    flat1, flat2, out = s1.ravel(), s2.ravel(), var.ravel()
-    for q in range(flat1.size):
-        a, b = int(flat1[q]), int(flat2[q])
-        out[q] = float(n_traj * b - a * a) / den
+    binding._check(binding.lib().ssa_finalize_sums(int(n_traj), s1.shape[0], s1.shape[1], s1.ctypes.data,
+                                                   s2.ctypes.data, mean.ctypes.data, var.ctypes.data))
     return mean, var

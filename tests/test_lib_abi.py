@@ -191,3 +191,35 @@ def test_rate_modifier_arguments_are_checked_before_touching_the_gpu():
     assert e.value.status == binding.SSA_EUNSUPPORTED
     m.set_rate_modifier(0, -1, 0.0, 0.0, 0.0)  # removed again
     m.close()
+
+
+def test_finalize_sums_on_the_host_equals_the_oracle():
+    """ssa_finalize_sums (host, no GPU) against the oracle's finalisation,
+    bit for bit, on sums of real ensembles and on hand-built extremes (sums
+    whose 128-bit numerator needs more than 64 bits, N = 1 and N = 2)."""
+    import oracle
+    import workloads as W
+    from paper_1007_1768_gb300.shards import finalize_sums
+    r = oracle.run(W.hiv_shaped(), 301, 30.0, 101, 9)
+    for n, s1, s2 in [(301, r.S1, r.S2)]:
+        mean, var = finalize_sums(s1, s2, n)
+        om, ov = oracle.finalize(n, s1, s2)
+        assert np.array_equal(mean.view(np.int64), om.view(np.int64))
+        assert np.array_equal(var.view(np.int64), ov.view(np.int64))
+    rng = np.random.default_rng(5)
+    n = 3_000_000_000  # N * sum2 needs about 125 bits
+    x = rng.integers(0, 2**31 - 1, size=(7, 3), dtype=np.int64)
+    s1 = x * 40
+    s2 = (x // 2**16) * (x // 2**16) * 2**20 + rng.integers(0, 2**40, size=(7, 3), dtype=np.int64)
+    for nn in (n, 2, 1):
+        mean, var = finalize_sums(s1, s2, nn)
+        om, ov = oracle.finalize(nn, s1, s2)
+        assert np.array_equal(mean.view(np.int64), om.view(np.int64))
+        assert np.array_equal(np.isnan(var), np.isnan(ov))
+        assert np.array_equal(var[~np.isnan(var)].view(np.int64), ov[~np.isnan(ov)].view(np.int64))
+    L = ssa.lib()
+    d = np.zeros((2, 2))
+    z = np.zeros((2, 2), dtype=np.int64)
+    assert L.ssa_finalize_sums(0, 2, 2, z.ctypes.data, z.ctypes.data, d.ctypes.data, d.ctypes.data) == \
+        binding.SSA_EINVAL
+    assert L.ssa_finalize_sums(5, 2, 2, None, z.ctypes.data, d.ctypes.data, d.ctypes.data) == binding.SSA_EINVAL
