@@ -37,9 +37,10 @@ class SSAEnsembleFunction(torch.autograd.Function):
         n_traj, t_end, n_grid, seed, device, opt_kw = ctx.call
         if grad_mean is None:
             grad_mean = torch.zeros_like(mean)
+        # the model stays open until the graph is freed (Model.__del__), so a
+        # second backward through a retained graph replays it again
         g, se, _ = _b.ensemble_grad(ctx.model, n_traj, t_end, n_grid, seed, grad_mean.contiguous(), mean,
                                     device=device, traj_events=ctx.traj_events, **opt_kw)
-        ctx.model.close()
         dev, dt = ctx.rates_meta
         SSAEnsembleFunction.last_standard_error = se.to(dev, dt)
         return g.to(dev, dt), None, None, None, None, None, None, None, None, None
