@@ -35,16 +35,13 @@
 // were measured slower: with them the integer ALU pipe, not the FP64 unit,
 // bounds a full GPU.)  Two per-warp regimes give the same bits:
 //   * one trajectory per lane;
-//   * cooperative (at most 4 trajectories left and no new work): the warp
-//     splits into groups of 8 lanes, one trajectory per group, and runs it in
-//     batches of 8 events.  The lanes of a group share the propensity
-//     products; the prefix chain, selection and update run replicated and
-//     back to back for the 8 events, with nothing else on that chain.  Once
-//     per batch, lane b forms the random numbers and the waiting time of
-//     event b, the group forms the 8 event times in order and finds where
-//     the trajectory ends (later events of the batch are undone), and lane b
-//     does event b's grid index, difference sums and log records.  This cuts
-//     the cycles per event of the long trajectories that end the run.
+//   * cooperative (at most 4 trajectories left and no new work): groups of
+//     8, 16 or 32 lanes run one trajectory each in batches of speculative
+//     rounds -- every lane evaluates the next selection from the state a
+//     path of likely reactions would reach, so one prefix chain fires
+//     several events -- then settle the batch's times, grid sums and records
+//     lane-parallel (described at coop_run below).  This cuts the latency per
+//     event of the long trajectories that end the run.
 #ifndef SSA_THREAD_KERNEL_CUH_
 #define SSA_THREAD_KERNEL_CUH_
 
@@ -66,7 +63,6 @@ constexpr unsigned long long kFnvOffset = 0xcbf29ce484222325ULL;
 constexpr unsigned long long kFnvPrime = 0x100000001b3ULL;
 constexpr long long kStateMax = 2147483647LL;
 constexpr unsigned kFullMask = 0xFFFFFFFFu;
-constexpr int kCoopGroup = 8;      // lanes per trajectory in cooperative mode
 constexpr int kCoopMaxTraj = 4;    // trajectories per warp in cooperative mode
 
 // x[s] for a runtime species index s < MAXS (select chain over registers).
@@ -265,6 +261,7 @@ struct StepEnv {
   const uint64_t* s_lnf;
   const int32_t* s_nu;
   const uint32_t* s_depmask;
+  const uint32_t* s_rmask;      // per species: the reactions whose propensity reads it
   unsigned long long* d1;
   unsigned long long* d2;
 };
@@ -444,188 +441,370 @@ __device__ __forceinline__ T shfl_all(T v, int src, int width = 32) {
   return __shfl_sync(kFullMask, v, src, width);
 }
 
-// Cooperative mode for the (at most 4) trajectories left in a warp when no
-// new work remains.  All 32 lanes enter together.  Group g (lanes 8g..8g+7)
-// takes the g-th remaining trajectory: its state is copied to every lane of
-// the group, which then runs it event by event with the work split as
-// described at the top of this file.
+// ---------------------------------------------------------------------------
+// Cooperative mode: speculative batches.
+//
+// When at most 4 trajectories are left in a warp and no new work remains, the
+// warp splits into groups of L lanes (L = 8 for 3 or 4 trajectories, 16 for
+// 2, 32 for 1; the warp regroups as trajectories end), one trajectory per
+// group.  A group runs its trajectory in batches of L events; lane b holds
+// the random numbers of event base + b of the batch.
+//
+// The events of a batch are selected in rounds.  In a round every lane of the
+// group takes one node of a heap-ordered tree: node 0 is the trajectory's
+// current state X; the children of node v are 2v + 1 and 2v + 2, reached by
+// firing H1 and H2, the two reactions with the largest propensities at the
+// start of the batch; the state of node v is X plus the net changes of the
+// reactions on its path.  Each lane recomputes, for its node's state, the
+// propensities the previous round changed, the left-to-right prefix sums and
+// the direct method's selection with the random number of the event at its
+// node's depth -- the same instructions in every lane, so a round costs one
+// prefix chain whatever the number of nodes.  A node is verified when its
+// parent selected the node's reaction and every ancestor is verified; the
+// deepest verified node w closes a path of depth(w) + 1 events, which the
+// round fires: each node on it made exactly the selection the plain loop
+// makes from the same state with the same random number.  Hypotheses decide
+// how many events a round fires, never which events.
+//
+// When the window is full (or an event would leave the int32 range) the batch
+// is settled: lane b forms event b's waiting time, the group forms the event
+// times in order and finds where the trajectory ends (past t_end, at
+// max_events or at an overflow: the later events are undone), and lane b does
+// event b's grid index, difference sums and log records, from the states
+// given by a scan of the batch's net changes.
+constexpr int kSpecMaxDepth = 5;  // node 31 of a 32-lane tree
+
+__device__ __forceinline__ int node_depth(int v) { return 31 - __clz(v + 1); }
+
+// The ancestor of node v at depth d (0 <= d <= depth(v)).
+__device__ __forceinline__ int node_ancestor(int v, int d) { return ((v + 1) >> (node_depth(v) - d)) - 1; }
+
+// Lanes per trajectory for n (<= 4) trajectories in a warp.
+__device__ __forceinline__ int spec_group_size(int n) { return n <= 1 ? 32 : (n <= 2 ? 16 : 8); }
+
+// The bits of a warp ballot that belong to the group starting at lane gbase.
+__device__ __forceinline__ unsigned group_bits(unsigned ballot, int gbase, int L) {
+  return L == 32 ? ballot : (ballot >> gbase) & ((1u << L) - 1u);
+}
+
+// Prefix sum j (left to right) from the propensities, given prefix j - 1.
+template <int J, int MAXM, int MAXS>
+__device__ __forceinline__ void prefix_at(int M, Traj<MAXM, MAXS>& q) {
+  if constexpr (J == 0) {
+    q.pre[0] = __longlong_as_double((long long)q.av[0]);
+  } else if constexpr (J < MAXM) {
+    const double s = __dadd_rn(q.pre[J - 1], __longlong_as_double((long long)q.av[J]));
+    q.pre[J] = (M == MAXM || J < M) ? s : q.pre[J - 1];
+  }
+}
+
+// Prefix sums and a0 when the propensities below `lo` (warp-uniform) are
+// unchanged: the prefixes below lo are reused bit for bit and the chain
+// restarts at lo (a jump into the unrolled chain).
+template <int MAXM, int MAXS>
+__device__ __forceinline__ double prefix_sums_from(int M, Traj<MAXM, MAXS>& q, int lo) {
+  switch (lo) {
+    case 0: prefix_at<0>(M, q); [[fallthrough]];
+    case 1: prefix_at<1>(M, q); [[fallthrough]];
+    case 2: prefix_at<2>(M, q); [[fallthrough]];
+    case 3: prefix_at<3>(M, q); [[fallthrough]];
+    case 4: prefix_at<4>(M, q); [[fallthrough]];
+    case 5: prefix_at<5>(M, q); [[fallthrough]];
+    case 6: prefix_at<6>(M, q); [[fallthrough]];
+    case 7: prefix_at<7>(M, q); [[fallthrough]];
+    case 8: prefix_at<8>(M, q); [[fallthrough]];
+    case 9: prefix_at<9>(M, q); [[fallthrough]];
+    case 10: prefix_at<10>(M, q); [[fallthrough]];
+    case 11: prefix_at<11>(M, q); [[fallthrough]];
+    case 12: prefix_at<12>(M, q); [[fallthrough]];
+    case 13: prefix_at<13>(M, q); [[fallthrough]];
+    case 14: prefix_at<14>(M, q); [[fallthrough]];
+    case 15: prefix_at<15>(M, q); [[fallthrough]];
+    default: break;
+  }
+  return q.pre[MAXM - 1];
+}
+
+// Direct-method selection: the first j with prefix_j > target (prefixes are
+// non-decreasing), else the last j with a_j > 0.
+template <int MAXM, int MAXS>
+__device__ __forceinline__ int select_reaction(int M, const Traj<MAXM, MAXS>& q, long long gb) {
+  int cnt = 0;
+#pragma unroll
+  for (int j = 0; j < MAXM; ++j) {
+    if (j < M) cnt += (obits(q.pre[j]) <= gb) ? 1 : 0;
+  }
+  int jsel = cnt;
+  if (cnt >= M) {
+    jsel = 0;
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) {
+      if (j < M && q.av[j] != 0ULL) jsel = j;
+    }
+  }
+  return jsel;
+}
+
 template <bool LOG, int MAXM, int MAXS>
 __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Traj<MAXM, MAXS>& q, unsigned act,
                                          unsigned long long* blk, const EventLog& lg, ThreadLog& tl) {
   const int lane = threadIdx.x & 31;
-  const int grp = lane / kCoopGroup;
-  const int gl = lane % kCoopGroup;
-  // owner lane of this group's trajectory: the grp-th set bit of act
-  unsigned m = act;
-  int owner = -1;
-#pragma unroll
-  for (int r = 0; r < kCoopMaxTraj; ++r) {
-    const int b = __ffs(m) - 1;
-    if (r == grp) owner = b;
-    if (b >= 0) m &= m - 1;
-  }
-  const bool gactive = owner >= 0;
-  const int src = gactive ? owner : lane;
-  // replicate the owner's state in the group
+  int L = 0, gl = 0;
+  int gbase = 0;
+  int P[MAXS], up[MAXS];  // net change along this lane's path and its largest rise, per species
+  bool path_ok = false;   // every reaction on the path exists
+  int H1 = -2, H2 = -2;   // hypotheses (-2: not chosen since the last regrouping)
+  uint32_t dirty = 0u;    // propensities this lane must recompute
+  bool entry = true;
+  unsigned owners = act;  // one lane per live trajectory
 #pragma unroll
   for (int s = 0; s < MAXS; ++s) {
-    q.x[s] = shfl_all(q.x[s], src);
-    q.pv[s] = shfl_all(q.pv[s], src);
-  }
-  q.li = shfl_all(q.li, src);
-  q.traj_id = shfl_all(q.traj_id, src);
-  q.t = shfl_all(q.t, src);
-  q.n = shfl_all(q.n, src);
-  q.k = shfl_all(q.k, src);
-  q.hash = shfl_all(q.hash, src);
-  q.maxx = shfl_all(q.maxx, src);
-  // a group without a trajectory carries no pending event (its lanes may
-  // hold the stale state of a trajectory now run by another group)
-  q.pend = (shfl_all((int)q.pend, src) != 0) && gactive;
-  q.pend_over = shfl_all((int)q.pend_over, src) != 0;
-  q.pend_j = shfl_all(q.pend_j, src);
-  q.pend_E = shfl_all(q.pend_E, src);
-  q.pend_a0 = shfl_all(q.pend_a0, src);
-  q.have = gactive;
-  q.dirty = (1u << MAXM) - 1u;  // recompute every propensity from the copied state
-  // this lane's propensity slots: j = gl + 8 i
-  constexpr int kSlots = (MAXM + kCoopGroup - 1) / kCoopGroup;
-  unsigned long long mine[kSlots];
-  int32_t mine_w[kSlots];
-  unsigned long long mine_c[kSlots];
-#pragma unroll
-  for (int i = 0; i < kSlots; ++i) {
-    mine[i] = 0ULL;
-    // the reaction index depends on the lane: pick its tables with selects
-    // over the constant indices (no dynamic indexing of the parameters)
-    mine_w[i] = 0;
-    mine_c[i] = 0ULL;
-#pragma unroll
-    for (int jj = 0; jj < MAXM; ++jj) {
-      if (jj / kCoopGroup == i) {
-        mine_w[i] = (jj % kCoopGroup == gl) ? a.sm.rinfo[jj] : mine_w[i];
-        mine_c[i] = (jj % kCoopGroup == gl) ? a.sm.cbits[jj] : mine_c[i];
-      }
-    }
-  }
-  // the pending event carried over from thread mode
-  {
-    const double tau = quotient(q.pend_E, q.pend_a0);
-    const bool done = settle<LOG>(a, e, q, tau, gl == 0, lg, tl) && q.have;
-    if (done) {
-      if (gl == 0) finish_trajectory(a, q, blk);
-      q.have = false;
-    }
-    q.pend = false;
+    P[s] = 0;
+    up[s] = 0;
   }
 
-  // Batches of kCoopGroup events.  The draws run back to back (selection and
-  // state update only); lane b keeps what event base + b needs afterwards
-  // (a0, the reaction, the state before it).  Then the waiting times (one
-  // quotient per lane), the event times in order, the end of the trajectory
-  // (past t_end, overflow or max_events: later events of the batch are
-  // undone) and the bookkeeping of the kept events (lane b: grid index,
-  // difference sums, log records, largest count).  Every group of a warp
-  // runs every step, so the shuffles see all 32 lanes.
-  while (__any_sync(kFullMask, q.have)) {
+  for (;;) {
+    const int nlive = __popc(owners);
+    if (nlive == 0) break;
+    // (re)grouping: at entry, and when the live trajectories fit larger groups
+    const int Lw = spec_group_size(nlive);
+    if (Lw != L) {
+      L = Lw;
+      gl = lane & (L - 1);
+      gbase = lane & ~(L - 1);
+      const int grp = lane / L;
+      unsigned m = owners;
+      int owner = -1;  // the grp-th live trajectory's lane
+#pragma unroll
+      for (int r = 0; r < kCoopMaxTraj; ++r) {
+        const int b = __ffs((int)m) - 1;
+        if (r == grp) owner = b;
+        if (b >= 0) m &= m - 1;
+      }
+      const bool gactive = owner >= 0;
+      const int src = gactive ? owner : lane;
+#pragma unroll
+      for (int s = 0; s < MAXS; ++s) q.x[s] = shfl_all(q.x[s], src);
+      q.li = shfl_all(q.li, src);
+      q.traj_id = shfl_all(q.traj_id, src);
+      q.t = shfl_all(q.t, src);
+      q.n = shfl_all(q.n, src);
+      q.k = shfl_all(q.k, src);
+      q.hash = shfl_all(q.hash, src);
+      q.maxx = shfl_all(q.maxx, src);
+      q.have = gactive;
+      H1 = H2 = -2;
+      if (entry) {
+        // the event drawn and applied in thread mode, not yet settled: a
+        // group without a trajectory carries none
+#pragma unroll
+        for (int s = 0; s < MAXS; ++s) q.pv[s] = shfl_all(q.pv[s], src);
+        q.pend = (shfl_all((int)q.pend, src) != 0) && gactive;
+        q.pend_over = shfl_all((int)q.pend_over, src) != 0;
+        q.pend_j = shfl_all(q.pend_j, src);
+        q.pend_E = shfl_all(q.pend_E, src);
+        q.pend_a0 = shfl_all(q.pend_a0, src);
+        const double tau = quotient(q.pend_E, q.pend_a0);
+        const bool done = settle<LOG>(a, e, q, tau, gl == 0, lg, tl) && q.have;
+        if (done) {
+          if (gl == 0) finish_trajectory(a, q, blk);
+          q.have = false;
+        }
+        q.pend = false;
+        entry = false;
+      }
+    }
+    if (!__any_sync(kFullMask, q.have)) break;
+
     const uint32_t base = q.n;
     const EventRandom rr = event_random(base + (uint32_t)gl, q.traj_id, e.sid, e.key0, e.key1, e.s_inv, e.s_lnf);
-    bool alive = q.have;  // the batch's events so far were applied
-    int nb = kCoopGroup;  // index of the first event that would overflow, else kCoopGroup
-    double my_a0 = 0.0;
-    int my_j = 0;
-#pragma unroll 1
-    for (int b = 0; b < kCoopGroup; ++b) {
-      // propensities: lane gl computes j = gl + 8 i when dirty
-#pragma unroll
-      for (int i = 0; i < kSlots; ++i) {
-        const int j = gl + kCoopGroup * i;
-        if (j < e.M && ((q.dirty >> j) & 1u))
-          mine[i] = propensity_fp64(mine_c[i], mass_action_h<MAXS>(mine_w[i], q.x));
-      }
-      // the changed ones into every lane of the group: one shuffle per
-      // reaction that any group of the warp recomputed
-      for (unsigned dm = __reduce_or_sync(kFullMask, q.dirty); dm != 0u; dm &= dm - 1u) {
-        const int j = __ffs((int)dm) - 1;
-        const unsigned long long v = shfl_all(j < kCoopGroup ? mine[0] : mine[kSlots - 1], j % kCoopGroup,
-                                              kCoopGroup);
-        const bool mine_changed = (q.dirty >> j) & 1u;
-#pragma unroll
-        for (int jj = 0; jj < MAXM; ++jj) q.av[jj] = (jj == j && mine_changed) ? v : q.av[jj];
-      }
-      const double a0 = prefix_sums(e.M, q);
-      const unsigned long long u2 = shfl_all(rr.u2, b, kCoopGroup);
-      const long long gb = obits(__dmul_rn(__longlong_as_double((long long)u2), a0));
-      // first j with prefix_j > target, else the last j with a_j > 0
-      int cnt = 0;
+    const int dep = node_depth(gl);
+    // hypotheses: the two largest propensities of the root lane (as left by
+    // the last round), as an unordered pair so that swaps keep the tree
+    {
+      unsigned long long b1 = 0ULL, b2 = 0ULL;
+      int i1 = -1, i2 = -1;
 #pragma unroll
       for (int j = 0; j < MAXM; ++j) {
-        if (j < e.M) cnt += (obits(q.pre[j]) <= gb) ? 1 : 0;
-      }
-      int jsel = cnt;
-      if (cnt >= e.M) {
-        jsel = 0;
-#pragma unroll
-        for (int j = 0; j < MAXM; ++j) {
-          if (j < e.M && q.av[j] != 0ULL) jsel = j;
+        if (j < e.M) {
+          const unsigned long long v = q.av[j];
+          const bool top = v > b1;
+          const bool second = !top && v > b2;
+          b2 = top ? b1 : (second ? v : b2);
+          i2 = top ? i1 : (second ? j : i2);
+          b1 = top ? v : b1;
+          i1 = top ? j : i1;
         }
       }
-      const int* row = e.s_nu + jsel * MAXS;
-      int rv[MAXS];
+      int h1 = (i2 < 0) ? i1 : min(i1, i2);
+      int h2 = (i2 < 0) ? -1 : max(i1, i2);
+      h1 = __shfl_sync(kFullMask, h1, 0, L);
+      h2 = __shfl_sync(kFullMask, h2, 0, L);
+      if (h1 != H1 || h2 != H2) {
+        H1 = h1;
+        H2 = h2;
+        int cum[MAXS];
+#pragma unroll
+        for (int s = 0; s < MAXS; ++s) {
+          cum[s] = 0;
+          up[s] = 0;
+        }
+        path_ok = true;
+#pragma unroll
+        for (int d = 1; d <= kSpecMaxDepth; ++d) {
+          if (d <= dep) {
+            const int anc = node_ancestor(gl, d);
+            const int hyp = (anc & 1) ? H1 : H2;
+            path_ok = path_ok && hyp >= 0;
+            const int* row = e.s_nu + max(hyp, 0) * MAXS;
+#pragma unroll
+            for (int s = 0; s < MAXS; ++s) {
+              cum[s] += row[s];
+              up[s] = max(up[s], cum[s]);
+            }
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < MAXS; ++s) P[s] = cum[s];
+        dirty = (1u << MAXM) - 1u;
+      }
+    }
+
+    // ---- rounds until the window of L events is full
+    int nres = 0;  // events of the batch drawn so far (group-uniform)
+    int nb = L;    // index of an event that would overflow (not applied), else L
+    double my_a0 = 0.0;
+    int my_j = 0;
+    bool run = q.have;
+    const int par = max((gl - 1) >> 1, 0);
+    const int hyp_me = (gl & 1) ? H1 : H2;
+    while (__any_sync(kFullMask, run)) {
+      int xl[MAXS];
+      bool safe = path_ok;
+#pragma unroll
+      for (int s = 0; s < MAXS; ++s) {
+        xl[s] = q.x[s] + P[s];
+        safe = safe && (long long)q.x[s] + up[s] <= kStateMax;
+      }
+#pragma unroll
+      for (int j = 0; j < MAXM; ++j) {
+        if (run && j < e.M && ((dirty >> j) & 1u))
+          q.av[j] = propensity_fp64(a.sm.cbits[j], mass_action_h<MAXS>(a.sm.rinfo[j], xl));
+      }
+      const int lo = __reduce_min_sync(kFullMask, (run && dirty != 0u) ? (__ffs((int)dirty) - 1) : MAXM);
+      const double a0 = prefix_sums_from(e.M, q, lo);
+      if (run) dirty = 0u;
+      const int ei = nres + dep;  // this node's event within the batch
+      const bool inwin = ei < L;
+      const unsigned long long u2 = __shfl_sync(kFullMask, rr.u2, min(ei, L - 1), L);
+      const long long gb = obits(__dmul_rn(__longlong_as_double((long long)u2), a0));
+      const int jsel = select_reaction(e.M, q, gb);
+      // verification
+      const int jp = __shfl_sync(kFullMask, jsel, par, L);
+      const bool cons = (gl == 0) || (jp == hyp_me && safe && inwin);
+      const unsigned C = group_bits(__ballot_sync(kFullMask, cons), gbase, L);
+      bool ver = run;
+      int v = gl;
+#pragma unroll
+      for (int i = 0; i < kSpecMaxDepth; ++i) {
+        if (v > 0) {
+          ver = ver && ((C >> v) & 1u);
+          v = (v - 1) >> 1;
+        }
+      }
+      const unsigned V = group_bits(__ballot_sync(kFullMask, ver), gbase, L);
+      const int w = 31 - __clz((int)(V | 1u));  // deepest verified node
+      const int dw = node_depth(w);
+      // lane nres + d records the event of the path's node at depth d
+      const int d = gl - nres;
+      const bool rec = run && d >= 0 && d <= dw;
+      const int src = rec ? node_ancestor(w, d) : gl;
+      const double a0_s = __shfl_sync(kFullMask, a0, src, L);
+      const int j_s = __shfl_sync(kFullMask, jsel, src, L);
+      if (rec) {
+        my_a0 = a0_s;
+        my_j = j_s;
+      }
+      // the new state: node w's state and its selection (not applied if it
+      // would leave the int32 range)
+      const int jw = __shfl_sync(kFullMask, jsel, w, L);
+      const int* roww = e.s_nu + jw * MAXS;
+      int xw[MAXS];
       bool over = false;
 #pragma unroll
       for (int s = 0; s < MAXS; ++s) {
-        rv[s] = row[s];
-        over |= (long long)q.x[s] + (long long)rv[s] > kStateMax;
+        xw[s] = __shfl_sync(kFullMask, xl[s], w, L);
+        over = over || (long long)xw[s] + roww[s] > kStateMax;
       }
-      if (gl == b) {
-        my_a0 = a0;
-        my_j = jsel;
-      }
-      const bool apply = alive && !over;
-      if (alive && over) nb = b;
+      if (run) {
+        uint32_t dm = 0u;
 #pragma unroll
-      for (int s = 0; s < MAXS; ++s) q.x[s] += apply ? rv[s] : 0;
-      q.dirty = apply ? e.s_depmask[jsel] : 0u;
-      alive = apply;
+        for (int s = 0; s < MAXS; ++s) {
+          const int xn = over ? xw[s] : xw[s] + roww[s];
+          dm |= (xn != q.x[s]) ? e.s_rmask[s] : 0u;
+          q.x[s] = xn;
+        }
+        dirty = dm;
+        if (over) nb = nres + dw;
+        nres += dw + 1;
+        run = !over && nres < L;
+      }
     }
 
-    // waiting times (lane b: event base + b), then the times in order
-    const double my_tau = quotient(rr.E, my_a0);
+    // ---- settle the batch: lane b < nres holds event base + b
+    const bool mine = gl < nres;
+    const double my_tau = quotient(rr.E, mine ? my_a0 : 1.0);
+    const int* myrow = e.s_nu + my_j * MAXS;
+    int cum[MAXS];  // net change of the batch's applied events up to this lane's (inclusive scan)
+#pragma unroll
+    for (int s = 0; s < MAXS; ++s) cum[s] = (mine && gl != nb) ? myrow[s] : 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      if (off < L) {
+#pragma unroll
+        for (int s = 0; s < MAXS; ++s) {
+          const int u = __shfl_up_sync(kFullMask, cum[s], off, L);
+          cum[s] += (gl >= off) ? u : 0;
+        }
+      }
+    }
+    // the event times in order, the end of the trajectory, the hash
     double tt = q.t;
     unsigned long long h = q.hash;
     int K = 0;      // events kept
     int endf = -1;  // the trajectory ends: 0 past t_end, 1 max_events, 2 overflow
     long long my_tb = 0;
-    int jb[kCoopGroup];
 #pragma unroll
-    for (int b = 0; b < kCoopGroup; ++b) {
-      const double tau_b = shfl_all(my_tau, b, kCoopGroup);
-      jb[b] = shfl_all(my_j, b, kCoopGroup);
-      const double t_b = __dadd_rn(tt, tau_b);
-      const long long tb_b = obits(t_b);
-      if (gl == b) my_tb = tb_b;
-      if (endf < 0) {
-        if (tb_b > e.t_end_bits) {
-          endf = 0;
-        } else if (b == nb) {
-          endf = 2;
-        } else {
-          K = b + 1;
-          tt = t_b;
-          const unsigned long long h1 = (h ^ (unsigned long long)jb[b]) * kFnvPrime;
-          h = (h1 ^ (unsigned long long)tb_b) * kFnvPrime;
-          if ((long long)base + K == a.max_events) endf = 1;
+    for (int b = 0; b < 32; ++b) {
+      if (b < L) {
+        const double tau_b = __shfl_sync(kFullMask, my_tau, b, L);
+        const int j_b = __shfl_sync(kFullMask, my_j, b, L);
+        if (endf < 0 && b < nres) {
+          const double t_b = __dadd_rn(tt, tau_b);
+          const long long tb_b = obits(t_b);
+          if (gl == b) my_tb = tb_b;
+          if (tb_b > e.t_end_bits) {
+            endf = 0;
+          } else if (b == nb) {
+            endf = 2;
+          } else {
+            K = b + 1;
+            tt = t_b;
+            const unsigned long long h1 = (h ^ (unsigned long long)j_b) * kFnvPrime;
+            h = (h1 ^ (unsigned long long)tb_b) * kFnvPrime;
+            if ((long long)base + K == a.max_events) endf = 1;
+          }
         }
       }
     }
-    // undo the applied events that were not kept
+    // states: at the start of the batch, and after the kept events
+    int xs[MAXS], xk[MAXS];
 #pragma unroll
-    for (int b = 0; b < kCoopGroup; ++b) {
-      const bool undo = b >= K && b < nb;
-      const int* row = e.s_nu + jb[b] * MAXS;
-#pragma unroll
-      for (int s = 0; s < MAXS; ++s) q.x[s] -= undo ? row[s] : 0;
+    for (int s = 0; s < MAXS; ++s) {
+      const int tot = __shfl_sync(kFullMask, cum[s], L - 1, L);
+      const int ck = __shfl_sync(kFullMask, cum[s], max(K - 1, 0), L);
+      xs[s] = q.x[s] - tot;
+      xk[s] = xs[s] + (K > 0 ? ck : 0);
     }
     // bookkeeping of the kept events, lane b for event base + b
     const bool mine_kept = q.have && gl < K;
@@ -633,23 +812,11 @@ __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Tra
     int mx = 0;
     if (mine_kept) {
       my_k = grid_index(a, my_tb, q.k);
-      // the state after this lane's event: the state after the kept events
-      // less the changes of the later kept ones
-      int xa[MAXS], pv[MAXS];
-#pragma unroll
-      for (int s = 0; s < MAXS; ++s) xa[s] = q.x[s];
-#pragma unroll
-      for (int b = 1; b < kCoopGroup; ++b) {
-        if (b > gl && b < K) {
-          const int* rowb = e.s_nu + jb[b] * MAXS;
-#pragma unroll
-          for (int s = 0; s < MAXS; ++s) xa[s] -= rowb[s];
-        }
-      }
-      const int* row = e.s_nu + my_j * MAXS;
+      int xa[MAXS], pv[MAXS];  // the state after this lane's event, and its change
 #pragma unroll
       for (int s = 0; s < MAXS; ++s) {
-        pv[s] = row[s];
+        xa[s] = xs[s] + cum[s];
+        pv[s] = myrow[s];
         if (pv[s] != 0) mx = max(mx, xa[s]);
         if (pv[s] != 0 && my_k < e.G) {
           const long long xo = (long long)xa[s] - pv[s];
@@ -660,20 +827,25 @@ __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Tra
       if constexpr (LOG) thread_log_event<MAXS>(lg, tl, my_tb, xa, pv);
     }
 #pragma unroll
-    for (int off = kCoopGroup / 2; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(kFullMask, mx, off, kCoopGroup));
-    const int k_last = shfl_all(my_k, K > 0 ? K - 1 : 0, kCoopGroup);
+    for (int off = 16; off > 0; off >>= 1) {
+      if (off < L) mx = max(mx, __shfl_xor_sync(kFullMask, mx, off, L));
+    }
+    const int k_last = __shfl_sync(kFullMask, my_k, K > 0 ? K - 1 : 0, L);
     if (q.have) {
       q.maxx = max(q.maxx, mx);
       if (K > 0) q.k = k_last;
       q.t = tt;
       q.n = base + (uint32_t)K;
       q.hash = h;
+#pragma unroll
+      for (int s = 0; s < MAXS; ++s) q.x[s] = xk[s];
       if (endf >= 0) {
         q.flags = (endf == 1) ? 1 : ((endf == 2) ? 2 : 0);
         if (gl == 0) finish_trajectory(a, q, blk);
         q.have = false;
       }
     }
+    owners = __ballot_sync(kFullMask, q.have && gl == 0);
   }
 }
 
@@ -687,6 +859,7 @@ __global__ void __launch_bounds__(512, 1) k_ssa_thread(const RunArgs a, const Ev
   uint64_t* s_lnf = reinterpret_cast<uint64_t*>(smem + L.log_lnf);
   int32_t* s_nu = reinterpret_cast<int32_t*>(smem + L.nu);
   uint32_t* s_depmask = reinterpret_cast<uint32_t*>(smem + L.depmask);
+  uint32_t* s_rmask = reinterpret_cast<uint32_t*>(smem + L.rmask);
   unsigned long long* d1 = SHARED_D ? reinterpret_cast<unsigned long long*>(smem + L.d1) : a.D1;
   unsigned long long* d2 = SHARED_D ? reinterpret_cast<unsigned long long*>(smem + L.d2) : a.D2;
 
@@ -699,6 +872,16 @@ __global__ void __launch_bounds__(512, 1) k_ssa_thread(const RunArgs a, const Ev
     s_nu[i] = (j < M && s < S) ? a.sm.nu[j * kSmallMax + s] : 0;
   }
   for (int j = tid; j < MAXM; j += T) s_depmask[j] = (j < M) ? a.sm.depmask[j] : 0u;
+  for (int s = tid; s < MAXS; s += T) {
+    uint32_t m = 0u;
+    for (int j = 0; j < M; ++j) {
+      const int32_t w = a.sm.rinfo[j];
+      const int kind = rinfo_kind(w);
+      const bool reads = (kind != kOrder0 && rinfo_a(w) == s) || (kind == kBi && rinfo_b(w) == s);
+      m |= reads ? (1u << j) : 0u;
+    }
+    s_rmask[s] = m;
+  }
   if (SHARED_D) {
     for (int i = tid; i < G * S; i += T) {
       d1[i] = 0ULL;
@@ -720,6 +903,7 @@ __global__ void __launch_bounds__(512, 1) k_ssa_thread(const RunArgs a, const Ev
   e.s_lnf = s_lnf;
   e.s_nu = s_nu;
   e.s_depmask = s_depmask;
+  e.s_rmask = s_rmask;
   e.d1 = d1;
   e.d2 = d2;
 
