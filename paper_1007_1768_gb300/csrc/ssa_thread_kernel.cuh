@@ -102,11 +102,15 @@ __device__ __forceinline__ bool propensity_int(unsigned long long cbits, long lo
   return ok && (unsigned long long)h < (1ULL << 53);
 }
 
+// (double)h for h outside [0, 2^53) (counts far beyond any seen in practice).
+// Kept out of line: as a select operand the conversion would be issued for
+// every product.
+__device__ __noinline__ double ll2double_rare(long long h) { return __ll2double_rn(h); }
+
 // a_j = RN(c_j * h) as bits with the hardware multiply.
 __device__ __forceinline__ unsigned long long propensity_fp64(unsigned long long cbits, long long h) {
-  const double hd = ((unsigned long long)h < (1ULL << 53))
-                        ? __longlong_as_double((long long)small_int_to_f64_bits((unsigned long long)h))
-                        : __ll2double_rn(h);
+  double hd = __longlong_as_double((long long)small_int_to_f64_bits((unsigned long long)h));
+  if (__builtin_expect((unsigned long long)h >= (1ULL << 53), 0)) hd = ll2double_rare(h);
   return (unsigned long long)obits(__dmul_rn(__longlong_as_double((long long)cbits), hd));
 }
 
@@ -291,14 +295,22 @@ __device__ __forceinline__ void start_trajectory(const RunArgs& a, const StepEnv
   q.pend_a0 = 0.0;
 }
 
+// The hardware division, for the rare operands the integer quotient does not
+// cover (a0 == 0 gives +inf: the state is absorbing).  Out of line and behind
+// a branch: as a select operand it would be issued (hundreds of cycles) for
+// every quotient.
+__device__ __noinline__ double quotient_rare(unsigned long long Eb, double a0) {
+  return __ddiv_rn(__longlong_as_double((long long)Eb), a0);
+}
+
 // tau = RN(E / a0) as a double: the exact integer quotient (branch-free, so
-// its instructions fill the stalls of the prefix chain it is issued with);
-// the hardware division for the rare operands it does not cover (a0 == 0
-// gives +inf: the state is absorbing).
+// its instructions fill the stalls of the prefix chain it is issued with).
 __device__ __forceinline__ double quotient(unsigned long long Eb, double a0) {
   bool ok;
   const unsigned long long qb = ssa_sf::div_pos(Eb, (unsigned long long)obits(a0), ok);
-  return ok ? __longlong_as_double((long long)qb) : __ddiv_rn(__longlong_as_double((long long)Eb), a0);
+  double q = __longlong_as_double((long long)qb);
+  if (__builtin_expect(!ok, 0)) q = quotient_rare(Eb, a0);
+  return q;
 }
 
 // Prefix sums and a0 from the propensities, left to right.
@@ -479,8 +491,9 @@ __device__ __forceinline__ int node_depth(int v) { return 31 - __clz(v + 1); }
 // The ancestor of node v at depth d (0 <= d <= depth(v)).
 __device__ __forceinline__ int node_ancestor(int v, int d) { return ((v + 1) >> (node_depth(v) - d)) - 1; }
 
-// Lanes per trajectory for n (<= 4) trajectories in a warp.
-__device__ __forceinline__ int spec_group_size(int n) { return n <= 1 ? 32 : (n <= 2 ? 16 : 8); }
+// Lanes per trajectory for n (1 <= n <= 16) trajectories in a warp: 32 / n
+// rounded down to a power of two.
+__device__ __forceinline__ int spec_group_size(int n) { return 32 >> (32 - __clz(n - 1)); }
 
 // The bits of a warp ballot that belong to the group starting at lane gbase.
 __device__ __forceinline__ unsigned group_bits(unsigned ballot, int gbase, int L) {
@@ -543,6 +556,117 @@ __device__ __forceinline__ int select_reaction(int M, const Traj<MAXM, MAXS>& q,
     }
   }
   return jsel;
+}
+
+// Settles a batch of the cooperative mode for groups of L lanes: lane b <
+// nres holds event base + b (its a0, reaction and random numbers), event nb
+// (if < L) would have left the int32 range and was not applied.  Lane b forms
+// event b's waiting time; the group forms the event times in order (one
+// unconditional FP64 chain, replicated in every lane: times only grow, so it
+// is right up to the first event that ends the trajectory) and the sequence
+// hash after every event; the first event past t_end or at the overflow, or
+// the max_events limit, ends the trajectory (later events are undone); lane b
+// does the grid index, difference sums and log records of its kept event from
+// the states given by a scan of the batch's net changes.
+template <int L, bool LOG, int MAXM, int MAXS>
+__device__ __forceinline__ void settle_batch(const RunArgs& a, const StepEnv& e, Traj<MAXM, MAXS>& q, int gl, int gbase,
+                                             uint32_t base, int nres, int nb, double my_a0, int my_j,
+                                             const EventRandom& rr, unsigned long long* blk, const EventLog& lg,
+                                             ThreadLog& tl) {
+  const bool mine = gl < nres;
+  const double my_tau = quotient(rr.E, mine ? my_a0 : 1.0);
+  const int* myrow = e.s_nu + my_j * MAXS;
+  int cum[MAXS];  // net change of the batch's applied events up to this lane's (inclusive scan)
+#pragma unroll
+  for (int s = 0; s < MAXS; ++s) cum[s] = (mine && gl != nb) ? myrow[s] : 0;
+#pragma unroll
+  for (int off = 1; off < L; off <<= 1) {
+#pragma unroll
+    for (int s = 0; s < MAXS; ++s) {
+      const int u = __shfl_up_sync(kFullMask, cum[s], off, L);
+      cum[s] += (gl >= off) ? u : 0;
+    }
+  }
+  // event times and prefix hashes in order; lane b keeps those after event b
+  double tt = q.t, my_t = q.t;
+  unsigned long long h = q.hash, my_h = q.hash;
+#pragma unroll 8
+  for (int b = 0; b < L; ++b) {
+    const double tau_b = __shfl_sync(kFullMask, my_tau, b, L);
+    const int j_b = __shfl_sync(kFullMask, my_j, b, L);
+    tt = __dadd_rn(tt, tau_b);
+    const unsigned long long h1 = (h ^ (unsigned long long)j_b) * kFnvPrime;
+    h = (h1 ^ (unsigned long long)obits(tt)) * kFnvPrime;
+    my_t = (gl == b) ? tt : my_t;
+    my_h = (gl == b) ? h : my_h;
+  }
+  const long long my_tb = obits(my_t);
+  // the first drawn event that is not kept: past t_end, or the overflowing one
+  const bool stop = mine && (my_tb > e.t_end_bits || gl == nb);
+  const unsigned stops = group_bits(__ballot_sync(kFullMask, stop), gbase, L);
+  const int K0 = stops ? (__ffs((int)stops) - 1) : nres;
+  const bool past_K0 = __shfl_sync(kFullMask, (int)(my_tb > e.t_end_bits), min(K0, L - 1), L) != 0;
+  const long long kmax = a.max_events - (long long)base;  // >= 1 for a live trajectory
+  int K;          // events kept
+  int endf = -1;  // the trajectory ends: 0 past t_end, 1 max_events, 2 overflow
+  if (kmax <= (long long)K0) {
+    K = (int)max(kmax, 0LL);
+    endf = 1;
+  } else {
+    K = K0;
+    if (K0 < nres) endf = past_K0 ? 0 : 2;
+  }
+  const int last = max(K - 1, 0);
+  const double t_last = __shfl_sync(kFullMask, my_t, last, L);
+  const unsigned long long h_last = __shfl_sync(kFullMask, my_h, last, L);
+  // states: at the start of the batch, and after the kept events
+  int xs[MAXS], xk[MAXS];
+#pragma unroll
+  for (int s = 0; s < MAXS; ++s) {
+    const int tot = __shfl_sync(kFullMask, cum[s], L - 1, L);
+    const int ck = __shfl_sync(kFullMask, cum[s], last, L);
+    xs[s] = q.x[s] - tot;
+    xk[s] = xs[s] + (K > 0 ? ck : 0);
+  }
+  // bookkeeping of the kept events, lane b for event base + b
+  const bool mine_kept = q.have && gl < K;
+  int my_k = q.k;
+  int mx = 0;
+  if (mine_kept) {
+    my_k = grid_index(a, my_tb, q.k);
+    int xa[MAXS], pv[MAXS];  // the state after this lane's event, and its change
+#pragma unroll
+    for (int s = 0; s < MAXS; ++s) {
+      xa[s] = xs[s] + cum[s];
+      pv[s] = myrow[s];
+      if (pv[s] != 0) mx = max(mx, xa[s]);
+      if (pv[s] != 0 && my_k >= 0 && my_k < e.G) {
+        const long long xo = (long long)xa[s] - pv[s];
+        atomicAdd(e.d1 + (size_t)my_k * e.S + s, (unsigned long long)(long long)pv[s]);
+        atomicAdd(e.d2 + (size_t)my_k * e.S + s, (unsigned long long)((2 * xo + pv[s]) * (long long)pv[s]));
+      }
+    }
+    if constexpr (LOG) thread_log_event<MAXS>(lg, tl, my_tb, xa, pv);
+  }
+#pragma unroll
+  for (int off = L / 2; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(kFullMask, mx, off, L));
+  const int k_last = __shfl_sync(kFullMask, my_k, last, L);
+  if (q.have) {
+    q.maxx = max(q.maxx, mx);
+    if (K > 0) {
+      q.k = k_last;
+      q.t = t_last;
+      q.hash = h_last;
+    }
+    q.n = base + (uint32_t)K;
+#pragma unroll
+    for (int s = 0; s < MAXS; ++s) q.x[s] = xk[s];
+    if (endf >= 0) {
+      q.flags = (endf == 1) ? 1 : ((endf == 2) ? 2 : 0);
+      if (gl == 0) finish_trajectory(a, q, blk);
+      q.have = false;
+    }
+  }
 }
 
 template <bool LOG, int MAXM, int MAXS>
@@ -686,10 +810,15 @@ __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Tra
         xl[s] = q.x[s] + P[s];
         safe = safe && (long long)q.x[s] + up[s] <= kStateMax;
       }
+      // products of the reactions any running lane must recompute (a
+      // warp-uniform branch per reaction skips the others entirely)
+      const uint32_t dany = __reduce_or_sync(kFullMask, run ? dirty : 0u);
 #pragma unroll
       for (int j = 0; j < MAXM; ++j) {
-        if (run && j < e.M && ((dirty >> j) & 1u))
-          q.av[j] = propensity_fp64(a.sm.cbits[j], mass_action_h<MAXS>(a.sm.rinfo[j], xl));
+        if ((dany >> j) & 1u) {
+          const unsigned long long pj = propensity_fp64(a.sm.cbits[j], mass_action_h<MAXS>(a.sm.rinfo[j], xl));
+          if (run && ((dirty >> j) & 1u)) q.av[j] = pj;
+        }
       }
       const int lo = __reduce_min_sync(kFullMask, (run && dirty != 0u) ? (__ffs((int)dirty) - 1) : MAXM);
       const double a0 = prefix_sums_from(e.M, q, lo);
@@ -751,99 +880,13 @@ __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Tra
       }
     }
 
-    // ---- settle the batch: lane b < nres holds event base + b
-    const bool mine = gl < nres;
-    const double my_tau = quotient(rr.E, mine ? my_a0 : 1.0);
-    const int* myrow = e.s_nu + my_j * MAXS;
-    int cum[MAXS];  // net change of the batch's applied events up to this lane's (inclusive scan)
-#pragma unroll
-    for (int s = 0; s < MAXS; ++s) cum[s] = (mine && gl != nb) ? myrow[s] : 0;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      if (off < L) {
-#pragma unroll
-        for (int s = 0; s < MAXS; ++s) {
-          const int u = __shfl_up_sync(kFullMask, cum[s], off, L);
-          cum[s] += (gl >= off) ? u : 0;
-        }
-      }
-    }
-    // the event times in order, the end of the trajectory, the hash
-    double tt = q.t;
-    unsigned long long h = q.hash;
-    int K = 0;      // events kept
-    int endf = -1;  // the trajectory ends: 0 past t_end, 1 max_events, 2 overflow
-    long long my_tb = 0;
-#pragma unroll
-    for (int b = 0; b < 32; ++b) {
-      if (b < L) {
-        const double tau_b = __shfl_sync(kFullMask, my_tau, b, L);
-        const int j_b = __shfl_sync(kFullMask, my_j, b, L);
-        if (endf < 0 && b < nres) {
-          const double t_b = __dadd_rn(tt, tau_b);
-          const long long tb_b = obits(t_b);
-          if (gl == b) my_tb = tb_b;
-          if (tb_b > e.t_end_bits) {
-            endf = 0;
-          } else if (b == nb) {
-            endf = 2;
-          } else {
-            K = b + 1;
-            tt = t_b;
-            const unsigned long long h1 = (h ^ (unsigned long long)j_b) * kFnvPrime;
-            h = (h1 ^ (unsigned long long)tb_b) * kFnvPrime;
-            if ((long long)base + K == a.max_events) endf = 1;
-          }
-        }
-      }
-    }
-    // states: at the start of the batch, and after the kept events
-    int xs[MAXS], xk[MAXS];
-#pragma unroll
-    for (int s = 0; s < MAXS; ++s) {
-      const int tot = __shfl_sync(kFullMask, cum[s], L - 1, L);
-      const int ck = __shfl_sync(kFullMask, cum[s], max(K - 1, 0), L);
-      xs[s] = q.x[s] - tot;
-      xk[s] = xs[s] + (K > 0 ? ck : 0);
-    }
-    // bookkeeping of the kept events, lane b for event base + b
-    const bool mine_kept = q.have && gl < K;
-    int my_k = q.k;
-    int mx = 0;
-    if (mine_kept) {
-      my_k = grid_index(a, my_tb, q.k);
-      int xa[MAXS], pv[MAXS];  // the state after this lane's event, and its change
-#pragma unroll
-      for (int s = 0; s < MAXS; ++s) {
-        xa[s] = xs[s] + cum[s];
-        pv[s] = myrow[s];
-        if (pv[s] != 0) mx = max(mx, xa[s]);
-        if (pv[s] != 0 && my_k < e.G) {
-          const long long xo = (long long)xa[s] - pv[s];
-          atomicAdd(e.d1 + (size_t)my_k * e.S + s, (unsigned long long)(long long)pv[s]);
-          atomicAdd(e.d2 + (size_t)my_k * e.S + s, (unsigned long long)((2 * xo + pv[s]) * (long long)pv[s]));
-        }
-      }
-      if constexpr (LOG) thread_log_event<MAXS>(lg, tl, my_tb, xa, pv);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      if (off < L) mx = max(mx, __shfl_xor_sync(kFullMask, mx, off, L));
-    }
-    const int k_last = __shfl_sync(kFullMask, my_k, K > 0 ? K - 1 : 0, L);
-    if (q.have) {
-      q.maxx = max(q.maxx, mx);
-      if (K > 0) q.k = k_last;
-      q.t = tt;
-      q.n = base + (uint32_t)K;
-      q.hash = h;
-#pragma unroll
-      for (int s = 0; s < MAXS; ++s) q.x[s] = xk[s];
-      if (endf >= 0) {
-        q.flags = (endf == 1) ? 1 : ((endf == 2) ? 2 : 0);
-        if (gl == 0) finish_trajectory(a, q, blk);
-        q.have = false;
-      }
+    // ---- settle the batch (loops unrolled for the group size)
+    switch (L) {
+      case 32: settle_batch<32, LOG>(a, e, q, gl, gbase, base, nres, nb, my_a0, my_j, rr, blk, lg, tl); break;
+      case 16: settle_batch<16, LOG>(a, e, q, gl, gbase, base, nres, nb, my_a0, my_j, rr, blk, lg, tl); break;
+      case 8: settle_batch<8, LOG>(a, e, q, gl, gbase, base, nres, nb, my_a0, my_j, rr, blk, lg, tl); break;
+      case 4: settle_batch<4, LOG>(a, e, q, gl, gbase, base, nres, nb, my_a0, my_j, rr, blk, lg, tl); break;
+      default: settle_batch<2, LOG>(a, e, q, gl, gbase, base, nres, nb, my_a0, my_j, rr, blk, lg, tl); break;
     }
     owners = __ballot_sync(kFullMask, q.have && gl == 0);
   }
