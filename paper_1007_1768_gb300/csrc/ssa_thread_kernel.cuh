@@ -35,8 +35,8 @@
 // were measured slower: with them the integer ALU pipe, not the FP64 unit,
 // bounds a full GPU.)  Two per-warp regimes give the same bits:
 //   * one trajectory per lane;
-//   * cooperative (at most 4 trajectories left and no new work): groups of
-//     8, 16 or 32 lanes run one trajectory each in batches of speculative
+//   * cooperative (at most 16 trajectories left and no new work): groups of
+//     2, 4, 8, 16 or 32 lanes run one trajectory each in batches of speculative
 //     rounds -- every lane evaluates the next selection from the state a
 //     path of likely reactions would reach, so one prefix chain fires
 //     several events -- then settle the batch's times, grid sums and records
@@ -63,7 +63,7 @@ constexpr unsigned long long kFnvOffset = 0xcbf29ce484222325ULL;
 constexpr unsigned long long kFnvPrime = 0x100000001b3ULL;
 constexpr long long kStateMax = 2147483647LL;
 constexpr unsigned kFullMask = 0xFFFFFFFFu;
-constexpr int kCoopMaxTraj = 4;    // trajectories per warp in cooperative mode
+constexpr int kCoopMaxTraj = 16;   // at most this many trajectories left: cooperative mode
 
 // x[s] for a runtime species index s < MAXS (select chain over registers).
 template <int MAXS>
@@ -456,10 +456,10 @@ __device__ __forceinline__ T shfl_all(T v, int src, int width = 32) {
 // ---------------------------------------------------------------------------
 // Cooperative mode: speculative batches.
 //
-// When at most 4 trajectories are left in a warp and no new work remains, the
-// warp splits into groups of L lanes (L = 8 for 3 or 4 trajectories, 16 for
-// 2, 32 for 1; the warp regroups as trajectories end), one trajectory per
-// group.  A group runs its trajectory in batches of L events; lane b holds
+// When at most 16 trajectories are left in a warp and no new work remains,
+// the warp splits into groups of L lanes (L = 32 / n rounded down to a power
+// of two for n trajectories: 2 lanes each for 9 to 16, ..., 32 for one; the
+// warp regroups as trajectories end), one trajectory per group.  A group runs its trajectory in batches of L events; lane b holds
 // the random numbers of event base + b of the batch.
 //
 // The events of a batch are selected in rounds.  In a round every lane of the
@@ -500,14 +500,31 @@ __device__ __forceinline__ unsigned group_bits(unsigned ballot, int gbase, int L
   return L == 32 ? ballot : (ballot >> gbase) & ((1u << L) - 1u);
 }
 
+// q.av[j] = v for a warp-uniform runtime j (a jump to one register move).
+template <int MAXM, int MAXS>
+__device__ __forceinline__ void set_propensity(Traj<MAXM, MAXS>& q, int j, unsigned long long v) {
+  switch (j) {
+#define SSA_SET_AV(J) \
+  case J:             \
+    if constexpr (J < MAXM) q.av[J] = v; \
+    break;
+    SSA_SET_AV(0) SSA_SET_AV(1) SSA_SET_AV(2) SSA_SET_AV(3) SSA_SET_AV(4) SSA_SET_AV(5) SSA_SET_AV(6)
+    SSA_SET_AV(7) SSA_SET_AV(8) SSA_SET_AV(9) SSA_SET_AV(10) SSA_SET_AV(11) SSA_SET_AV(12) SSA_SET_AV(13)
+    SSA_SET_AV(14) SSA_SET_AV(15)
+#undef SSA_SET_AV
+    default: break;
+  }
+}
+
 // Prefix sum j (left to right) from the propensities, given prefix j - 1.
+// Propensities of the bucket's padding reactions (j >= M) are +0, so the
+// padding prefixes equal prefix M - 1 and the last one is a0.
 template <int J, int MAXM, int MAXS>
-__device__ __forceinline__ void prefix_at(int M, Traj<MAXM, MAXS>& q) {
+__device__ __forceinline__ void prefix_at(Traj<MAXM, MAXS>& q) {
   if constexpr (J == 0) {
     q.pre[0] = __longlong_as_double((long long)q.av[0]);
   } else if constexpr (J < MAXM) {
-    const double s = __dadd_rn(q.pre[J - 1], __longlong_as_double((long long)q.av[J]));
-    q.pre[J] = (M == MAXM || J < M) ? s : q.pre[J - 1];
+    q.pre[J] = __dadd_rn(q.pre[J - 1], __longlong_as_double((long long)q.av[J]));
   }
 }
 
@@ -515,24 +532,24 @@ __device__ __forceinline__ void prefix_at(int M, Traj<MAXM, MAXS>& q) {
 // unchanged: the prefixes below lo are reused bit for bit and the chain
 // restarts at lo (a jump into the unrolled chain).
 template <int MAXM, int MAXS>
-__device__ __forceinline__ double prefix_sums_from(int M, Traj<MAXM, MAXS>& q, int lo) {
+__device__ __forceinline__ double prefix_sums_from(Traj<MAXM, MAXS>& q, int lo) {
   switch (lo) {
-    case 0: prefix_at<0>(M, q); [[fallthrough]];
-    case 1: prefix_at<1>(M, q); [[fallthrough]];
-    case 2: prefix_at<2>(M, q); [[fallthrough]];
-    case 3: prefix_at<3>(M, q); [[fallthrough]];
-    case 4: prefix_at<4>(M, q); [[fallthrough]];
-    case 5: prefix_at<5>(M, q); [[fallthrough]];
-    case 6: prefix_at<6>(M, q); [[fallthrough]];
-    case 7: prefix_at<7>(M, q); [[fallthrough]];
-    case 8: prefix_at<8>(M, q); [[fallthrough]];
-    case 9: prefix_at<9>(M, q); [[fallthrough]];
-    case 10: prefix_at<10>(M, q); [[fallthrough]];
-    case 11: prefix_at<11>(M, q); [[fallthrough]];
-    case 12: prefix_at<12>(M, q); [[fallthrough]];
-    case 13: prefix_at<13>(M, q); [[fallthrough]];
-    case 14: prefix_at<14>(M, q); [[fallthrough]];
-    case 15: prefix_at<15>(M, q); [[fallthrough]];
+    case 0: prefix_at<0>(q); [[fallthrough]];
+    case 1: prefix_at<1>(q); [[fallthrough]];
+    case 2: prefix_at<2>(q); [[fallthrough]];
+    case 3: prefix_at<3>(q); [[fallthrough]];
+    case 4: prefix_at<4>(q); [[fallthrough]];
+    case 5: prefix_at<5>(q); [[fallthrough]];
+    case 6: prefix_at<6>(q); [[fallthrough]];
+    case 7: prefix_at<7>(q); [[fallthrough]];
+    case 8: prefix_at<8>(q); [[fallthrough]];
+    case 9: prefix_at<9>(q); [[fallthrough]];
+    case 10: prefix_at<10>(q); [[fallthrough]];
+    case 11: prefix_at<11>(q); [[fallthrough]];
+    case 12: prefix_at<12>(q); [[fallthrough]];
+    case 13: prefix_at<13>(q); [[fallthrough]];
+    case 14: prefix_at<14>(q); [[fallthrough]];
+    case 15: prefix_at<15>(q); [[fallthrough]];
     default: break;
   }
   return q.pre[MAXM - 1];
@@ -810,18 +827,16 @@ __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Tra
         xl[s] = q.x[s] + P[s];
         safe = safe && (long long)q.x[s] + up[s] <= kStateMax;
       }
-      // products of the reactions any running lane must recompute (a
-      // warp-uniform branch per reaction skips the others entirely)
-      const uint32_t dany = __reduce_or_sync(kFullMask, run ? dirty : 0u);
-#pragma unroll
-      for (int j = 0; j < MAXM; ++j) {
-        if ((dany >> j) & 1u) {
-          const unsigned long long pj = propensity_fp64(a.sm.cbits[j], mass_action_h<MAXS>(a.sm.rinfo[j], xl));
-          if (run && ((dirty >> j) & 1u)) q.av[j] = pj;
-        }
+      // products of the reactions any running lane must recompute, one
+      // warp-uniform reaction at a time
+      const uint32_t dany = __reduce_or_sync(kFullMask, run ? dirty : 0u) & ((1u << MAXM) - 1u);
+      for (uint32_t dm = dany; dm != 0u; dm &= dm - 1u) {
+        const int j = __ffs((int)dm) - 1;
+        const unsigned long long pj = propensity_fp64(a.sm.cbits[j], mass_action_h<MAXS>(a.sm.rinfo[j], xl));
+        if (run && ((dirty >> j) & 1u)) set_propensity(q, j, pj);
       }
       const int lo = __reduce_min_sync(kFullMask, (run && dirty != 0u) ? (__ffs((int)dirty) - 1) : MAXM);
-      const double a0 = prefix_sums_from(e.M, q, lo);
+      const double a0 = prefix_sums_from(q, lo);
       if (run) dirty = 0u;
       const int ei = nres + dep;  // this node's event within the batch
       const bool inwin = ei < L;
