@@ -95,6 +95,9 @@ def parse_args():
     p.add_argument("--batch-div", type=int, default=1,
                    help="batch workload: divide every network's trajectory count by this")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true",
+                   help="headline line only (by default the HIV-shaped FP64 line also carries a 'forms' object: the "
+                        "random network in FP64 and FP32, the gradient and the full batch, a few steps each)")
     p.add_argument("--profile-small", action="store_true",
                    help="one small step for an ncu capture (--profile-n trajectories); prints no bench line")
     p.add_argument("--profile-n", type=int, default=16384)
@@ -177,6 +180,23 @@ def fp64_ops_per_event(n_reactions: int) -> int:
     return 2 * n_reactions + 2
 
 
+def survey_ops_per_event(net) -> float:
+    """FP64 operations of one event by the instruction-count estimate of the
+    scope table (a plain implementation with FP64 uniform map, logarithm and
+    division): 4 (uniform map) + 20 (log) + 9 (division) + 1 (t add) + M (a0)
+    + M (selection scan) + 2 d (d = mean number of propensities an event
+    changes); 34 + 2M + 2d, about 60 for M = 10."""
+    import numpy as np
+    R = np.asarray(net.reactants)
+    nu = np.asarray(net.products) - R
+    reads = R > 0                              # [M, S]: reaction k reads species s
+    changes = nu != 0                          # [M, S]: reaction j changes species s
+    dep = (changes.astype(int) @ reads.T.astype(int)) > 0   # [j, k]
+    d = float(dep.sum(axis=1).mean())
+    M = R.shape[0]
+    return 34.0 + 2.0 * M + 2.0 * d
+
+
 def oracle_mode(args):
     """(schedule, precision) of the oracle matching the GPU run: the warp
     layout's W32 order for the random network, FP32 when asked."""
@@ -186,8 +206,28 @@ def oracle_mode(args):
     return schedule, precision
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(w, n_traj_sample: int, args=None):
-    """The oracle as it stands, on all host cores (one thread per id range)."""
+    """The oracle as it stands, on all host cores (one thread per id range),
+    and on one thread over an eighth of the same ids."""
     import oracle
     cores = os.cpu_count() or 1
     schedule, precision = oracle_mode(args) if args is not None else (oracle.SCHEDULE_L, oracle.PRECISION_FP64)
@@ -195,9 +235,44 @@ def cpu_baseline(w, n_traj_sample: int, args=None):
     r = oracle.run(w.net, n_traj_sample, w.t_end, w.n_grid, w.seed, threads=cores, schedule=schedule,
                    precision=precision)
     dt = time.perf_counter() - t0
+    n1 = max(1, n_traj_sample // 8)
+    t1 = time.perf_counter()
+    r1 = oracle.run(w.net, n1, w.t_end, w.n_grid, w.seed, threads=1, schedule=schedule, precision=precision)
+    dt1 = time.perf_counter() - t1
     return {"value": r.events / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"trajectories 0..{n_traj_sample - 1} of the workload (seed {w.seed}), "
-                      f"{r.events} events in {dt:.3f} s on {cores} threads"}
+                      f"{r.events} events in {dt:.3f} s on {cores} threads",
+            "value_1thread": r1.events / dt1,
+            "sample_1thread": f"trajectories 0..{n1 - 1}, {r1.events} events in {dt1:.3f} s on 1 thread",
+            "cpu_model": cpu_model()}
+
+
+def cpu_baseline_grad(w, n_traj_sample: int, target):
+    """The oracle's forward ensemble and likelihood-ratio contributions
+    (oracle.grad) on all host cores; events counted twice as on the GPU."""
+    import numpy as np
+
+    import oracle
+    cores = os.cpu_count() or 1
+    tgt = np.asarray(target, dtype=np.float64)
+
+    def one(n, threads):
+        t0 = time.perf_counter()
+        r = oracle.run(w.net, n, w.t_end, w.n_grid, w.seed, threads=threads)
+        mean, _ = oracle.finalize(n, r.S1, r.S2)
+        wgt = np.zeros_like(mean)
+        wgt[:, 2] = 2.0 * (mean[:, 2] - tgt)
+        oracle.grad(w.net, n, w.t_end, w.n_grid, w.seed, wgt, mean, threads=threads)
+        return 2 * r.events, time.perf_counter() - t0
+    ev, dt = one(n_traj_sample, cores)
+    n1 = max(1, n_traj_sample // 8)
+    ev1, dt1 = one(n1, 1)
+    return {"value": ev / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"trajectories 0..{n_traj_sample - 1} (seed {w.seed}): forward + likelihood-ratio "
+                      f"contributions, {ev} events counted twice in {dt:.3f} s on {cores} threads",
+            "value_1thread": ev1 / dt1,
+            "sample_1thread": f"trajectories 0..{n1 - 1}, {ev1} events counted twice in {dt1:.3f} s on 1 thread",
+            "cpu_model": cpu_model()}
 
 
 def run_reference(args):
@@ -279,7 +354,7 @@ def run_ours(args):
     if args.profile_small:
         run_step(1)
         torch.cuda.synchronize()
-        return 0
+        return None
 
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     for i in range(args.warmup):
@@ -375,6 +450,8 @@ def run_ours(args):
                          "traffic": (spec["dram_bytes"][args.precision] if isinstance(spec["dram_bytes"], dict)
                                      else spec["dram_bytes"]),
                          "kernel_ms": kern_avg, "ops_per_event": fp64_ops_per_event(M),
+                         "ops_per_event_survey": survey_ops_per_event(w.net),
+                         "frac_survey": survey_ops_per_event(w.net) * (events / K) / (kern_avg * 1e-3) * 1e-9 / peak,
                          "peak_basis": "2 FP64 ops/clk/SM x 152 SMs x median SM clock (nominal 1.25 TFLOP/s dense)"},
             "cpu_baseline": cpu,
             "fp64_same_gpu": fp64_same_gpu,
@@ -383,11 +460,10 @@ def run_ours(args):
             "gpu_launches": 3 * K,
             "clocks": clk,
         }
-        print(json.dumps(result))
     model.close()
     if pg:
         pg.destroy_process_group()
-    return 0
+    return result
 
 
 def compare_with_fp64(args, ssa, torch, model, w, n, run_step, totals, stream, flush):
@@ -498,7 +574,7 @@ def run_grad(args):
         step(1)
         torch.cuda.synchronize()
         model.close()
-        return 0
+        return None
     for i in range(args.warmup):
         step(1 + i)
     torch.cuda.synchronize()
@@ -542,6 +618,7 @@ def run_grad(args):
     kern = statistics.mean(grad_ms)
     ops_bwd = (4 * M + 2) * (events / 2 / K)
     achieved = ops_bwd / (kern * 1e-3) * 1e-9
+    line = None
     if rank == 0:
         t0 = time.perf_counter()
         e_ev = 0
@@ -556,7 +633,7 @@ def run_grad(args):
         e_dt = time.perf_counter() - t0
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            cpu = cpu_baseline(w, min(n, spec["cpu_sample"]))
+            cpu = cpu_baseline_grad(w, min(n, spec["cpu_sample"]), target.cpu().numpy())
         g, se = last
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -576,17 +653,17 @@ def run_grad(args):
                          "ops_per_event": 4 * M + 2,
                          "peak_basis": "2 FP64 ops/clk/SM x 152 SMs x median SM clock"},
             "cpu_baseline": cpu,
-            "e2e": {"value": e_ev / e_dt, "unit": UNIT, "h2d_bytes_per_step": int(8 * M),
-                    "d2h_bytes_per_step": int(8 * M), "steps": args.e2e_steps,
-                    "note": "torch autograd: rates in, loss.backward(), rates.grad read back; events as timed"},
+            "e2e": ({"value": e_ev / e_dt, "unit": UNIT, "h2d_bytes_per_step": int(8 * M),
+                     "d2h_bytes_per_step": int(8 * M), "steps": args.e2e_steps,
+                     "note": "torch autograd: rates in, loss.backward(), rates.grad read back; events as timed"}
+                    if args.e2e_steps > 0 else None),
             "gpu_launches": K * 7,
             "clocks": clk,
         }
-        print(json.dumps(line))
     model.close()
     if pg:
         pg.destroy_process_group()
-    return 0
+    return line
 
 
 def ssa_events_estimate(events_total, steps):
@@ -642,6 +719,7 @@ def run_avgxy(args):
     peak = FP64_OPS_PER_SM_CLK * SMS_GB300 * sm_mhz * 1e6 * 1e-9
     simulated = 1.0 + min(n, 4096) / n  # the logging run and the pilot
     achieved = simulated * (2 * M + 2) * events_per_run / (total_ms / K * 1e-3) * 1e-9
+    line = None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -662,9 +740,8 @@ def run_avgxy(args):
             "gpu_launches": None,
             "clocks": clk,
         }
-        print(json.dumps(line))
     model.close()
-    return 0
+    return line
 
 
 def run_batch(args):
@@ -701,7 +778,7 @@ def run_batch(args):
         batch.close()
         for m in models:
             m.close()
-        return 0
+        return None
     threads, split, tune_ms = batch.tune()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     for i in range(args.warmup):
@@ -743,6 +820,7 @@ def run_batch(args):
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
     peak = FP64_OPS_PER_SM_CLK * SMS_GB300 * sm_mhz * 1e6 * 1e-9
     achieved = ops / (total_ms * 1e-3) * 1e-9
+    line = None
     if rank == 0:
         # end to end: one-shot host call (model tables, graph, launch, copies back)
         host_means = [np.empty((g, m.n_species)) for g, m in zip(n_grid, models)]
@@ -778,18 +856,18 @@ def run_batch(args):
                          "ops_per_event": "M_b + 2 (FP64 re-summation of a0, r2 * A32, quotient, t add)",
                          "peak_basis": "2 FP64 ops/clk/SM x 152 SMs x median SM clock"},
             "cpu_baseline": cpu,
-            "e2e": {"value": e_events / e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "steps": args.e2e_steps, "note": "one-shot batches from host: create, tune-free launch, copy"},
+            "e2e": ({"value": e_events / e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                     "steps": args.e2e_steps, "note": "one-shot batches from host: create, tune-free launch, copy"}
+                    if args.e2e_steps > 0 else None),
             "gpu_launches": K * (2 + n_groups(ws, split)),
             "clocks": clk,
         }
-        print(json.dumps(line))
     batch.close()
     for m in models:
         m.close()
     if pg:
         pg.destroy_process_group()
-    return 0
+    return line
 
 
 def n_groups(ws, split: bool) -> int:
@@ -806,35 +884,81 @@ def n_groups(ws, split: bool) -> int:
 
 def cpu_baseline_batch(ws, per_network: int):
     """The oracle on all host cores over the first `per_network` trajectories
-    of every network of the batch (FP32 propensities, W32)."""
+    of every network of the batch (FP32 propensities, W32), and on one thread
+    over the first trajectory of every eighth network."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
     cores = os.cpu_count() or 1
 
-    def one(w):
-        r = oracle.run(w.net, min(per_network, w.n_traj), w.t_end, w.n_grid, w.seed, max_events=1000000,
+    def one(w, n=per_network):
+        r = oracle.run(w.net, min(n, w.n_traj), w.t_end, w.n_grid, w.seed, max_events=1000000,
                        schedule=oracle.SCHEDULE_W32, precision=oracle.PRECISION_FP32)
         return r.events
     t0 = time.perf_counter()
     with ThreadPoolExecutor(cores) as ex:
         ev = sum(ex.map(one, ws))
     dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    ev1 = sum(one(w, 1) for w in ws[::8])
+    dt1 = time.perf_counter() - t1
     return {"value": ev / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {per_network} trajectories of each of the {len(ws)} networks, {ev} events in "
-                      f"{dt:.2f} s on {cores} threads"}
+                      f"{dt:.2f} s on {cores} threads",
+            "value_1thread": ev1 / dt1,
+            "sample_1thread": f"first trajectory of every 8th network, {ev1} events in {dt1:.2f} s on 1 thread",
+            "cpu_model": cpu_model()}
+
+
+def run_forms(args):
+    """The other forms of the method on this GPU, each with a few timed steps
+    (their default workloads at full size): the random 32 x 128 network in
+    FP64 (W32) and FP32 (with the FP32-vs-FP64 standard-error report), the
+    rate gradient on 1,048,576 trajectories and the full 256-network batch."""
+    def sub(**kw):
+        d = dict(vars(args))
+        d.update(kw)
+        d.setdefault("batch_div", 1)
+        return argparse.Namespace(**d)
+
+    def brief(line):
+        if line is None:
+            return None
+        keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "traj_per_s", "events_per_step",
+                "roofline", "cpu_baseline", "e2e", "fp64_same_gpu", "fp32_vs_fp64", "grad_kernel_ms", "clocks",
+                "gpu_launches")
+        return {k: line[k] for k in keep if k in line}
+
+    forms = {}
+    common = {"profile_small": False, "no_cpu_baseline": args.no_cpu_baseline}
+    forms["random_fp64"] = brief(run_ours(sub(workload="random", precision="fp64", n_traj=262144, steps=2,
+                                              warmup=1, e2e_steps=1, **common)))
+    forms["random_fp32"] = brief(run_ours(sub(workload="random", precision="fp32", n_traj=262144, steps=2,
+                                              warmup=1, e2e_steps=1, **common)))
+    forms["grad"] = brief(run_grad(sub(workload="grad", precision="fp64", n_traj=1048576, steps=2, warmup=1,
+                                       e2e_steps=1, **common)))
+    forms["batch"] = brief(run_batch(sub(workload="batch", precision="fp32", n_traj=None, steps=1, warmup=1,
+                                         e2e_steps=0, batch_div=1, **common)))
+    return forms
 
 
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batch":
-        return run_batch(args)
-    if args.workload == "grad":
-        return run_grad(args)
-    if args.workload == "avgxy":
-        return run_avgxy(args)
-    return run_ours(args)
+    runner = {"batch": run_batch, "grad": run_grad, "avgxy": run_avgxy}.get(args.workload, run_ours)
+    line = runner(args)
+    if line is None:
+        return 0
+    _, world, _ = dist_env()
+    if args.workload == "hiv_shaped" and args.precision == "fp64" and world == 1 and not args.no_forms:
+        forms = run_forms(args)
+        line["forms"] = forms
+        r32 = forms.get("random_fp32") or {}
+        # the FP32-propensity form against the plain FP64 kernel on the same GPU (random 32 x 128 network)
+        line["fp64_same_gpu"] = r32.get("fp64_same_gpu")
+        line["fp32_vs_fp64"] = r32.get("fp32_vs_fp64")
+    print(json.dumps(line))
+    return 0
 
 
 if __name__ == "__main__":
