@@ -155,6 +155,8 @@ def lib():
         L.oracle_select.restype = ctypes.c_int
         L.oracle_prefix.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, vp]
         L.oracle_prefix.restype = None
+        L.oracle_fp32_a0.argtypes = [ctypes.c_int, vp, ctypes.c_int]
+        L.oracle_fp32_a0.restype = f64
         L.oracle_finalize.argtypes = [i64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]
         L.oracle_finalize.restype = None
         inv, lnf, ln2, k3, k5 = log_constants()
@@ -404,6 +406,14 @@ def prefix_sums(a, schedule: int = SCHEDULE_L):
     a0 = np.zeros(1, dtype=np.float64)
     lib().oracle_prefix(int(av.shape[0]), av.ctypes.data, int(schedule), pre.ctypes.data, a0.ctypes.data)
     return pre, float(a0[0])
+
+
+def fp32_a0(a32, schedule: int = SCHEDULE_W32) -> float:
+    """a0 of the FP32-propensity mode for binary32 propensities ``a32``: one
+    compensated binary32 pair (L) or the lanes' pairs combined by the W32
+    scan in pair arithmetic (W32), widened to FP64 once."""
+    av = np.ascontiguousarray(a32, dtype=np.float32)
+    return float(lib().oracle_fp32_a0(int(av.shape[0]), av.ctypes.data, int(schedule)))
 
 
 def finalize(n_traj: int, S1: np.ndarray, S2: np.ndarray):

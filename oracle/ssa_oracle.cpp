@@ -45,10 +45,13 @@
 //     run's schedule (L or W32), with total A32 (the last prefix or the
 //     scan's lane-31 value);
 //   * a0 in FP64, formed again at every event (no incremental drift): under
-//     W32 each lane's chunk is summed left to right in binary32 with
-//     error compensation (compensated_sum), widened to FP64, and the 32
-//     lane values are combined by the W32 Kogge-Stone scan in FP64; under L
-//     the whole list is one compensated sum; t_next = t + (-ln r1) / a0;
+//     W32 each lane's chunk is summed left to right in binary32 with error
+//     compensation and kept as a binary32 pair (head, error sum)
+//     (compensated_pair); the 32 pairs are combined by the W32 Kogge-Stone
+//     scan in pair arithmetic (heads by TwoSum, errors added in binary32:
+//     pair_add), and lane 31's pair is widened and added once in FP64; under
+//     L the whole list is one compensated pair, widened and added the same
+//     way; t_next = t + (-ln r1) / a0;
 //   * selection: smallest j with a_j > 0 and (double)prefix_j > r2 *
 //     (double)A32 (FP64 product); if none, the last j with a_j > 0.
 // When every product and sum is exact in binary32, this mode reproduces the
@@ -226,25 +229,17 @@ void w32_prefix(const std::vector<T>& a, int M, std::vector<T>& prefix, T* a0) {
   *a0 = scan[31];
 }
 
-// Inclusive Kogge-Stone scan of 32 lane values (offsets 1, 2, 4, 8, 16,
-// every lane reading the previous step's values); total = lane 31's value.
-void w32_lanes(const std::vector<double>& v, std::vector<double>& scan, double* total) {
-  for (int l = 0; l < 32; ++l) scan[l] = v[l];
-  for (int off = 1; off < 32; off <<= 1) {
-    double prev[32];
-    for (int l = 0; l < 32; ++l) prev[l] = scan[l];
-    for (int l = off; l < 32; ++l) scan[l] = prev[l] + prev[l - off];
-  }
-  *total = scan[31];
-}
+// FP32 mode: the binary32 pair (head, error) of an unevaluated sum.
+struct Pair32 {
+  float s, e;
+};
 
-// FP32 mode: a0's share of a[b..e) (binary32 values), summed left to right
-// with error compensation in binary32 -- the cascaded TwoSum of Ogita, Rump
-// and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 26(6),
-// 2005, Algorithm Sum2): s_j = s_{j-1} + a_j rounded, its exact rounding
-// error by Knuth's TwoSum, the errors added up in binary32 -- and the two
-// parts widened exactly and added once in FP64.
-double compensated_sum(const std::vector<float>& a, int b, int e) {
+// FP32 mode: a[b..e) (binary32 values) summed left to right with error
+// compensation in binary32 -- the cascaded TwoSum of Ogita, Rump and Oishi
+// ("Accurate sum and dot product", SIAM J. Sci. Comput. 26(6), 2005,
+// Algorithm Sum2): s_j = s_{j-1} + a_j rounded, its exact rounding error by
+// Knuth's TwoSum, the errors added up in binary32 -- kept as the pair (s, err).
+Pair32 compensated_pair(const std::vector<float>& a, int b, int e) {
   float s = a[b], err = 0.0f;
   for (int j = b + 1; j < e; ++j) {
     const float x = a[j];
@@ -254,7 +249,43 @@ double compensated_sum(const std::vector<float>& a, int b, int e) {
     err = err + d;
     s = t;
   }
-  return (double)s + (double)err;
+  return Pair32{s, err};
+}
+
+// The sum of two pairs in the same spirit: the heads added with their exact
+// rounding error (TwoSum), the two error parts and that error added in
+// binary32.  (TwoSum's error is the exact residual, so the result does not
+// depend on the order of the operands.)
+Pair32 pair_add(Pair32 p, Pair32 q) {
+  const float t = p.s + q.s;
+  const float bp = t - p.s;
+  const float d = (p.s - (t - bp)) + (q.s - bp);
+  return Pair32{t, (p.e + q.e) + d};
+}
+
+// A pair widened exactly to FP64 and its two parts added once (rounded).
+double pair_value(Pair32 p) { return (double)p.s + (double)p.e; }
+
+// FP32 mode, schedule L: a0 from one compensated pair over the whole list.
+double compensated_sum(const std::vector<float>& a, int b, int e) { return pair_value(compensated_pair(a, b, e)); }
+
+// FP32 mode, schedule W32: each lane's chunk as a compensated pair, the 32
+// pairs combined by the inclusive Kogge-Stone scan of w32_prefix (offsets 1,
+// 2, 4, 8, 16, every lane reading the previous step's values) with pair_add,
+// and lane 31's pair widened.
+double w32_pair_a0(const std::vector<float>& a32, int M) {
+  const int chunk = (M + 31) / 32;
+  Pair32 scan[32];
+  for (int l = 0; l < 32; ++l) {
+    const int b = l * chunk, e = std::min(M, b + chunk);
+    scan[l] = (b < e) ? compensated_pair(a32, b, e) : Pair32{0.0f, 0.0f};
+  }
+  for (int off = 1; off < 32; off <<= 1) {
+    Pair32 prev[32];
+    for (int l = 0; l < 32; ++l) prev[l] = scan[l];
+    for (int l = off; l < 32; ++l) scan[l] = pair_add(prev[l], prev[l - off]);
+  }
+  return pair_value(scan[31]);
 }
 
 // Selection (Sec. 2: one of the possible transitions is chosen): the
@@ -343,15 +374,7 @@ TrajResult run_one(const Model& m, uint64_t traj_id, double t_end, int G, const 
         a0 = compensated_sum(a32, 0, m.M);
       } else {
         w32_prefix(a32, m.M, prefix32, &a0_32);
-        // lane l's chunk summed with compensation, then the lanes' FP64 values
-        // in the W32 scan order
-        const int chunk = (m.M + 31) / 32;
-        std::vector<double> lane_sum(32, 0.0), lane_scan(32);
-        for (int l = 0; l < 32; ++l) {
-          const int b = l * chunk, e = std::min(m.M, b + chunk);
-          lane_sum[l] = (b < e) ? compensated_sum(a32, b, e) : 0.0;
-        }
-        w32_lanes(lane_sum, lane_scan, &a0);
+        a0 = w32_pair_a0(a32, m.M);
       }
       for (int j = 0; j < m.M; ++j) prefix[j] = (double)prefix32[j];
     }
@@ -676,6 +699,13 @@ void oracle_prefix(int M, const double* a, int schedule, double* prefix, double*
     w32_prefix(av, M, pv, a0);
   }
   for (int j = 0; j < M; ++j) prefix[j] = pv[j];
+}
+
+// FP32 mode's a0 for binary32 propensities a[0..M) in the given schedule
+// (L: one compensated pair; W32: the lanes' pairs scanned).  For tests.
+double oracle_fp32_a0(int M, const float* a, int schedule) {
+  std::vector<float> av(a, a + M);
+  return (schedule == 0) ? compensated_sum(av, 0, M) : w32_pair_a0(av, M);
 }
 
 // The reaction the direct method picks for propensities a[0..M) (FP64

@@ -171,3 +171,94 @@ def test_moment_sums_match_traces():
         s4 += xs.astype(np.float64) ** 4
     assert np.allclose(r.S3, s3, rtol=1e-12) and np.allclose(r.S4, s4, rtol=1e-12)
     assert r.S1[0, 0] == N * 1000 and math.isclose(r.S3[0, 0], N * 1e9)
+
+
+def _fp64_lane_scan(a32):
+    """The former reading, for contrast only: each lane's compensated chunk
+    widened to FP64 on its own, the 32 lane values scanned in FP64."""
+    M = len(a32)
+    ch = (M + 31) // 32
+    lanes = []
+    for l in range(32):
+        c = [np.float32(v) for v in a32[l * ch:min(M, (l + 1) * ch)]]
+        if not c:
+            lanes.append(0.0)
+            continue
+        s, err = c[0], np.float32(0.0)
+        for x in c[1:]:
+            t = np.float32(s + x)
+            bp = np.float32(t - s)
+            err = np.float32(err + np.float32(np.float32(s - np.float32(t - bp)) + np.float32(x - bp)))
+            s = t
+        lanes.append(float(s) + float(err))
+    v = lanes[:]
+    off = 1
+    while off < 32:
+        prev = v[:]
+        for l in range(off, 32):
+            v[l] = prev[l] + prev[l - off]
+        off *= 2
+    return v[31]
+
+
+def test_w32_a0_pair_scan_is_exact_where_every_error_is_representable():
+    """Lane sums that leave FP64 rounding in a plain FP64 scan of the lanes
+    but whose errors are exact binary32 values: the pair scan keeps every
+    error until the one final FP64 addition, so a0 is the exact sum (an
+    integer here), and the first event time is E / a0."""
+    from fractions import Fraction
+    M = 64  # two reactions per lane
+    cases = []
+    a = np.zeros(M, np.float32)
+    a[0], a[2], a[4] = 2.0 ** 53, 1.0, 1.0          # lanes 0, 1, 2
+    cases.append(a)
+    a = np.zeros(M, np.float32)
+    a[0], a[1], a[6], a[9] = 2.0 ** 40, 3.0, 2.0 ** 13, 1.0
+    cases.append(a)
+    a = np.zeros(M, np.float32)
+    a[::2] = 2.0 ** 52
+    a[1::2] = 1.0                                     # 32 lanes of (2^52, 1)
+    cases.append(a)
+    differs = 0
+    for a in cases:
+        exact = sum(Fraction(float(v)) for v in a)
+        assert exact == int(exact) and float(exact) == exact  # representable in FP64
+        got = oracle.fp32_a0(a, oracle.SCHEDULE_W32)
+        assert Fraction(got) == exact
+        differs += _fp64_lane_scan(a) != got
+    assert differs >= 1  # the cases tell the pair scan from a plain FP64 scan of the lanes
+    # the same through a trajectory's first event: order-0 reactions with these rates
+    a = cases[0]
+    R = np.zeros((M, 1), np.int32)
+    P = np.zeros((M, 1), np.int32)
+    net = W.Network("pair_scan", ["X"], R, P, a.astype(np.float64), np.array([0], np.int32))
+    for seed in (3, 4):
+        t, _, E = _first_event(net, seed, schedule=oracle.SCHEDULE_W32)
+        assert t == E / (2.0 ** 53 + 2.0)
+
+
+@pytest.mark.parametrize("M", [8, 64, 128, 300, 512])
+def test_w32_a0_is_within_the_pair_summation_bound(M):
+    """Random non-negative binary32 propensities over 20 binades: the pair
+    scan's a0 is within 2^-40 (relative) of the exact sum -- the bound of
+    compensated summation in binary32 pairs ((n u)^2 with u = 2^-24, n <= 512
+    terms, plus one FP64 rounding) -- far inside what a plain binary32 sum
+    reaches on the same data."""
+    from fractions import Fraction
+    rng = np.random.default_rng(M)
+    worst, worst32 = 0.0, 0.0
+    for _ in range(40):
+        a = (rng.random(M) * 2.0 ** rng.integers(-10, 10, size=M)).astype(np.float32)
+        a[rng.random(M) < 0.2] = 0.0
+        exact = sum(Fraction(float(v)) for v in a)
+        if exact == 0:
+            continue
+        got = oracle.fp32_a0(a, oracle.SCHEDULE_W32)
+        worst = max(worst, abs(float((Fraction(got) - exact) / exact)))
+        s32 = np.float32(0.0)
+        for v in a:
+            s32 = np.float32(s32 + v)
+        worst32 = max(worst32, abs(float((Fraction(float(s32)) - exact) / exact)))
+        assert got == oracle.fp32_a0(a[::-1].copy()[::-1].copy(), oracle.SCHEDULE_W32)  # deterministic
+    assert worst <= 2.0 ** -40
+    assert worst32 > 2.0 ** -30  # the data do exercise binary32 rounding
