@@ -72,6 +72,10 @@ __global__ void __launch_bounds__(256) k_ssa_batch(const BatchLaunch L) {
   uint64_t* s_lnf = s_inv + kLogCells;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int32_t* xs = reinterpret_cast<int32_t*>(s_lnf + kLogCells) + (size_t)warp * L.smax;
+  // per-warp pre-event counts of a batch, after every warp's state slots
+  int32_t* xrec = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(s_lnf + kLogCells) +
+                                             align_up((size_t)(blockDim.x >> 5) * L.smax * 4, 16)) +
+                  (size_t)warp * 32 * kRecPerEvent;
   for (int i = tid; i < kLogCells; i += blockDim.x) {
     s_inv[i] = d_log_tables.inv[i];
     s_lnf[i] = d_log_tables.lnf[i];
@@ -93,7 +97,7 @@ __global__ void __launch_bounds__(256) k_ssa_batch(const BatchLaunch L) {
     }
     const WarpNet net = L.nets[lo].net;
     const unsigned long long id = L.traj_offset + (unsigned long long)(item - L.work_begin[lo]);
-    const WarpTraj r = warp_trajectory<MAXCH, F32>(net, xs, id, key0, key1, L.max_events, s_inv, s_lnf);
+    const WarpTraj r = warp_trajectory<MAXCH, F32>(net, xs, xrec, id, key0, key1, L.max_events, s_inv, s_lnf);
     if (lane == 0) {
       unsigned long long* st = L.stats + (size_t)lo * 4;
       atomicAdd(st + 0, (unsigned long long)r.n);
@@ -106,6 +110,16 @@ __global__ void __launch_bounds__(256) k_ssa_batch(const BatchLaunch L) {
 }
 
 __global__ void k_set_word(unsigned long long* p, unsigned long long v) { *p = v; }
+
+// The most species any reaction of a model changes (from its host tables).
+int model_nnz_max(const ssa_model* m) {
+  ModelImageView mv;
+  if (!model_image_view(m, &mv)) return 1 << 30;
+  const int32_t* ptr = reinterpret_cast<const int32_t*>(mv.image + mv.off_nu_ptr);
+  int mx = 0;
+  for (int j = 0; j < mv.M; ++j) mx = std::max(mx, ptr[j + 1] - ptr[j]);
+  return mx;
+}
 
 // Per-network tables the batch derives on the device: dependency bits for
 // the warp layout and the binary32 rates.
@@ -156,7 +170,8 @@ cudaError_t batch_kernel(bool fp32, int bucket, bool launch, const BatchLaunch* 
 }
 
 size_t batch_smem(int threads, int smax) {
-  return (size_t)kLogCells * 16 + align_up((size_t)(threads / 32) * smax * 4, 16);
+  return (size_t)kLogCells * 16 + align_up((size_t)(threads / 32) * smax * 4, 16) +
+         (size_t)(threads / 32) * 32 * kRecPerEvent * 4;
 }
 
 }  // namespace
@@ -506,6 +521,7 @@ ssa_status ssa_batch_create(int32_t n_models, const ssa_model* const* models, co
     w.S = b->S[i];
     w.M = b->M[i];
     w.G = b->G[i];
+    w.nnz_max = model_nnz_max(b->models[i]);
     const bool uniform = !gr || host_grid_is_uniform(gr, b->G[i], te);
     w.grid_uniform = (uniform && b->G[i] >= 2 && b->G[i] <= (1 << 20) && te < 1e30) ? 1 : 0;
     w.grid_scale = (float)((double)(b->G[i] - 1) / te);

@@ -12,7 +12,7 @@ namespace {
 
 // Shared-memory layout of the warp kernel (bytes).
 struct WarpSmem {
-  size_t log_inv, log_lnf, cbits, c32, rinfo, nu_ptr, nu_idx, nu_val, x0, depw, mod, x, total;
+  size_t log_inv, log_lnf, cbits, c32, rinfo, nu_ptr, nu_idx, nu_val, x0, depw, mod, x, xrec, total;
 };
 
 // The rate-modifier tables (4 x M words) are always reserved: they are small
@@ -32,6 +32,7 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int M, int S, int nnz, int 
   L.depw = o; o += align_up((size_t)M * 32 * 2, 16);
   L.mod = o; o += align_up((size_t)M * 4, 16) + (size_t)M * 24;
   L.x = o; o += align_up((size_t)warps * S * 4, 16);
+  L.xrec = o; o += (size_t)warps * 32 * kRecPerEvent * 4;  // pre-event counts of a batch, per warp
   L.total = o;
   return L;
 }
@@ -42,6 +43,7 @@ template <int MAXCH, bool F32, bool LOG>
 __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a, const EventLog lg) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long blk[4];
+  __shared__ int s_nnz_max;
   const int S = a.m.S, M = a.m.M, T = blockDim.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
   const int ch = (M + 31) / 32;
@@ -57,6 +59,8 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a, const EventLo
   int32_t* s_x0 = reinterpret_cast<int32_t*>(smem + L.x0);
   uint16_t* s_depw = reinterpret_cast<uint16_t*>(smem + L.depw);
   int32_t* xs = reinterpret_cast<int32_t*>(smem + L.x) + (size_t)warp * S;
+  int32_t* xrec = reinterpret_cast<int32_t*>(smem + L.xrec) + (size_t)warp * 32 * kRecPerEvent;
+  if (tid == 0) s_nnz_max = 0;
 
   for (int i = tid; i < kLogCells; i += T) {
     s_inv[i] = d_log_tables.inv[i];
@@ -67,7 +71,11 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a, const EventLo
     s_c32[j] = __double2float_rn(a.m.c[j]);
     s_rinfo[j] = a.m.rinfo[j];
   }
-  for (int j = tid; j <= M; j += T) s_nuptr[j] = a.m.nu_ptr[j];
+  __syncthreads();
+  for (int j = tid; j <= M; j += T) {
+    s_nuptr[j] = a.m.nu_ptr[j];
+    if (j < M) atomicMax(&s_nnz_max, a.m.nu_ptr[j + 1] - a.m.nu_ptr[j]);
+  }
   for (int i = tid; i < a.m.nnz; i += T) {
     s_nuidx[i] = a.m.nu_idx[i];
     s_nuval[i] = a.m.nu_val[i];
@@ -110,6 +118,7 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a, const EventLo
   net.S = S;
   net.M = M;
   net.G = a.G;
+  net.nnz_max = s_nnz_max;
   net.grid_uniform = a.grid_uniform;
   net.grid_scale = a.grid_scale;
   net.grid_margin = a.grid_margin;
@@ -123,8 +132,8 @@ __global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a, const EventLo
     next = __shfl_sync(kFullMask, next, 0);
     if (next >= (unsigned long long)a.N) break;
     const long long li = (long long)next;
-    const WarpTraj r = warp_trajectory<MAXCH, F32, LOG>(net, xs, a.traj_offset + next, key0, key1, a.max_events,
-                                                        s_inv, s_lnf, &lg, &lst);
+    const WarpTraj r = warp_trajectory<MAXCH, F32, LOG>(net, xs, xrec, a.traj_offset + next, key0, key1,
+                                                        a.max_events, s_inv, s_lnf, &lg, &lst);
     if (lane == 0) {
       if (a.traj_events) a.traj_events[li] = (long long)r.n;
       if (a.traj_hash) a.traj_hash[li] = r.hash;

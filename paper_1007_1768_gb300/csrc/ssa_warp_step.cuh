@@ -28,9 +28,12 @@
 //
 // FP32-propensity mode (F32): a_j = (float)c_j * (float)h_j in binary32,
 // binary32 selection sums; a0 formed anew at every event from each lane's
-// error-compensated binary32 chunk sum (Ogita-Rump-Oishi Sum2), widened and
-// scanned in FP64; FP64 time; selection compares the widened binary32
-// prefixes with r2 times the binary32 total.
+// error-compensated binary32 chunk sum (Ogita-Rump-Oishi Sum2) kept as a
+// binary32 pair, the lanes' pairs scanned in pair arithmetic (TwoSum heads,
+// binary32 error sums) and lane 31's pair widened once to FP64 (lane b keeps
+// event b's pair and widens it when the batch is settled); FP64 time;
+// selection compares the binary32 prefixes with r2 times the binary32 total
+// (an FP64 product) rounded down to binary32.
 #ifndef SSA_WARP_STEP_CUH_
 #define SSA_WARP_STEP_CUH_
 
@@ -43,6 +46,10 @@ namespace {
 
 constexpr int kWarpFlagTruncated = 1;  // per-trajectory flag bits
 constexpr int kWarpFlagOverflow = 2;
+// Pre-event counts recorded per event of a batch (per-warp scratch of
+// 32 x kRecPerEvent words): networks whose reactions change at most this
+// many species each book their kept events lane-parallel.
+constexpr int kRecPerEvent = 4;
 
 // Exact binary32 -> binary64 widening of a non-negative value on the integer pipe.
 __device__ __forceinline__ double widen(float f) {
@@ -75,6 +82,7 @@ struct WarpNet {
   const double* mod_hi;
   long long t_end_bits;
   int S, M, G;
+  int nnz_max;                        // most species any reaction changes
   int grid_uniform;
   float grid_scale, grid_margin;
   uint32_t sid;                       // fourth Philox counter word
@@ -175,13 +183,18 @@ __device__ __forceinline__ void log_close(const EventLog& lg, WarpLogState& st) 
 // the state in xs[0..S) (shared memory, this warp's own).  MAXCH bounds the
 // chunk ceil(M / 32) (registers only; the chunk itself is the runtime value).
 // LOG: also write the event log (lg, lst).
+// xrec: the warp's own scratch of 32 x kRecPerEvent words (pre-event counts).
 template <int MAXCH, bool F32, bool LOG = false>
-__device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t* xs, unsigned long long traj_id,
-                                                    uint32_t key0, uint32_t key1, long long max_events,
-                                                    const uint64_t* s_inv, const uint64_t* s_lnf,
-                                                    const EventLog* lg = nullptr, WarpLogState* lst = nullptr) {
+__device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t* xs, int32_t* xrec,
+                                                    unsigned long long traj_id, uint32_t key0, uint32_t key1,
+                                                    long long max_events, const uint64_t* s_inv,
+                                                    const uint64_t* s_lnf, const EventLog* lg = nullptr,
+                                                    WarpLogState* lst = nullptr) {
   const int lane = threadIdx.x & 31;
   const int S = net.S, M = net.M;
+  // kept events booked lane-parallel from recorded pre-event counts (else the
+  // serial walk back through the batch; the event log takes that path too)
+  const bool fast = !LOG && net.nnz_max <= kRecPerEvent;
   const int ch = (M + 31) / 32;
   const int my0 = lane * ch;                          // first reaction of this lane
   const int mine = max(0, min(ch, M - my0));          // reactions this lane owns
@@ -217,7 +230,8 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
   for (;;) {
     const uint32_t base = n;
     const EventRandom rr = event_random(base + (uint32_t)lane, traj_id, net.sid, key0, key1, s_inv, s_lnf);
-    double my_a0 = 0.0;  // lane b: a0 of event b
+    double my_a0 = 0.0;  // lane b: a0 of event b (FP64 mode)
+    float my_s = 0.0f, my_e = 0.0f;  // lane b: a0 of event b as a binary32 pair (FP32 mode)
     int my_j = 0;        // lane b: reaction of event b
     int nb = 32;         // events applied (base .. base + nb - 1)
     int nrec = 32;       // events whose time is formed: the applied ones and the one that stopped the draws
@@ -262,7 +276,8 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
       // sum is the chunk sum (+0 for an empty lane).
       double run[MAXCH];   // FP64 mode: running sums
       float run32[MAXCH];  // FP32 mode: binary32 running sums
-      double a0, excl = 0.0, sel_total;
+      double a0 = 0.0, excl = 0.0, sel_total;
+      bool absorbing;  // every a_j is 0
       float excl32 = 0.0f;
       // loops over the chunk stop at ch (warp-uniform), the runtime chunk size
       if constexpr (F32) {
@@ -283,9 +298,10 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
         excl32 = __shfl_up_sync(kFullMask, v32, 1);
         sel_total = widen(__shfl_sync(kFullMask, v32, 31));
         // a0, formed anew each event: the lane's chunk summed left to right in
-        // binary32 with its rounding errors carried (cascaded TwoSum), the two
-        // parts widened and added in FP64, the lane values scanned in FP64.
-        // A past-the-end a_j = +0 leaves both parts unchanged.
+        // binary32 with its rounding errors carried (cascaded TwoSum), kept as
+        // the pair (cs, cerr); the lanes' pairs scanned in pair arithmetic
+        // (the Kogge-Stone pattern; heads by TwoSum, error parts added in
+        // binary32).  A past-the-end a_j = +0 leaves both parts unchanged.
         float cs = af[0], cerr = 0.0f;
 #pragma unroll
         for (int q = 1; q < MAXCH; ++q) {
@@ -297,13 +313,25 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
           cerr = __fadd_rn(cerr, d);
           cs = tt;
         }
-        double r64 = __dadd_rn(widen(cs), widen_signed(cerr));
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-          const double u = __shfl_up_sync(kFullMask, r64, off);
-          if (lane >= off) r64 = __dadd_rn(r64, u);
+          const float us = __shfl_up_sync(kFullMask, cs, off);
+          const float ue = __shfl_up_sync(kFullMask, cerr, off);
+          if (lane >= off) {
+            const float tt = __fadd_rn(cs, us);
+            const float bp = __fsub_rn(tt, cs);
+            const float d = __fadd_rn(__fsub_rn(cs, __fsub_rn(tt, bp)), __fsub_rn(us, bp));
+            cerr = __fadd_rn(__fadd_rn(cerr, ue), d);
+            cs = tt;
+          }
         }
-        a0 = __shfl_sync(kFullMask, r64, 31);
+        const float a0s = __shfl_sync(kFullMask, cs, 31);
+        const float a0e = __shfl_sync(kFullMask, cerr, 31);
+        if (lane == b) {
+          my_s = a0s;
+          my_e = a0e;
+        }
+        absorbing = __float_as_uint(a0s) == 0u;  // the head is +0 exactly when every a_j is 0
       } else {
         double v = av[0];
         run[0] = v;
@@ -321,9 +349,10 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
         excl = __shfl_up_sync(kFullMask, v, 1);
         a0 = __shfl_sync(kFullMask, v, 31);
         sel_total = a0;
+        absorbing = obits(a0) == 0;
       }
-      if (lane == b) my_a0 = a0;
-      if (obits(a0) == 0) {  // absorbing: the event's time is +inf
+      if (!F32 && lane == b) my_a0 = a0;
+      if (absorbing) {  // the event's time is +inf
         nb = b;
         nrec = b + 1;
         break;
@@ -369,11 +398,15 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
         jsel = __shfl_sync(kFullMask, mylast, 31 - __clz(pos));
       }
       if (lane == b) my_j = jsel;
-      // state change of jsel, one nonzero entry per lane
+      // state change of jsel, one nonzero entry per lane (the fast path
+      // records the pre-event count of entry e in xrec[b][e])
       const int q0 = net.nu_ptr[jsel], q1 = net.nu_ptr[jsel + 1];
       bool over = false;
-      for (int e = q0 + lane; e < q1; e += 32)
-        over |= (long long)xs[net.nu_idx[e]] + (long long)net.nu_val[e] > kStateMax;
+      for (int e = q0 + lane; e < q1; e += 32) {
+        const int xo = xs[net.nu_idx[e]];
+        over |= (long long)xo + (long long)net.nu_val[e] > kStateMax;
+        if (fast) xrec[b * kRecPerEvent + (e - q0)] = xo;
+      }
       if (__any_sync(kFullMask, over)) {  // not applied: the trajectory ends here unless past t_end
         nb = b;
         nrec = b + 1;
@@ -385,14 +418,17 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
       dirty = net.depw[jsel * 32 + lane];
     }
 
-    // the event times in order (lane b: event b's waiting time)
-    const double my_tau = quotient(rr.E, my_a0);  // a0 == 0: +inf
+    // the event times in order (lane b: event b's waiting time; FP32 mode
+    // widens its event's a0 pair here, once per batch)
+    if constexpr (F32) my_a0 = __dadd_rn(widen(my_s), widen_signed(my_e));
+    const double my_tau = quotient(rr.E, lane < nrec ? my_a0 : 1.0);  // a0 == 0: +inf
     double tt = t;
     long long my_tb = 0;
     int K = 0;      // events kept
     int endf = -1;  // the trajectory ends: 0 past t_end, 1 max_events, 2 overflow
     for (int b = 0; b < nrec && endf < 0; ++b) {
       const double t_b = __dadd_rn(tt, __shfl_sync(kFullMask, my_tau, b));
+      const int j_b = __shfl_sync(kFullMask, my_j, b);
       const long long tb_b = obits(t_b);
       if (lane == b) my_tb = tb_b;
       if (tb_b > net.t_end_bits) {
@@ -402,6 +438,8 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
       } else {
         K = b + 1;
         tt = t_b;
+        hash = (hash ^ (unsigned long long)j_b) * kFnvPrime;  // the sequence hash, in order
+        hash = (hash ^ (unsigned long long)tb_b) * kFnvPrime;
         if ((long long)base + K == max_events) endf = 1;
       }
     }
@@ -412,66 +450,88 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
       for (int e = q0 + lane; e < q1; e += 32) xs[net.nu_idx[e]] -= net.nu_val[e];
       __syncwarp();
     }
-    // grid indices (lane b: event b's) and the sequence hash, in order
-    int my_k = k, kk = k;
-    for (int b = 0; b < K; ++b) {
-      const int j = __shfl_sync(kFullMask, my_j, b);
-      const long long tb_b = __shfl_sync(kFullMask, my_tb, b);
-      kk = grid_index_net(net, tb_b, kk);
-      if (lane == b) my_k = kk;
-      hash = (hash ^ (unsigned long long)j) * kFnvPrime;
-      hash = (hash ^ (unsigned long long)tb_b) * kFnvPrime;
-    }
-    // kept events, last first: the counts before each one (walking the state
-    // back), its difference sums and log records, the largest count
-    for (int b = K - 1; b >= 0; --b) {
-      const int j = __shfl_sync(kFullMask, my_j, b);
-      const long long tb_b = __shfl_sync(kFullMask, my_tb, b);
-      const int kb = __shfl_sync(kFullMask, my_k, b);
-      const int q0 = net.nu_ptr[j], q1 = net.nu_ptr[j + 1];
-      bool logged = false;
-      // an event with no net change still adds its time to the union: one
-      // record with v = 0 (species 0, no effect on the sums)
-      const int nrc = (q1 > q0) ? (q1 - q0) : 1;
-      if constexpr (LOG) {
-        logged = log_reserve(*lg, *lst, nrc);
-        if (logged && q1 == q0 && lane == 0) {
-          const unsigned long long slot = lst->base + (unsigned long long)lst->fill;
-          lg->key[slot] = (unsigned long long)tb_b;
-          lg->rec[slot] = LogRec{0, 0, 0};
-        }
-      }
-      for (int e = q0 + lane; e < q1; e += 32) {
-        const int s = net.nu_idx[e];
-        const int vv = net.nu_val[e];
-        const int xn = xs[s];
-        const int xo = xn - vv;
-        xs[s] = xo;
-        maxx = max(maxx, xn);
-        const long long d2 = (2 * (long long)xo + vv) * (long long)vv;
-        if (kb < net.G) {
-          atomicAdd(net.D1 + (size_t)kb * S + s, (unsigned long long)(long long)vv);
-          atomicAdd(net.D2 + (size_t)kb * S + s, (unsigned long long)d2);
-        }
-        if constexpr (LOG) {
-          if (logged) {
-            const unsigned long long slot = lst->base + (unsigned long long)(lst->fill + (e - q0));
-            lg->key[slot] = (unsigned long long)tb_b;
-            lg->rec[slot] = LogRec{s, vv, d2};
+    int kk = k;
+    if (fast) {
+      // lane b books kept event b: its grid index (searched from the batch's
+      // starting index), difference sums from the recorded pre-event counts,
+      // and the largest count; xs already holds the state after the kept events
+      int my_k = k;
+      if (lane < K) {
+        my_k = grid_index_net(net, my_tb, k);
+        const int q0 = net.nu_ptr[my_j], q1 = net.nu_ptr[my_j + 1];
+        for (int e = q0; e < q1; ++e) {
+          const int sp = net.nu_idx[e];
+          const int vv = net.nu_val[e];
+          const int xo = xrec[lane * kRecPerEvent + (e - q0)];
+          maxx = max(maxx, xo + vv);
+          if (my_k < net.G) {
+            atomicAdd(net.D1 + (size_t)my_k * S + sp, (unsigned long long)(long long)vv);
+            atomicAdd(net.D2 + (size_t)my_k * S + sp,
+                      (unsigned long long)((2 * (long long)xo + vv) * (long long)vv));
           }
         }
       }
-      if constexpr (LOG) {
-        if (logged) lst->fill += nrc;
+      kk = __shfl_sync(kFullMask, my_k, max(K - 1, 0));
+      __syncwarp();
+    } else {
+      // grid indices (lane b: event b's), in order
+      int my_k = k;
+      for (int b = 0; b < K; ++b) {
+        const long long tb_b = __shfl_sync(kFullMask, my_tb, b);
+        kk = grid_index_net(net, tb_b, kk);
+        if (lane == b) my_k = kk;
       }
-      __syncwarp();
-    }
-    // and forward again to the state after the kept events
-    for (int b = 0; b < K; ++b) {
-      const int j = __shfl_sync(kFullMask, my_j, b);
-      const int q0 = net.nu_ptr[j], q1 = net.nu_ptr[j + 1];
-      for (int e = q0 + lane; e < q1; e += 32) xs[net.nu_idx[e]] += net.nu_val[e];
-      __syncwarp();
+      // kept events, last first: the counts before each one (walking the state
+      // back), its difference sums and log records, the largest count
+      for (int b = K - 1; b >= 0; --b) {
+        const int j = __shfl_sync(kFullMask, my_j, b);
+        const long long tb_b = __shfl_sync(kFullMask, my_tb, b);
+        const int kb = __shfl_sync(kFullMask, my_k, b);
+        const int q0 = net.nu_ptr[j], q1 = net.nu_ptr[j + 1];
+        bool logged = false;
+        // an event with no net change still adds its time to the union: one
+        // record with v = 0 (species 0, no effect on the sums)
+        const int nrc = (q1 > q0) ? (q1 - q0) : 1;
+        if constexpr (LOG) {
+          logged = log_reserve(*lg, *lst, nrc);
+          if (logged && q1 == q0 && lane == 0) {
+            const unsigned long long slot = lst->base + (unsigned long long)lst->fill;
+            lg->key[slot] = (unsigned long long)tb_b;
+            lg->rec[slot] = LogRec{0, 0, 0};
+          }
+        }
+        for (int e = q0 + lane; e < q1; e += 32) {
+          const int sp = net.nu_idx[e];
+          const int vv = net.nu_val[e];
+          const int xn = xs[sp];
+          const int xo = xn - vv;
+          xs[sp] = xo;
+          maxx = max(maxx, xn);
+          const long long d2 = (2 * (long long)xo + vv) * (long long)vv;
+          if (kb < net.G) {
+            atomicAdd(net.D1 + (size_t)kb * S + sp, (unsigned long long)(long long)vv);
+            atomicAdd(net.D2 + (size_t)kb * S + sp, (unsigned long long)d2);
+          }
+          if constexpr (LOG) {
+            if (logged) {
+              const unsigned long long slot = lst->base + (unsigned long long)(lst->fill + (e - q0));
+              lg->key[slot] = (unsigned long long)tb_b;
+              lg->rec[slot] = LogRec{sp, vv, d2};
+            }
+          }
+        }
+        if constexpr (LOG) {
+          if (logged) lst->fill += nrc;
+        }
+        __syncwarp();
+      }
+      // and forward again to the state after the kept events
+      for (int b = 0; b < K; ++b) {
+        const int j = __shfl_sync(kFullMask, my_j, b);
+        const int q0 = net.nu_ptr[j], q1 = net.nu_ptr[j + 1];
+        for (int e = q0 + lane; e < q1; e += 32) xs[net.nu_idx[e]] += net.nu_val[e];
+        __syncwarp();
+      }
     }
     if (K > 0) {
       t = tt;
