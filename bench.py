@@ -780,6 +780,8 @@ def run_batch(args):
             m.close()
         return None
     threads, split, tune_ms = batch.tune()
+    scheds = [batch.network_stats(b).schedule for b in range(len(ws))]
+    sched_counts = {"thread": scheds.count(1), "warp": scheds.count(2)}
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     for i in range(args.warmup):
         batch.launch(1 + i, stats=False)
@@ -846,7 +848,8 @@ def run_batch(args):
             "dtype": "f32-propensities/f64-time", "data": "synthetic",
             "config": {"workload": spec["name"], "networks": len(ws), "n_traj_total": int(sum(n_traj)),
                        "traj_div": args.batch_div, "n_grid": 501, "t_end": 10.0, "precision": "fp32-propensities",
-                       "launch": {"block_threads": threads, "split_by_bucket": split, "tune_sample_ms": tune_ms},
+                       "launch": {"block_threads": threads, "split_by_bucket": split, "tune_sample_ms": tune_ms,
+                                  "schedules": sched_counts},
                        "l2": "flushed between timed steps (256 MiB write outside the step events)",
                        "parallelism": f"replicas x{world} (trajectory-id shards)"},
             "traj_per_s": world * sum(n_traj) / (total_ms * 1e-3 / K),

@@ -134,6 +134,8 @@ typedef struct ssa_run_stats {
   int64_t overflowed;   /* trajectories stopped by SSA_STATE_MAX */
   int64_t max_x;        /* largest count seen in any trajectory */
   double kernel_ms;     /* device time of the simulation + reduction kernels */
+  int32_t schedule;     /* SSA_SCHED_THREAD or SSA_SCHED_WARP: the schedule that ran (for a
+                           whole batch SSA_SCHED_AUTO; per network see ssa_batch_network_stats) */
 } ssa_run_stats;
 
 /* Text for a status code (static storage). */
@@ -362,10 +364,13 @@ ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n_traj, doub
  * graph is captured at the first launch and replayed for every seed.
  *
  * Network b runs n_traj[b] trajectories with ids opts->traj_offset + i and
- * Philox stream id (fourth counter word) opts->stream_id + b, one trajectory
- * per warp (schedule W32) in opts->precision.  Its results are bit-identical
- * to ssa_ensemble_run of that network alone with schedule SSA_SCHED_WARP and
- * stream_id = opts->stream_id + b; they do not depend on the launch shape.
+ * Philox stream id (fourth counter word) opts->stream_id + b in
+ * opts->precision, on one schedule: one trajectory per warp (W32, any
+ * network) or one per thread (L, FP64 networks of at most 16 reactions and
+ * 16 species without rate modifiers), each on its own branch of the graph.
+ * Its results are bit-identical to ssa_ensemble_run of that network alone
+ * with that schedule and stream_id = opts->stream_id + b; they do not depend
+ * on the launch shape.  ssa_batch_network_stats reports the schedule.
  */
 typedef struct ssa_batch ssa_batch; /* opaque, owned by the library */
 
@@ -380,8 +385,13 @@ typedef struct ssa_batch ssa_batch; /* opaque, owned by the library */
  * opts (NULL for defaults): precision, max_events, traj_offset, stream_id
  * (stream_id + n_models <= 2^32), cuda_stream (where launches run), memory
  * (where ssa_batch_launch's output buffers live), block_threads (0 = 128
- * until ssa_batch_tune picks; else 64, 128 or 256).  schedule must be AUTO or
- * WARP.  Allocates one device slab for every network's grid, tables,
+ * until ssa_batch_tune picks; else 64, 128 or 256), schedule: AUTO (networks
+ * that fit the thread schedule start on it, as in ssa_ensemble_run, until
+ * ssa_batch_tune times both schedules per network and keeps the faster),
+ * WARP (every network per warp) or THREAD (every network per thread; each
+ * must fit it, else SSA_EUNSUPPORTED); WARP and THREAD are not changed by
+ * the tuner.  FP32 batches run the warp schedule (the thread schedule is
+ * FP64).  Allocates one device slab for every network's grid, tables,
  * difference sums and results; synchronous.
  * Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA, SSA_EUNSUPPORTED.
  */
@@ -390,13 +400,16 @@ ssa_status ssa_batch_create(int32_t n_models, const ssa_model* const* models, co
                             const ssa_run_opts* opts, ssa_batch** out);
 
 /*
- * Autotuner: times every launch shape (block size 64, 128 or 256; one kernel
- * per register bucket or one kernel for all) on a sample of the batch (the
- * first ceil(n_traj[b] / 8) trajectories of every network), keeps the
- * fastest and reports it (each output pointer may be NULL): block_threads,
- * split (1 = one kernel per bucket), sample_ms (device time of the chosen
- * shape on the sample).  Results of later launches are unchanged by it.
- * Synchronous.
+ * Autotuner, on a sample of the batch (the first ceil(n_traj[b] / 8)
+ * trajectories of every network).  First, under schedule AUTO, every network
+ * that fits both schedules is timed alone on each and keeps the faster (the
+ * choice is recorded: ssa_batch_network_stats reports it, and later launches
+ * reproduce its results exactly).  Then every launch shape of the warp
+ * kernels (block size 64, 128 or 256; one kernel per register bucket or one
+ * kernel for all) is timed and the fastest kept, which leaves results
+ * unchanged.  Reports (each output pointer may be NULL): block_threads, split
+ * (1 = one kernel per bucket), sample_ms (device time of the chosen shape on
+ * the sample).  Synchronous.
  */
 ssa_status ssa_batch_tune(ssa_batch* batch, int32_t* block_threads, int32_t* split, double* sample_ms);
 
@@ -421,7 +434,8 @@ ssa_status ssa_batch_result(const ssa_batch* batch, int32_t index, const double*
                             const int64_t** sum1, const int64_t** sum2);
 
 /* Totals of network `index` (events, truncated, overflowed, max_x) from the
- * last launch that waited for the stream; kernel_ms is 0. */
+ * last launch that waited for the stream, and the schedule it runs on
+ * (SSA_SCHED_THREAD or SSA_SCHED_WARP); kernel_ms is 0. */
 ssa_status ssa_batch_network_stats(const ssa_batch* batch, int32_t index, ssa_run_stats* out);
 
 /* Releases a batch.  NULL is ignored.  No launch of it may be pending. */

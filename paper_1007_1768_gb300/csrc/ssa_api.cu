@@ -565,6 +565,7 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
   a.N = n_traj;
   a.traj_offset = o.traj_offset;
   a.seed = seed;
+  a.seed_word = nullptr;
   a.stream_id = o.stream_id;
   a.max_events = max_events;
   a.t_end = t_end;
@@ -632,6 +633,7 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
     stats->overflowed = (int64_t)hstats[kStatOverflowed];
     stats->max_x = (int64_t)hstats[kStatMaxX];
     stats->kernel_ms = ms;
+    stats->schedule = use_warp ? SSA_SCHED_WARP : SSA_SCHED_THREAD;
   }
   if (hstats[kStatOverflowed] > 0)
     return fail(SSA_EOVERFLOW, "%llu trajectories stopped at the int32 state limit", hstats[kStatOverflowed]);

@@ -636,6 +636,7 @@ extern "C" ssa_status ssa_ensemble_avg_xy(const ssa_model* model, int64_t n_traj
     a.N = n_traj;
     a.traj_offset = o.traj_offset;
     a.seed = seed;
+    a.seed_word = nullptr;
     a.stream_id = o.stream_id;
     a.max_events = o.max_events;
     a.t_end = t_end;

@@ -188,13 +188,36 @@ struct ssa_batch {
   std::vector<int64_t> N;
   std::vector<int32_t> G, S, M;
   std::vector<double> t_end;
-  std::vector<int> order;  // position -> network index
+  std::vector<int> order;  // position -> network index (warp-schedule networks first)
   std::vector<int> pos;    // network index -> position
+  // schedules (SSA_SCHED_THREAD / SSA_SCHED_WARP) by network index; networks
+  // that fit the thread kernel (FP64, at most 16 reactions and species, no
+  // rate modifiers) may take either, which ssa_batch_tune decides by timing
+  // unless opts->schedule fixed it
+  std::vector<int> sched;
+  std::vector<char> thread_ok;
+  bool sched_fixed = false;
+  int n_warp = 0;          // positions [0, n_warp) run on the warp schedule
+  int smem_optin = 0;
+  // per network index: the warp layout's descriptor and finalisation entry
+  // (slab pointers), the device tables and the small-network tables
+  std::vector<WarpNet> wnets;
+  std::vector<FinalizeNet> fnets;
+  std::vector<DevModel> dms;
+  std::vector<SmallModelCopy> smalls;
+  // thread-schedule networks by position - n_warp: launch arguments for the
+  // full run and for the tuner's sample, with their launch shapes
+  struct ThreadNet {
+    RunArgs full, sample;
+    LaunchPlan plan_full, plan_sample;
+  };
+  std::vector<ThreadNet> tnets;
   // device slab and the offsets of each network's pieces (by network index)
   unsigned char* slab = nullptr;
   std::vector<size_t> off_grid, off_d1, off_d2, off_mean, off_var, off_s1, off_s2, off_depw, off_c32;
   size_t off_nets = 0, off_fin = 0, off_cta = 0, off_work = 0, off_work_sample = 0, off_counters = 0,
          off_stats = 0, off_seed = 0, zero_begin = 0, zero_bytes = 0;
+  static constexpr int kGroupCounters = 32;  // counters of the warp groups; thread networks follow
   int total_ctas = 0, max_G = 0;
   // launch plan
   int threads = 128;
@@ -244,32 +267,47 @@ ssa_status plan_groups(ssa_batch* b) {
     b->groups.push_back(g);
     return SSA_OK;
   };
+  // warp-schedule networks only (positions [0, n_warp))
+  const int nw = b->n_warp;
+  if (nw == 0) return SSA_OK;
   if (b->split) {
     int p = 0;
-    while (p < b->n) {
+    while (p < nw) {
       const int bk = bucket_of(b->M[b->order[p]]);
       int q = p;
-      while (q < b->n && bucket_of(b->M[b->order[q]]) == bk) ++q;
+      while (q < nw && bucket_of(b->M[b->order[q]]) == bk) ++q;
       const ssa_status st = add(bk, p, q);
       if (st != SSA_OK) return st;
       p = q;
     }
   } else {
     int bk = 1;
-    for (int i = 0; i < b->n; ++i) bk = std::max(bk, bucket_of(b->M[i]));
-    const ssa_status st = add(bk, 0, b->n);
+    for (int p = 0; p < nw; ++p) bk = std::max(bk, bucket_of(b->M[b->order[p]]));
+    const ssa_status st = add(bk, 0, nw);
     if (st != SSA_OK) return st;
   }
   return SSA_OK;
 }
 
-// Enqueues one full pass (zeroing, simulation, finalisation) on `st`, the
-// groups on the fork streams.  sample: use the sample work ranges.
+// Enqueues one full pass (zeroing, simulation, finalisation) on `st`: the
+// warp groups and the thread-schedule networks each on a fork stream.
+// sample: the tuner's sample (the first ceil(N / 8) trajectories of each
+// network, no finalisation).
 ssa_status enqueue_pass(ssa_batch* b, cudaStream_t st, bool sample) {
   unsigned char* s = b->slab;
   SSA_B_TRY(cudaMemsetAsync(s + b->zero_begin, 0, b->zero_bytes, st));
   const int ng = (int)b->groups.size();
+  const int nt = (int)b->tnets.size();
   SSA_B_TRY(cudaEventRecord(b->evs[0], st));
+  for (int t = 0; t < nt; ++t) {
+    const ssa_batch::ThreadNet& tn = b->tnets[t];
+    const LaunchPlan& pl = sample ? tn.plan_sample : tn.plan_full;
+    cudaStream_t fs = b->forks[ng + t];
+    SSA_B_TRY(cudaStreamWaitEvent(fs, b->evs[0], 0));
+    SSA_B_TRY(launch_thread_kernel(sample ? tn.sample : tn.full, pl.blocks, pl.threads, false, pl.smem, fs));
+    SSA_B_TRY(cudaEventRecord(b->evs[1 + ng + t], fs));
+    SSA_B_TRY(cudaStreamWaitEvent(st, b->evs[1 + ng + t], 0));
+  }
   for (int g = 0; g < ng; ++g) {
     const ssa_batch::Group& gr = b->groups[g];
     cudaStream_t fs = b->forks[g];
@@ -296,7 +334,7 @@ ssa_status enqueue_pass(ssa_batch* b, cudaStream_t st, bool sample) {
 }
 
 ssa_status ensure_streams(ssa_batch* b) {
-  const size_t need = b->groups.size();
+  const size_t need = b->groups.size() + b->tnets.size();
   if (!b->cap) SSA_B_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
   while (b->forks.size() < need) {
     cudaStream_t f;
@@ -344,6 +382,150 @@ ssa_status set_seed(ssa_batch* b, uint64_t seed, cudaStream_t st) {
   return SSA_OK;
 }
 
+// The thread-schedule launches of network i (full run and the tuner's
+// sample), with the counter kGroupCounters + p and the stats slot of
+// position p, and their launch shapes.
+ssa_status thread_net(ssa_batch* b, int i, int p, ssa_batch::ThreadNet* tn) {
+  const int div = 8;
+  unsigned char* s = b->slab;
+  const WarpNet& w = b->wnets[i];
+  RunArgs& a = tn->full;
+  a.sm = b->smalls[i].small;
+  a.m = b->dms[i];
+  a.G = b->G[i];
+  a.N = b->N[i];
+  a.traj_offset = b->opts.traj_offset;
+  a.seed = 0;
+  a.seed_word = reinterpret_cast<const unsigned long long*>(s + b->off_seed);
+  a.stream_id = b->opts.stream_id + (uint64_t)i;
+  a.max_events = b->opts.max_events;
+  a.t_end = b->t_end[i];
+  a.grid = w.grid;
+  a.D1 = w.D1;
+  a.D2 = w.D2;
+  a.counter = reinterpret_cast<unsigned long long*>(s + b->off_counters) + ssa_batch::kGroupCounters + p;
+  a.stats = reinterpret_cast<unsigned long long*>(s + b->off_stats) + 4 * (size_t)p;
+  a.traj_events = nullptr;
+  a.traj_hash = nullptr;
+  a.traj_flags = nullptr;
+  a.device_totals = nullptr;
+  a.grid_uniform = w.grid_uniform;
+  a.grid_scale = w.grid_scale;
+  a.grid_margin = w.grid_margin;
+  tn->sample = a;
+  tn->sample.N = (b->N[i] + div - 1) / div;
+  const char* msg = plan_thread_launch(b->S[i], b->M[i], b->G[i], tn->full.N, b->sms, (size_t)b->smem_optin,
+                                       SSA_REDUCE_GLOBAL, 0, 0, &tn->plan_full);
+  if (!msg)
+    msg = plan_thread_launch(b->S[i], b->M[i], b->G[i], tn->sample.N, b->sms, (size_t)b->smem_optin,
+                             SSA_REDUCE_GLOBAL, 0, 0, &tn->plan_sample);
+  if (msg) return (ssa_status)set_error(SSA_EUNSUPPORTED, msg);
+  SSA_B_TRY(thread_kernel_set_smem(b->M[i], b->S[i], false, std::max(tn->plan_full.smem, tn->plan_sample.smem)));
+  return SSA_OK;
+}
+
+// Device time of network i's sample on one schedule alone (the second of two
+// passes; the first warms up), on the capture stream.
+ssa_status time_schedule(ssa_batch* b, int i, bool thread, double* ms_out) {
+  const int p = b->pos[i];
+  unsigned char* s = b->slab;
+  ssa_batch::ThreadNet tn;
+  BatchLaunch L;
+  int blocks = 0;
+  size_t smem = 0;
+  if (thread) {
+    const ssa_status st = thread_net(b, i, p, &tn);
+    if (st != SSA_OK) return st;
+  } else {
+    L.nets = reinterpret_cast<const BatchNetDev*>(s + b->off_nets);
+    L.work_begin = reinterpret_cast<const long long*>(s + b->off_work_sample);
+    L.pos_lo = p;
+    L.pos_hi = p + 1;
+    L.counter = reinterpret_cast<unsigned long long*>(s + b->off_counters) + (ssa_batch::kGroupCounters - 1);
+    L.stats = reinterpret_cast<unsigned long long*>(s + b->off_stats);
+    L.seed = reinterpret_cast<const unsigned long long*>(s + b->off_seed);
+    L.traj_offset = b->opts.traj_offset;
+    L.max_events = b->opts.max_events;
+    L.smax = std::max(1, b->S[i]);
+    smem = batch_smem(b->threads, L.smax);
+    int per_sm = 0;
+    SSA_B_TRY(batch_kernel(b->fp32, bucket_of(b->M[i]), false, nullptr, 0, b->threads, smem, nullptr, &per_sm));
+    if (per_sm < 1) return (ssa_status)set_error(SSA_EUNSUPPORTED, "batch kernel cannot be resident with this shape");
+    blocks = b->sms * per_sm;
+  }
+  float ms = 0.f;
+  for (int rep = 0; rep < 2; ++rep) {
+    SSA_B_TRY(cudaMemsetAsync(s + b->zero_begin, 0, b->zero_bytes, b->cap));
+    SSA_B_TRY(cudaEventRecord(b->t0, b->cap));
+    if (thread) {
+      SSA_B_TRY(launch_thread_kernel(tn.sample, tn.plan_sample.blocks, tn.plan_sample.threads, false,
+                                     tn.plan_sample.smem, b->cap));
+    } else {
+      SSA_B_TRY(batch_kernel(b->fp32, bucket_of(b->M[i]), true, &L, blocks, b->threads, smem, b->cap, nullptr));
+    }
+    SSA_B_TRY(cudaEventRecord(b->t1, b->cap));
+    SSA_B_TRY(cudaEventSynchronize(b->t1));
+    SSA_B_TRY(cudaEventElapsedTime(&ms, b->t0, b->t1));
+  }
+  *ms_out = ms;
+  return SSA_OK;
+}
+
+// Orders the networks -- warp-schedule ones first, by register bucket and M
+// descending (the costliest steps first, so that in one kernel for all
+// networks the largest networks' trajectories do not start last), then
+// thread-schedule ones, most trajectories first -- writes the by-position
+// descriptor tables into the slab and prepares the thread-schedule launches
+// (network i uses the counter kGroupCounters + its position and its stats
+// slot).  Synchronous.
+ssa_status upload_tables(ssa_batch* b) {
+  const int n = b->n;
+  b->order.resize(n);
+  for (int i = 0; i < n; ++i) b->order[i] = i;
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+    const bool tx = b->sched[x] == SSA_SCHED_THREAD, ty = b->sched[y] == SSA_SCHED_THREAD;
+    if (tx != ty) return !tx;
+    if (tx) return b->N[x] > b->N[y];
+    const int bx = bucket_of(b->M[x]), by = bucket_of(b->M[y]);
+    if (bx != by) return bx > by;
+    return b->M[x] > b->M[y];
+  });
+  b->pos.resize(n);
+  b->n_warp = 0;
+  for (int p = 0; p < n; ++p) {
+    b->pos[b->order[p]] = p;
+    if (b->sched[b->order[p]] != SSA_SCHED_THREAD) ++b->n_warp;
+  }
+  std::vector<BatchNetDev> nets(n);
+  std::vector<FinalizeNet> fin(n);
+  std::vector<int> cta(n + 1, 0);
+  std::vector<long long> work(n + 1, 0), work_s(n + 1, 0);
+  const int div = 8;
+  unsigned char* s = b->slab;
+  b->tnets.clear();
+  for (int p = 0; p < n; ++p) {
+    const int i = b->order[p];
+    nets[p].net = b->wnets[i];
+    nets[p].N = b->N[i];
+    fin[p] = b->fnets[i];
+    work[p + 1] = work[p] + b->N[i];
+    work_s[p + 1] = work_s[p] + (b->N[i] + div - 1) / div;
+    cta[p + 1] = cta[p] + b->S[i];
+    if (b->sched[i] != SSA_SCHED_THREAD) continue;
+    ssa_batch::ThreadNet tn;
+    const ssa_status st = thread_net(b, i, p, &tn);
+    if (st != SSA_OK) return st;
+    b->tnets.push_back(tn);
+  }
+  SSA_B_TRY(cudaMemcpy(s + b->off_nets, nets.data(), sizeof(BatchNetDev) * n, cudaMemcpyHostToDevice));
+  SSA_B_TRY(cudaMemcpy(s + b->off_fin, fin.data(), sizeof(FinalizeNet) * n, cudaMemcpyHostToDevice));
+  SSA_B_TRY(cudaMemcpy(s + b->off_cta, cta.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+  SSA_B_TRY(cudaMemcpy(s + b->off_work, work.data(), 8 * (size_t)(n + 1), cudaMemcpyHostToDevice));
+  SSA_B_TRY(cudaMemcpy(s + b->off_work_sample, work_s.data(), 8 * (size_t)(n + 1), cudaMemcpyHostToDevice));
+  SSA_B_TRY(cudaDeviceSynchronize());
+  return SSA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -360,8 +542,7 @@ ssa_status ssa_batch_create(int32_t n_models, const ssa_model* const* models, co
   if (o.precision != SSA_PREC_FP64 && o.precision != SSA_PREC_FP32)
     return (ssa_status)set_error(SSA_EINVAL, "bad precision");
   if (o.memory != SSA_MEM_HOST && o.memory != SSA_MEM_DEVICE) return (ssa_status)set_error(SSA_EINVAL, "bad memory kind");
-  if (o.schedule == SSA_SCHED_THREAD)
-    return (ssa_status)set_error(SSA_EUNSUPPORTED, "batches run one trajectory per warp (schedule W32)");
+  if (o.schedule < SSA_SCHED_AUTO || o.schedule > SSA_SCHED_WARP) return (ssa_status)set_error(SSA_EINVAL, "bad schedule");
   if (o.block_threads != 0 && o.block_threads != 64 && o.block_threads != 128 && o.block_threads != 256)
     return (ssa_status)set_error(SSA_EINVAL, "batch block_threads must be 0, 64, 128 or 256");
   if (o.max_events <= 0) o.max_events = SSA_DEFAULT_MAX_EVENTS;
@@ -410,28 +591,30 @@ ssa_status ssa_batch_create(int32_t n_models, const ssa_model* const* models, co
     b->M.push_back(M);
     b->t_end.push_back(t_end[i]);
   }
+  // schedules: networks that fit the thread kernel start on it under AUTO
+  // (the rule of ssa_ensemble_run), until ssa_batch_tune times both
+  const int n = n_models;
+  b->sched.assign(n, SSA_SCHED_WARP);
+  b->thread_ok.assign(n, 0);
+  b->smalls.resize(n);
+  b->sched_fixed = o.schedule != SSA_SCHED_AUTO;
+  for (int i = 0; i < n; ++i) {
+    model_small_copy(b->models[i], &b->smalls[i]);
+    b->thread_ok[i] = (!b->fp32 && b->smalls[i].has_small) ? 1 : 0;
+    if (o.schedule == SSA_SCHED_THREAD && !b->thread_ok[i])
+      return bail(set_error(SSA_EUNSUPPORTED, "the thread schedule takes FP64 networks of at most 16 reactions and "
+                                              "16 species without rate modifiers"));
+    if (o.schedule != SSA_SCHED_WARP && b->thread_ok[i]) b->sched[i] = SSA_SCHED_THREAD;
+  }
   cudaError_t e = cudaGetDevice(&b->dev);
   if (e != cudaSuccess) return bail(set_error(SSA_ECUDA, cudaGetErrorString(e)));
   cudaDeviceProp prop;
   e = cudaGetDeviceProperties(&prop, b->dev);
   if (e != cudaSuccess) return bail(set_error(SSA_ECUDA, cudaGetErrorString(e)));
   b->sms = prop.multiProcessorCount;
+  b->smem_optin = (int)prop.sharedMemPerBlockOptin;
 
-  // launch order: bucket descending, then M descending, then index -- the
-  // costliest steps first, so that in one kernel for all networks the
-  // largest networks' trajectories do not start last and end the launch
-  const int n = n_models;
-  b->order.resize(n);
-  for (int i = 0; i < n; ++i) b->order[i] = i;
-  std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
-    const int bx = bucket_of(b->M[x]), by = bucket_of(b->M[y]);
-    if (bx != by) return bx > by;
-    return b->M[x] > b->M[y];
-  });
-  b->pos.resize(n);
-  for (int p = 0; p < n; ++p) b->pos[b->order[p]] = p;
-
-  // slab layout
+  // slab layout (pieces by network index)
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t at = off;
@@ -465,7 +648,7 @@ ssa_status ssa_batch_create(int32_t n_models, const ssa_model* const* models, co
   }
   // everything from here on is zeroed before every pass
   b->zero_begin = off;
-  b->off_counters = take(8 * 32);
+  b->off_counters = take(8 * (size_t)(ssa_batch::kGroupCounters + n));
   b->off_stats = take(8 * 4 * (size_t)n);
   for (int i = 0; i < n; ++i) {
     const size_t gs = (size_t)b->G[i] * b->S[i];
@@ -476,15 +659,12 @@ ssa_status ssa_batch_create(int32_t n_models, const ssa_model* const* models, co
   e = cudaMalloc(reinterpret_cast<void**>(&b->slab), off);
   if (e != cudaSuccess) return bail(set_error(SSA_ENOMEM, cudaGetErrorString(e)));
 
-  // tables, grids and descriptors
-  std::vector<BatchNetDev> nets(n);
-  std::vector<FinalizeNet> fin(n);
-  std::vector<int> cta(n + 1, 0);
-  std::vector<long long> work(n + 1, 0), work_s(n + 1, 0);
-  const int div = 8;
-  for (int p = 0; p < n; ++p) {
-    const int i = b->order[p];
-    DevModel dm;
+  // per network: device tables, derived tables, grid, descriptors
+  b->wnets.resize(n);
+  b->fnets.resize(n);
+  b->dms.resize(n);
+  for (int i = 0; i < n; ++i) {
+    DevModel& dm = b->dms[i];
     int st = model_device_tables(b->models[i], b->dev, &dm);
     if (st != SSA_OK) return bail(st);
     unsigned char* s = b->slab;
@@ -500,7 +680,7 @@ ssa_status ssa_batch_create(int32_t n_models, const ssa_model* const* models, co
       e = launch_uniform_grid(dgrid, b->G[i], b->t_end[i], nullptr);
     }
     if (e != cudaSuccess) return bail(set_error(SSA_ECUDA, cudaGetErrorString(e)));
-    WarpNet& w = nets[p].net;
+    WarpNet& w = b->wnets[i];
     w.rinfo = dm.rinfo;
     w.cbits = reinterpret_cast<const unsigned long long*>(dm.c);
     w.c32 = reinterpret_cast<const float*>(s + b->off_c32[i]);
@@ -527,10 +707,7 @@ ssa_status ssa_batch_create(int32_t n_models, const ssa_model* const* models, co
     w.grid_scale = (float)((double)(b->G[i] - 1) / te);
     w.grid_margin = (float)((double)b->G[i] * 0x1p-21);
     w.sid = (uint32_t)(o.stream_id + (uint64_t)i);
-    nets[p].N = b->N[i];
-    work[p + 1] = work[p] + b->N[i];
-    work_s[p + 1] = work_s[p] + (b->N[i] + div - 1) / div;
-    FinalizeNet& f = fin[p];
+    FinalizeNet& f = b->fnets[i];
     f.D1 = w.D1;
     f.D2 = w.D2;
     f.x0 = dm.x0;
@@ -541,19 +718,11 @@ ssa_status ssa_batch_create(int32_t n_models, const ssa_model* const* models, co
     f.G = b->G[i];
     f.S = b->S[i];
     f.N = b->N[i];
-    cta[p + 1] = cta[p] + b->S[i];
     b->max_G = std::max(b->max_G, b->G[i]);
   }
-  b->total_ctas = cta[n];
-  unsigned char* s = b->slab;
-  if ((e = cudaMemcpy(s + b->off_nets, nets.data(), sizeof(BatchNetDev) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(s + b->off_fin, fin.data(), sizeof(FinalizeNet) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(s + b->off_cta, cta.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(s + b->off_work, work.data(), 8 * (size_t)(n + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(s + b->off_work_sample, work_s.data(), 8 * (size_t)(n + 1), cudaMemcpyHostToDevice)) !=
-          cudaSuccess ||
-      (e = cudaDeviceSynchronize()) != cudaSuccess)
-    return bail(set_error(SSA_ECUDA, cudaGetErrorString(e)));
+  for (int i = 0; i < n; ++i) b->total_ctas += b->S[i];
+  ssa_status ust = upload_tables(b);
+  if (ust != SSA_OK) return bail(ust);
 
   b->threads = o.block_threads ? o.block_threads : 128;
   b->split = true;
@@ -573,6 +742,26 @@ ssa_status ssa_batch_tune(ssa_batch* b, int32_t* block_threads, int32_t* split, 
   int best_t = b->threads;
   bool best_split = b->split;
   ssa_status st = SSA_OK;
+  // thread versus warp for every network that fits both (unless opts fixed
+  // the schedule): each timed alone on its sample, the faster kept and
+  // recorded; the batch's results then follow the recorded schedules
+  if (!b->sched_fixed) {
+    bool any = false;
+    for (int i = 0; i < b->n; ++i) any = any || b->thread_ok[i];
+    if (any) {
+      if ((st = ensure_streams(b)) != SSA_OK) return st;
+      if ((st = set_seed(b, 0x5eedULL ^ 0xA5A5A5A5ULL, b->cap)) != SSA_OK) return st;
+      for (int i = 0; i < b->n; ++i) {
+        if (!b->thread_ok[i]) continue;
+        double t_thread = 0.0, t_warp = 0.0;
+        if ((st = time_schedule(b, i, true, &t_thread)) != SSA_OK) return st;
+        if ((st = time_schedule(b, i, false, &t_warp)) != SSA_OK) return st;
+        b->sched[i] = (t_thread <= t_warp) ? SSA_SCHED_THREAD : SSA_SCHED_WARP;
+      }
+      if ((st = upload_tables(b)) != SSA_OK) return st;
+      drop_graph(b);
+    }
+  }
   for (int sp = 0; sp < 2; ++sp) {
     for (int ti = 0; ti < 3; ++ti) {
       b->threads = cand_threads[ti];
@@ -650,6 +839,9 @@ ssa_status ssa_batch_launch(ssa_batch* b, uint64_t seed, double* const* means, d
     stats->overflowed = (int64_t)ov;
     stats->max_x = (int64_t)mx;
     stats->kernel_ms = ms;
+    int common = b->sched[0];
+    for (int i = 1; i < b->n; ++i) common = (b->sched[i] == common) ? common : SSA_SCHED_AUTO;
+    stats->schedule = common;
   }
   if (bad >= 0) {
     char msg[128];
@@ -678,6 +870,7 @@ ssa_status ssa_batch_network_stats(const ssa_batch* b, int32_t index, ssa_run_st
   out->overflowed = (int64_t)h[2];
   out->max_x = (int64_t)h[3];
   out->kernel_ms = 0.0;
+  out->schedule = b->sched[index];
   return SSA_OK;
 }
 

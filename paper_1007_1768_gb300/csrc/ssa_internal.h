@@ -71,6 +71,7 @@ struct RunArgs {
   int64_t N;
   uint64_t traj_offset;
   uint64_t seed;
+  const unsigned long long* seed_word;  // device word holding the seed (batch graphs), or null: use seed
   uint64_t stream_id;
   int64_t max_events;
   double t_end;

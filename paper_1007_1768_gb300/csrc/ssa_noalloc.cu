@@ -194,6 +194,7 @@ extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n
   a.N = n_traj;
   a.traj_offset = o.traj_offset;
   a.seed = seed;
+  a.seed_word = nullptr;
   a.stream_id = o.stream_id;
   a.max_events = (o.max_events > 0) ? o.max_events : SSA_DEFAULT_MAX_EVENTS;
   a.t_end = t_end;
@@ -233,6 +234,7 @@ extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n
   stats->overflowed = (int64_t)h[kStatOverflowed];
   stats->max_x = (int64_t)h[kStatMaxX];
   stats->kernel_ms = 0.0;
+  stats->schedule = SSA_SCHED_THREAD;
   if (h[kStatOverflowed] > 0) return record_error(SSA_EOVERFLOW, "a trajectory stopped at the int32 state limit");
   const long double bound = (long double)n_traj * (long double)h[kStatMaxX] * (long double)h[kStatMaxX];
   if (bound >= 9.2233720368547758e18L) return record_error(SSA_EOVERFLOW, "N * max_x^2 may exceed int64 sums");

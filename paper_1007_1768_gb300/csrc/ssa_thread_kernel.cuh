@@ -954,8 +954,9 @@ __global__ void __launch_bounds__(512, 1) k_ssa_thread(const RunArgs a, const Ev
   e.S = S;
   e.G = G;
   e.t_end_bits = obits(a.t_end);
-  e.key0 = (uint32_t)a.seed;
-  e.key1 = (uint32_t)(a.seed >> 32);
+  const uint64_t seed = a.seed_word ? (uint64_t)*a.seed_word : a.seed;
+  e.key0 = (uint32_t)seed;
+  e.key1 = (uint32_t)(seed >> 32);
   e.sid = (uint32_t)a.stream_id;
   e.s_inv = s_inv;
   e.s_lnf = s_lnf;

@@ -1,8 +1,9 @@
 """GPU checks of batched ensembles (ssa_batch_*): every network of a batch
-must give exactly the results of running it alone (ssa_ensemble_run, warp
-schedule, stream id = batch stream id + its index), whatever the launch
-shape the autotuner picks; the captured graph must replay correctly for new
-seeds; two networks are also checked against the oracle directly."""
+must give exactly the results of running it alone (ssa_ensemble_run in the
+schedule the batch reports for it, stream id = batch stream id + its index),
+whatever the launch shape and schedules the autotuner picks; the captured
+graph must replay correctly for new seeds; networks are also checked against
+the oracle directly in their recorded schedule."""
 import numpy as np
 import pytest
 
@@ -24,10 +25,14 @@ def _mixed():
     return nets, n, t_end, G
 
 
-def _alone(net, n, t_end, G, seed, stream_id, precision, grid=None, max_events=4000):
+SCHED_NAME = {1: "thread", 2: "warp"}
+ORACLE_SCHED = {1: oracle.SCHEDULE_L, 2: oracle.SCHEDULE_W32}
+
+
+def _alone(net, n, t_end, G, seed, stream_id, precision, grid=None, max_events=4000, schedule="warp"):
     model = ssa.Model.from_network(net)
     try:
-        r = ssa.ensemble_run(model, n, t_end, G, seed, grid=grid, schedule="warp", precision=precision,
+        r = ssa.ensemble_run(model, n, t_end, G, seed, grid=grid, schedule=schedule, precision=precision,
                              stream_id=stream_id, max_events=max_events)
     finally:
         model.close()
@@ -44,19 +49,28 @@ def test_batch_matches_each_network_alone(precision):
     batch = ssa.Batch(models, n, t_end, G, grids, precision=precision, max_events=4000, stream_id=3)
     outs, st = batch.launch(11, want_sums=True)
     total = 0
+    scheds = []
     for b, net in enumerate(nets):
-        r = _alone(net, n[b], t_end[b], G[b], 11, 3 + b, precision, grid=grids[b])
+        ns = batch.network_stats(b)
+        scheds.append(ns.schedule)
+        r = _alone(net, n[b], t_end[b], G[b], 11, 3 + b, precision, grid=grids[b], schedule=SCHED_NAME[ns.schedule])
+        assert r.schedule == ns.schedule
         for k in ("sum1", "sum2", "mean", "var"):
             assert np.array_equal(outs[b][k].view(np.int64), getattr(r, k).view(np.int64)), (b, k)
-        ns = batch.network_stats(b)
         assert ns.events == r.events and ns.max_x == r.max_x
         total += r.events
     assert st.events == total
+    # schedule AUTO before tuning: the rule of ssa_ensemble_run (the thread
+    # schedule for small FP64 networks; FP32 batches run every network per warp)
+    if precision == "fp64":
+        assert scheds == [1, 1, 2, 2, 1, 1, 2]
+    else:
+        assert scheds == [2] * len(nets)
     # two networks straight against the oracle (same schedule and precision)
     prec = oracle.PRECISION_FP32 if precision == "fp32" else oracle.PRECISION_FP64
     for b in (1, 3):
-        o = oracle.run(nets[b], n[b], t_end[b], G[b], 11, grid=grids[b], stream=3 + b, schedule=oracle.SCHEDULE_W32,
-                       precision=prec, max_events=4000, threads=16)
+        o = oracle.run(nets[b], n[b], t_end[b], G[b], 11, grid=grids[b], stream=3 + b,
+                       schedule=ORACLE_SCHED[scheds[b]], precision=prec, max_events=4000, threads=16)
         assert np.array_equal(outs[b]["sum1"], o.S1) and np.array_equal(outs[b]["sum2"], o.S2)
     batch.close()
     for m in models:
@@ -112,3 +126,45 @@ def test_uneven_256_network_batch_sampled():
     batch.close()
     for m in models:
         m.close()
+
+
+def test_tuner_picks_a_schedule_per_network_and_results_follow_it():
+    """FP64 batch: ssa_batch_tune times the thread and the warp schedule of
+    every network that fits both and records the faster; each network then
+    equals the oracle in its recorded schedule (L or W32), launches repeat
+    bit for bit, and fixed schedules are left alone by the tuner."""
+    nets, n, t_end, G = _mixed()
+    models = [ssa.Model.from_network(x) for x in nets]
+    fits = [True, True, False, False, True, True, False]  # at most 16 reactions and species
+    batch = ssa.Batch(models, n, t_end, G, precision="fp64", max_events=4000, stream_id=5)
+    threads, split, ms = batch.tune()
+    assert threads in (64, 128, 256) and ms > 0
+    outs, _ = batch.launch(21, want_sums=True)
+    again, _ = batch.launch(21, want_sums=True)
+    for b, net in enumerate(nets):
+        sched = batch.network_stats(b).schedule
+        assert sched in (1, 2) and (fits[b] or sched == 2), (b, sched)
+        o = oracle.run(net, n[b], t_end[b], G[b], 21, stream=5 + b, schedule=ORACLE_SCHED[sched],
+                       max_events=4000, threads=16, per_traj=True)
+        assert np.array_equal(outs[b]["sum1"], o.S1) and np.array_equal(outs[b]["sum2"], o.S2), (b, sched)
+        om, ov = oracle.finalize(n[b], o.S1, o.S2)
+        assert np.array_equal(outs[b]["mean"].view(np.int64), om.view(np.int64))
+        assert np.array_equal(again[b]["sum2"], outs[b]["sum2"])
+        assert batch.network_stats(b).events == o.events
+    batch.close()
+    # fixed schedules: every network per warp, or (small networks only) per thread
+    for sched, idx in (("warp", list(range(len(nets)))), ("thread", [0, 1, 4, 5])):
+        sub = [models[i] for i in idx]
+        fixed = ssa.Batch(sub, [n[i] for i in idx], [t_end[i] for i in idx], [G[i] for i in idx], precision="fp64",
+                          max_events=4000, stream_id=5, schedule=sched)
+        fixed.tune()
+        res, _ = fixed.launch(22, want_sums=True)
+        for q, i in enumerate(idx):
+            ns = fixed.network_stats(q)
+            assert SCHED_NAME[ns.schedule] == sched
+            r = _alone(nets[i], n[i], t_end[i], G[i], 22, 5 + q, "fp64", schedule=sched)
+            assert np.array_equal(res[q]["sum2"], r.sum2) and np.array_equal(res[q]["sum1"], r.sum1)
+        fixed.close()
+    for m in models:
+        m.close()
+

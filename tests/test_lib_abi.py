@@ -13,6 +13,7 @@ import pytest
 
 import paper_1007_1768_gb300 as ssa
 from paper_1007_1768_gb300 import binding
+import workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "ssa.h")
@@ -94,9 +95,10 @@ def test_struct_layout_matches_header():
 #include <stddef.h>
 #include "ssa.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(ssa_run_opts), offsetof(ssa_run_opts, max_events),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ssa_run_opts), offsetof(ssa_run_opts, max_events),
          offsetof(ssa_run_opts, cuda_stream), offsetof(ssa_run_opts, workspace_bytes),
-         offsetof(ssa_run_opts, traj_flags), sizeof(ssa_run_stats), offsetof(ssa_run_stats, kernel_ms));
+         offsetof(ssa_run_opts, traj_flags), sizeof(ssa_run_stats), offsetof(ssa_run_stats, kernel_ms),
+         offsetof(ssa_run_stats, schedule));
   return 0;
 }
 """
@@ -108,7 +110,7 @@ int main(void) {
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     R, S = binding.RunOpts, binding.RunStats
     assert vals == [ctypes.sizeof(R), R.max_events.offset, R.cuda_stream.offset, R.workspace_bytes.offset,
-                    R.traj_flags.offset, ctypes.sizeof(S), S.kernel_ms.offset]
+                    R.traj_flags.offset, ctypes.sizeof(S), S.kernel_ms.offset, S.schedule.offset]
 
 
 def test_host_run_rejects_bad_arguments_before_touching_the_gpu():
@@ -163,9 +165,22 @@ def test_batch_arguments_are_refused_before_touching_the_gpu():
     with pytest.raises(ssa.SSAError) as e:
         ssa.Batch([m, m], [10, 10], [1.0, 1.0], [11, 11], stream_id=(1 << 32) - 1)
     assert e.value.status == binding.SSA_EINVAL
+    # the thread schedule takes FP64 networks of at most 16 reactions and species only
     with pytest.raises(ssa.SSAError) as e:
-        ssa.Batch([m], [10], [1.0], [11], schedule="thread")
+        ssa.Batch([m], [10], [1.0], [11], schedule="thread", precision="fp32")
     assert e.value.status == binding.SSA_EUNSUPPORTED
+    big = ssa.Model.from_network(W.random_network(5, n_species=8, n_reactions=20))
+    with pytest.raises(ssa.SSAError) as e:
+        ssa.Batch([m, big], [10, 10], [1.0, 1.0], [11, 11], schedule="thread")
+    assert e.value.status == binding.SSA_EUNSUPPORTED
+    big.close()
+    bad = ssa.make_opts()
+    bad.schedule = 7
+    hp = binding._ptr_array([m.handle.value])
+    n, te, g = np.array([10], np.int64), np.array([1.0]), np.array([11], np.int32)
+    h = ctypes.c_void_p()
+    assert ssa.lib().ssa_batch_create(1, hp, n.ctypes.data, te.ctypes.data, g.ctypes.data, None, ctypes.byref(bad),
+                                      ctypes.byref(h)) == binding.SSA_EINVAL
     with pytest.raises(ssa.SSAError) as e:
         ssa.Batch([m], [0], [1.0], [11])
     assert e.value.status == binding.SSA_EINVAL
