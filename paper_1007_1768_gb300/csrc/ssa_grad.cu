@@ -82,6 +82,17 @@ __device__ __forceinline__ int grad_grid_index(const GradArgs& a, long long tb, 
 
 constexpr int kGradThreads = 128;
 
+// (double)v for any int64: exact integer bit assembly for |v| < 2^53 (the
+// counts, propensity factors and their changes met here), the hardware
+// conversion out of line otherwise.  Same bits as the conversion, without
+// issuing it on the SM's FP64 unit.
+__device__ __forceinline__ double int_to_f64(long long v) {
+  const unsigned long long mag = (v < 0) ? 0ULL - (unsigned long long)v : (unsigned long long)v;
+  double r = __longlong_as_double((long long)(small_int_to_f64_bits(mag) | (v < 0 ? (1ULL << 63) : 0ULL)));
+  if (__builtin_expect(mag >= (1ULL << 53), 0)) r = ll2double_rare(v);
+  return r;
+}
+
 // Per-thread score state in shared memory, slot (j, tid) at j * 128 + tid:
 // B_j, the gradient g_j, and the running interval sums at g_j's last update.
 struct GradSlots {
@@ -155,12 +166,12 @@ __global__ void __launch_bounds__(kGradThreads) k_ssa_grad(const GradArgs a) {
         const bool dj = j < M && ((dirty >> j) & 1u);
         if (dj || j == fired) {
           const int idx = j * T + tid;
-          flush_slot(sl, idx, __ll2double_rn(h[j]), SU, SUG);
+          flush_slot(sl, idx, int_to_f64(h[j]), SU, SUG);
           double Bj = sl.B[idx];
           if (j == fired) Bj = __dadd_rn(Bj, a.invc[j]);
           if (dj) {
             const long long hn = mass_action_h<MAXS>(a.sm.rinfo[j], x);
-            Bj = __dadd_rn(Bj, __dmul_rn(__ll2double_rn(hn - h[j]), t));
+            Bj = __dadd_rn(Bj, __dmul_rn(int_to_f64(hn - h[j]), t));
             h[j] = hn;
             av[j] = __longlong_as_double((long long)propensity_fp64(a.sm.cbits[j], hn));
           }
@@ -184,7 +195,7 @@ __global__ void __launch_bounds__(kGradThreads) k_ssa_grad(const GradArgs a) {
 #pragma unroll
         for (int s = 0; s < MAXS; ++s) {
           if (s < S) {
-            const double xd = (double)x[s];
+            const double xd = int_to_f64(x[s]);
             U = __dadd_rn(U, __dmul_rn(xd, __dsub_rn(a.Pw[(size_t)k2 * S + s], a.Pw[(size_t)k * S + s])));
             UG = __dadd_rn(UG, __dmul_rn(xd, __dsub_rn(a.Pgw[(size_t)k2 * S + s], a.Pgw[(size_t)k * S + s])));
           }
@@ -225,7 +236,7 @@ __global__ void __launch_bounds__(kGradThreads) k_ssa_grad(const GradArgs a) {
 #pragma unroll
       for (int s = 0; s < MAXS; ++s) {
         if (s < S) {
-          const double xd = (double)x[s];
+          const double xd = int_to_f64(x[s]);
           U = __dadd_rn(U, __dmul_rn(xd, __dsub_rn(a.Pw[(size_t)G * S + s], a.Pw[(size_t)k * S + s])));
           UG = __dadd_rn(UG, __dmul_rn(xd, __dsub_rn(a.Pgw[(size_t)G * S + s], a.Pgw[(size_t)k * S + s])));
         }
@@ -237,7 +248,7 @@ __global__ void __launch_bounds__(kGradThreads) k_ssa_grad(const GradArgs a) {
     for (int j = 0; j < MAXM; ++j) {
       if (j < M) {
         const int idx = j * T + tid;
-        flush_slot(sl, idx, __ll2double_rn(h[j]), SU, SUG);
+        flush_slot(sl, idx, int_to_f64(h[j]), SU, SUG);
         a.gtraj[(size_t)j * a.N + li] = sl.g[idx];
       }
     }
