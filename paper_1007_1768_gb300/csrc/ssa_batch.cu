@@ -65,8 +65,12 @@ struct BatchLaunch {
   int smax;                        // largest S of the launch (per-warp state slots)
 };
 
+// FP32 instantiations are held to 85 registers (three CTAs of 256 threads per
+// SM): more resident warps hide the step's latencies better than the
+// registers it gives up (measured on the uneven 256-network batch: 1.71 ->
+// 1.55 s per step at 1/16 of its trajectories); FP64 ones keep 128.
 template <int MAXCH, bool F32>
-__global__ void __launch_bounds__(256) k_ssa_batch(const BatchLaunch L) {
+__global__ void __launch_bounds__(256, F32 ? 3 : 2) k_ssa_batch(const BatchLaunch L) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* s_inv = reinterpret_cast<uint64_t*>(smem);
   uint64_t* s_lnf = s_inv + kLogCells;
