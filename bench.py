@@ -57,7 +57,7 @@ WORKLOADS = {
                "kernel": "k_ssa_warp", "dram_bytes": {"fp64": 606464, "fp32": 627968}},
     "grad": {"factory": "workload_hiv_shaped", "name": "hiv_shaped_grad_S4_M10_G3001_T30_loss_V", "n_traj": 1048576,
              "steps": 5, "e2e_steps": 2, "cpu_sample": 2048, "ref_sample": 1024,
-             "kernel": "k_ssa_grad", "dram_bytes": None},
+             "kernel": "k_ssa_grad", "dram_bytes": 256370000},
     "paper_hiv": {"factory": "workload_paper_hiv", "name": "paper_hiv_S10_M27_G1001_T10_tnf_modifiers",
                   "n_traj": 4096, "steps": 3, "e2e_steps": 1, "cpu_sample": 48, "ref_sample": 16,
                   "kernel": "k_ssa_warp", "dram_bytes": None},
