@@ -136,6 +136,8 @@ typedef struct ssa_run_stats {
   double kernel_ms;     /* device time of the simulation + reduction kernels */
   int32_t schedule;     /* SSA_SCHED_THREAD or SSA_SCHED_WARP: the schedule that ran (for a
                            whole batch SSA_SCHED_AUTO; per network see ssa_batch_network_stats) */
+  int64_t handoffs;     /* trajectories one warp passed to another during the run (thread
+                           schedule of ssa_ensemble_run; 0 elsewhere); results do not depend on it */
 } ssa_run_stats;
 
 /* Text for a status code (static storage). */

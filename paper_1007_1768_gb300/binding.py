@@ -54,7 +54,8 @@ class RunOpts(ctypes.Structure):
 
 class RunStats(ctypes.Structure):
     _fields_ = [("events", ctypes.c_int64), ("truncated", ctypes.c_int64), ("overflowed", ctypes.c_int64),
-                ("max_x", ctypes.c_int64), ("kernel_ms", ctypes.c_double), ("schedule", ctypes.c_int32)]
+                ("max_x", ctypes.c_int64), ("kernel_ms", ctypes.c_double), ("schedule", ctypes.c_int32),
+                ("handoffs", ctypes.c_int64)]
 
 
 _lib = None
@@ -190,6 +191,7 @@ class EnsembleResult:
     traj_hash: object = None
     traj_flags: object = None
     schedule: int = 0  # SCHED value of the schedule that ran (1 thread, 2 warp)
+    handoffs: int = 0  # trajectories passed between warps (thread schedule)
 
 
 def make_opts(precision="fp64", schedule="auto", reduce="auto", memory=MEM_HOST, max_events=0, traj_offset=0,
@@ -272,7 +274,7 @@ def ensemble_run(model: Model, n_traj: int, t_end: float, n_grid: int, seed: int
                                       mean.data_ptr(), var.data_ptr(), None if s1 is None else s1.data_ptr(),
                                       None if s2 is None else s2.data_ptr(), ctypes.byref(st) if stats else None))
     return EnsembleResult(mean, var, s1, s2, int(st.events), int(st.truncated), int(st.overflowed), int(st.max_x),
-                          float(st.kernel_ms), tev, ths, tfl, int(st.schedule))
+                          float(st.kernel_ms), tev, ths, tfl, int(st.schedule), int(st.handoffs))
 
 
 def ensemble_grad(model: Model, n_traj: int, t_end: float, n_grid: int, seed: int, dL_dmean, mean, grid=None, *,

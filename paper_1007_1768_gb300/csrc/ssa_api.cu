@@ -227,7 +227,7 @@ ssa_status model_on_device(const ssa_model* cm, int dev, DevModel* out) {
 
 // Workspace layout (bytes, 256-aligned pieces).
 struct Workspace {
-  size_t counter, stats, d1, d2, grid, mean, var, sum1, sum2, tev, thash, tflags, total;
+  size_t counter, stats, pool, d1, d2, grid, pool_slots, mean, var, sum1, sum2, tev, thash, tflags, total;
 };
 
 Workspace workspace_layout(int S, int G, int64_t N, const ssa_run_opts& o) {
@@ -241,9 +241,11 @@ Workspace workspace_layout(int S, int G, int64_t N, const ssa_run_opts& o) {
   const size_t gs = (size_t)G * S;
   w.counter = take(8);
   w.stats = take(8 * kStatCount);
+  w.pool = take(kPoolHeaderBytes);
   w.d1 = take(8 * gs);
   w.d2 = take(8 * gs);
   w.grid = take(8 * (size_t)G);
+  w.pool_slots = take(kPoolSlotBytes);
   const bool host = o.memory == SSA_MEM_HOST;
   w.mean = host ? take(8 * gs) : 0;
   w.var = host ? take(8 * gs) : 0;
@@ -516,7 +518,7 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
     plan.blocks = o.grid_blocks ? o.grid_blocks : (int)(want < cap ? want : cap);
   } else {
     if (const char* msg = plan_thread_launch(S, m->M, G, n_traj, di.sms, di.smem_optin, o.reduce, o.block_threads,
-                                             o.grid_blocks, &plan))
+                                             o.grid_blocks, &plan, true))
       return fail(SSA_EINVAL, "%s", msg);
     SSA_CUDA_TRY(thread_kernel_set_smem(m->M, S, plan.shared_d, plan.smem));
   }
@@ -545,7 +547,7 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
     }                                                                                          \
   } while (0)
 
-  SSA_RUN_TRY(cudaMemsetAsync(ws, 0, wl.grid, stream));  // counter, stats, D1, D2
+  SSA_RUN_TRY(cudaMemsetAsync(ws, 0, wl.grid, stream));  // counter, stats, hand-off counters, D1, D2
   const double* d_grid;
   double* ws_grid = reinterpret_cast<double*>(ws + wl.grid);
   if (!grid) {
@@ -573,6 +575,8 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
   a.D1 = reinterpret_cast<unsigned long long*>(ws + wl.d1);
   a.D2 = reinterpret_cast<unsigned long long*>(ws + wl.d2);
   a.counter = reinterpret_cast<unsigned long long*>(ws + wl.counter);
+  a.pool = use_warp ? nullptr : reinterpret_cast<unsigned long long*>(ws + wl.pool);
+  a.pool_slots = use_warp ? nullptr : reinterpret_cast<unsigned long long*>(ws + wl.pool_slots);
   a.stats = reinterpret_cast<unsigned long long*>(ws + wl.stats);
   a.traj_events = host ? (o.traj_events ? reinterpret_cast<int64_t*>(ws + wl.tev) : nullptr) : o.traj_events;
   a.traj_hash = host ? (o.traj_hash ? reinterpret_cast<uint64_t*>(ws + wl.thash) : nullptr) : o.traj_hash;
@@ -634,7 +638,10 @@ ssa_status ssa_ensemble_run(const ssa_model* m, int64_t n_traj, double t_end, in
     stats->max_x = (int64_t)hstats[kStatMaxX];
     stats->kernel_ms = ms;
     stats->schedule = use_warp ? SSA_SCHED_WARP : SSA_SCHED_THREAD;
+    stats->handoffs = (int64_t)hstats[kStatHandoffs];
   }
+  if (hstats[kStatPoolError] > 0)
+    return fail(SSA_ETIMEOUT, "%llu hand-off waits between warps ran out", hstats[kStatPoolError]);
   if (hstats[kStatOverflowed] > 0)
     return fail(SSA_EOVERFLOW, "%llu trajectories stopped at the int32 state limit", hstats[kStatOverflowed]);
   // sum x^2 over N trajectories must stay below 2^63

@@ -846,6 +846,7 @@ ssa_status ssa_batch_launch(ssa_batch* b, uint64_t seed, double* const* means, d
     int common = b->sched[0];
     for (int i = 1; i < b->n; ++i) common = (b->sched[i] == common) ? common : SSA_SCHED_AUTO;
     stats->schedule = common;
+    stats->handoffs = 0;
   }
   if (bad >= 0) {
     char msg[128];
@@ -875,6 +876,7 @@ ssa_status ssa_batch_network_stats(const ssa_batch* b, int32_t index, ssa_run_st
   out->max_x = (int64_t)h[3];
   out->kernel_ms = 0.0;
   out->schedule = b->sched[index];
+  out->handoffs = 0;
   return SSA_OK;
 }
 

@@ -49,7 +49,25 @@ struct DevModel {
 };
 
 // Slots of the per-run device totals.
-enum { kStatEvents = 0, kStatTruncated = 1, kStatOverflowed = 2, kStatMaxX = 3, kStatCount = 8 };
+enum { kStatEvents = 0, kStatTruncated = 1, kStatOverflowed = 2, kStatMaxX = 3, kStatPoolError = 4, kStatHandoffs = 5,
+       kStatCount = 8 };
+
+// Hand-off pool of the thread kernel.  In the cooperative tail a warp that
+// still runs two or more trajectories passes one, between batches, to a warp
+// that has none left (anywhere in the launch), so that the last long
+// trajectories do not share a warp or an SM that others have left.  The pool
+// is a ring of trajectory states with four counters, each on its own
+// 128-byte line: registrations of waiting warps not yet claimed by a
+// producer (avail), states taken (head), states claimed for writing (tail)
+// and warps that may still hand off (multi); then one sequence word per
+// slot (p + 1 once state p is written, p + 1 + 2^62 once it is read).  The
+// counters and sequence words start at zero on every launch; the slots need
+// no initialisation.
+constexpr int kPoolSlots = 4096;
+constexpr int kPoolSlotWords = 16;
+constexpr int kPoolAvail = 0, kPoolHead = 16, kPoolTail = 32, kPoolMulti = 48, kPoolSeq = 64;
+constexpr size_t kPoolHeaderBytes = 8 * (size_t)(kPoolSeq + kPoolSlots);      // counters + sequence words
+constexpr size_t kPoolSlotBytes = 8 * (size_t)kPoolSlotWords * kPoolSlots;    // states
 
 // Small-network tables passed by value to the thread kernel (M <= 16,
 // S <= 16): reads with a per-reaction constant index come straight from the
@@ -79,6 +97,8 @@ struct RunArgs {
   unsigned long long* D1;             // [G * S] per-grid sums of count changes (global)
   unsigned long long* D2;             // [G * S] per-grid sums of square changes (global)
   unsigned long long* counter;        // next trajectory index
+  unsigned long long* pool = nullptr;  // hand-off counters and sequence words (zeroed), or null: no hand-off
+  unsigned long long* pool_slots = nullptr;  // [kPoolSlots * kPoolSlotWords] hand-off states
   unsigned long long* stats;          // [kStatCount]
   int64_t* traj_events;               // [N] or null
   uint64_t* traj_hash;                // [N] or null
@@ -239,18 +259,22 @@ struct LaunchPlan {
 };
 
 // Chooses the launch shape: threads per CTA from the trajectories per SM
-// (64..512, multiples of 32) unless given.  The difference sums go to global
+// (64..512, multiples of 32) unless given.  With hand-off between warps
+// (`handoff`), more than 256 trajectories per SM take full 512-thread CTAs,
+// at least one per SM: the warps left without a trajectory wait for handed-off
+// ones from the start.  The difference sums go to global
 // memory by default (fire-and-forget reductions that never stall a warp,
 // measured faster than shared-memory atomics here); SSA_REDUCE_SHARED stages
 // them per CTA in shared memory instead.
 // Returns nullptr or an error message.
 inline const char* plan_thread_launch(int S, int M, int G, int64_t N, int sms, size_t smem_optin, int reduce,
-                                      int block_threads, int grid_blocks, LaunchPlan* p) {
+                                      int block_threads, int grid_blocks, LaunchPlan* p, bool handoff = false) {
   int threads = block_threads;
+  const int64_t per_sm = (N + sms - 1) / sms;
   if (threads == 0) {
-    const int64_t per_sm = (N + sms - 1) / sms;
     const int64_t t = (per_sm + 31) / 32 * 32;
     threads = (int)(t < 64 ? 64 : (t > 512 ? 512 : t));
+    if (handoff && per_sm > 256) threads = 512;
   }
   const int mb = bucket_m(M), sb = bucket_s(S);
   const ThreadSmem sh = thread_smem_layout(mb, sb, S, G, true);
@@ -267,13 +291,14 @@ inline const char* plan_thread_launch(int S, int M, int G, int64_t N, int sms, s
   int blocks = grid_blocks;
   if (blocks == 0) {
     const int64_t want = (N + threads - 1) / threads;
-    int per_sm = 1;
+    int ctas_per_sm = 1;
     if (!shared_d) {
-      per_sm = (int)(smem_optin / (lay.total > 0 ? lay.total : 1));
-      per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+      ctas_per_sm = (int)(smem_optin / (lay.total > 0 ? lay.total : 1));
+      ctas_per_sm = ctas_per_sm < 1 ? 1 : (ctas_per_sm > 4 ? 4 : ctas_per_sm);
     }
-    const int64_t cap = (int64_t)sms * per_sm;
+    const int64_t cap = (int64_t)sms * ctas_per_sm;
     blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+    if (handoff && block_threads == 0 && blocks < sms) blocks = sms;
   }
   p->blocks = blocks;
   p->threads = threads;

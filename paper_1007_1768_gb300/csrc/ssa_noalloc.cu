@@ -235,6 +235,7 @@ extern "C" ssa_status ssa_ensemble_run_noalloc(const ssa_model* model, int64_t n
   stats->max_x = (int64_t)h[kStatMaxX];
   stats->kernel_ms = 0.0;
   stats->schedule = SSA_SCHED_THREAD;
+  stats->handoffs = 0;
   if (h[kStatOverflowed] > 0) return record_error(SSA_EOVERFLOW, "a trajectory stopped at the int32 state limit");
   const long double bound = (long double)n_traj * (long double)h[kStatMaxX] * (long double)h[kStatMaxX];
   if (bound >= 9.2233720368547758e18L) return record_error(SSA_EOVERFLOW, "N * max_x^2 may exceed int64 sums");

@@ -454,6 +454,111 @@ __device__ __forceinline__ T shfl_all(T v, int src, int width = 32) {
 }
 
 // ---------------------------------------------------------------------------
+// Hand-off between warps (the pool is described in ssa_internal.h).
+//
+// A waiting warp registers on `avail`; a producer claims one registration
+// before it writes a state, so the states claimed and not yet taken never
+// outnumber the warps still waiting: no state is left without a taker.  A
+// waiting warp leaves only by taking back an unclaimed registration, once no
+// warp can hand off any more (multi == 0: every warp counts there from its
+// start until it runs at most one trajectory) or after a long idle wait.
+// Every wait is bounded; a wait that runs out counts an error in the run's
+// stats.
+
+constexpr int kPoolClaimTries = 64;              // CAS attempts on a contended counter
+constexpr int kPoolIdlePolls = 1 << 17;          // polls without work (about 1 s) before a waiting warp may leave
+constexpr int kPoolMaxPolls = 1 << 18;           // bound on any wait, about 2 s at most (an error beyond it)
+constexpr unsigned long long kPoolRead = 1ULL << 62;  // sequence mark: the state was read
+
+__device__ __forceinline__ unsigned long long vload(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+// Takes one unit from a counter if it is positive.
+__device__ __forceinline__ bool pool_take_one(unsigned long long* c) {
+  unsigned long long v = vload(c);
+  for (int i = 0; i < kPoolClaimTries && v > 0ULL; ++i) {
+    const unsigned long long o = atomicCAS(c, v, v - 1ULL);
+    if (o == v) return true;
+    v = o;
+  }
+  return false;
+}
+
+// Writes trajectory q (between batches: nothing pending) to the next slot.
+// One lane.  Returns false (error counted) if the slot's previous state was
+// never read.
+template <int MAXM, int MAXS>
+__device__ __forceinline__ bool pool_put(const RunArgs& a, const Traj<MAXM, MAXS>& q) {
+  unsigned long long* P = a.pool;
+  const unsigned long long p = atomicAdd(P + kPoolTail, 1ULL);
+  const int slot = (int)(p % (unsigned long long)kPoolSlots);
+  unsigned long long* seq = P + kPoolSeq + slot;
+  const unsigned long long prev = (p >= (unsigned long long)kPoolSlots) ? (p - kPoolSlots + 1ULL + kPoolRead) : 0ULL;
+  int i = 0;
+  while (vload(seq) != prev && i < kPoolMaxPolls) {
+    __nanosleep(256);
+    ++i;
+  }
+  if (i == kPoolMaxPolls) {
+    atomicAdd(a.stats + kStatPoolError, 1ULL);
+    return false;
+  }
+  volatile unsigned long long* w = a.pool_slots + (size_t)slot * kPoolSlotWords;
+  w[0] = (unsigned long long)obits(q.t);
+  w[1] = q.hash;
+  w[2] = q.traj_id;
+  w[3] = (unsigned long long)q.li;
+  w[4] = (unsigned long long)q.n | ((unsigned long long)(uint32_t)q.k << 32);
+  w[5] = (unsigned long long)(uint32_t)q.maxx;
+#pragma unroll
+  for (int s = 0; s < MAXS; s += 2) {
+    const unsigned long long hi = (s + 1 < MAXS) ? (unsigned long long)(uint32_t)q.x[s + 1] : 0ULL;
+    w[6 + s / 2] = (unsigned long long)(uint32_t)q.x[s] | (hi << 32);
+  }
+  __threadfence();
+  atomicExch(seq, p + 1ULL);
+  atomicAdd(a.stats + kStatHandoffs, 1ULL);
+  return true;
+}
+
+// Reads state p (claimed by this warp) into q.  One lane.  Returns false
+// (error counted) if it never appears.
+template <int MAXM, int MAXS>
+__device__ __forceinline__ bool pool_get(const RunArgs& a, unsigned long long p, Traj<MAXM, MAXS>& q) {
+  const int slot = (int)(p % (unsigned long long)kPoolSlots);
+  unsigned long long* seq = a.pool + kPoolSeq + slot;
+  int i = 0;
+  while (vload(seq) != p + 1ULL && i < kPoolMaxPolls) {
+    __nanosleep(128);
+    ++i;
+  }
+  if (i == kPoolMaxPolls) {
+    atomicAdd(a.stats + kStatPoolError, 1ULL);
+    return false;
+  }
+  __threadfence();
+  const volatile unsigned long long* w = a.pool_slots + (size_t)slot * kPoolSlotWords;
+  q.t = __longlong_as_double((long long)w[0]);
+  q.hash = w[1];
+  q.traj_id = w[2];
+  q.li = (long long)w[3];
+  const unsigned long long nk = w[4];
+  q.n = (uint32_t)nk;
+  q.k = (int)(uint32_t)(nk >> 32);
+  q.maxx = (int)(uint32_t)w[5];
+#pragma unroll
+  for (int s = 0; s < MAXS; s += 2) {
+    const unsigned long long v = w[6 + s / 2];
+    q.x[s] = (int)(uint32_t)v;
+    if (s + 1 < MAXS) q.x[s + 1] = (int)(uint32_t)(v >> 32);
+  }
+  __threadfence();
+  atomicExch(seq, p + 1ULL + kPoolRead);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
 // Cooperative mode: speculative batches.
 //
 // When at most 16 trajectories are left in a warp and no new work remains,
@@ -498,22 +603,6 @@ __device__ __forceinline__ int spec_group_size(int n) { return 32 >> (32 - __clz
 // The bits of a warp ballot that belong to the group starting at lane gbase.
 __device__ __forceinline__ unsigned group_bits(unsigned ballot, int gbase, int L) {
   return L == 32 ? ballot : (ballot >> gbase) & ((1u << L) - 1u);
-}
-
-// q.av[j] = v for a warp-uniform runtime j (a jump to one register move).
-template <int MAXM, int MAXS>
-__device__ __forceinline__ void set_propensity(Traj<MAXM, MAXS>& q, int j, unsigned long long v) {
-  switch (j) {
-#define SSA_SET_AV(J) \
-  case J:             \
-    if constexpr (J < MAXM) q.av[J] = v; \
-    break;
-    SSA_SET_AV(0) SSA_SET_AV(1) SSA_SET_AV(2) SSA_SET_AV(3) SSA_SET_AV(4) SSA_SET_AV(5) SSA_SET_AV(6)
-    SSA_SET_AV(7) SSA_SET_AV(8) SSA_SET_AV(9) SSA_SET_AV(10) SSA_SET_AV(11) SSA_SET_AV(12) SSA_SET_AV(13)
-    SSA_SET_AV(14) SSA_SET_AV(15)
-#undef SSA_SET_AV
-    default: break;
-  }
 }
 
 // Prefix sum j (left to right) from the propensities, given prefix j - 1.
@@ -688,10 +777,13 @@ __device__ __forceinline__ void settle_batch(const RunArgs& a, const StepEnv& e,
 
 template <bool LOG, int MAXM, int MAXS>
 __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Traj<MAXM, MAXS>& q, unsigned act,
-                                         unsigned long long* blk, const EventLog& lg, ThreadLog& tl) {
+                                         bool& in_multi, unsigned long long* blk, const EventLog& lg, ThreadLog& tl) {
   const int lane = threadIdx.x & 31;
   int L = 0, gl = 0;
   int gbase = 0;
+  unsigned anc_mask = 0u;  // the nodes on this lane's path below the root (heap order)
+  unsigned long long avail_seen = 0ULL;  // waiting warps seen at the start of the batch (lane 0)
+  double root_a0 = 0.0;            // a0 of this lane's node in the last round (the root's on group lane 0)
   int P[MAXS], up[MAXS];  // net change along this lane's path and its largest rise, per species
   bool path_ok = false;   // every reaction on the path exists
   int H1 = -2, H2 = -2;   // hypotheses (-2: not chosen since the last regrouping)
@@ -707,12 +799,23 @@ __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Tra
   for (;;) {
     const int nlive = __popc(owners);
     if (nlive == 0) break;
+    if constexpr (!LOG) {
+      if (a.pool) {
+        const bool want = nlive >= 2;
+        if (want != in_multi) {
+          if (lane == 0) atomicAdd(a.pool + kPoolMulti, want ? 1ULL : ~0ULL);
+          in_multi = want;
+        }
+      }
+    }
     // (re)grouping: at entry, and when the live trajectories fit larger groups
     const int Lw = spec_group_size(nlive);
     if (Lw != L) {
       L = Lw;
       gl = lane & (L - 1);
       gbase = lane & ~(L - 1);
+      anc_mask = 0u;
+      for (int v = gl; v > 0; v = (v - 1) >> 1) anc_mask |= 1u << v;
       const int grp = lane / L;
       unsigned m = owners;
       int owner = -1;  // the grp-th live trajectory's lane
@@ -756,6 +859,9 @@ __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Tra
       }
     }
     if (!__any_sync(kFullMask, q.have)) break;
+    if constexpr (!LOG) {
+      if (in_multi && lane == 0) avail_seen = vload(a.pool + kPoolAvail);
+    }
 
     const uint32_t base = q.n;
     const EventRandom rr = event_random(base + (uint32_t)gl, q.traj_id, e.sid, e.key0, e.key1, e.s_inv, e.s_lnf);
@@ -827,35 +933,47 @@ __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Tra
         xl[s] = q.x[s] + P[s];
         safe = safe && (long long)q.x[s] + up[s] <= kStateMax;
       }
-      // products of the reactions any running lane must recompute, one
-      // warp-uniform reaction at a time
+      // products of the reactions any running lane must recompute (a
+      // warp-uniform set), unrolled so that each reaction's word and rate
+      // are launch constants and no index is dynamic
       const uint32_t dany = __reduce_or_sync(kFullMask, run ? dirty : 0u) & ((1u << MAXM) - 1u);
-      for (uint32_t dm = dany; dm != 0u; dm &= dm - 1u) {
-        const int j = __ffs((int)dm) - 1;
-        const unsigned long long pj = propensity_fp64(a.sm.cbits[j], mass_action_h<MAXS>(a.sm.rinfo[j], xl));
-        if (run && ((dirty >> j) & 1u)) set_propensity(q, j, pj);
+#pragma unroll
+      for (int j = 0; j < MAXM; ++j) {
+        if ((dany >> j) & 1u) {
+          const unsigned long long pj = propensity_fp64(a.sm.cbits[j], mass_action_h<MAXS>(a.sm.rinfo[j], xl));
+          if (run && ((dirty >> j) & 1u)) q.av[j] = pj;
+        }
       }
-      const int lo = __reduce_min_sync(kFullMask, (run && dirty != 0u) ? (__ffs((int)dirty) - 1) : MAXM);
+      // the lowest changed reaction of any running lane: the lowest bit of
+      // the union
+      const int lo = (dany != 0u) ? (__ffs((int)dany) - 1) : MAXM;
       const double a0 = prefix_sums_from(q, lo);
+      root_a0 = a0;
       if (run) dirty = 0u;
       const int ei = nres + dep;  // this node's event within the batch
       const bool inwin = ei < L;
       const unsigned long long u2 = __shfl_sync(kFullMask, rr.u2, min(ei, L - 1), L);
       const long long gb = obits(__dmul_rn(__longlong_as_double((long long)u2), a0));
       const int jsel = select_reaction(e.M, q, gb);
-      // verification
+      // this node's state after its own selection (taken as the new state if
+      // the node closes the round's path); not applied if it would leave the
+      // int32 range
+      int xpost[MAXS];
+      bool over_me = false;
+      {
+        const int* rowj = e.s_nu + jsel * MAXS;
+#pragma unroll
+        for (int s = 0; s < MAXS; ++s) {
+          xpost[s] = xl[s] + rowj[s];
+          over_me = over_me || (long long)xl[s] + rowj[s] > kStateMax;
+        }
+      }
+      // verification: a node is verified when it and every ancestor below
+      // the root made their parent's hypothesis
       const int jp = __shfl_sync(kFullMask, jsel, par, L);
       const bool cons = (gl == 0) || (jp == hyp_me && safe && inwin);
       const unsigned C = group_bits(__ballot_sync(kFullMask, cons), gbase, L);
-      bool ver = run;
-      int v = gl;
-#pragma unroll
-      for (int i = 0; i < kSpecMaxDepth; ++i) {
-        if (v > 0) {
-          ver = ver && ((C >> v) & 1u);
-          v = (v - 1) >> 1;
-        }
-      }
+      const bool ver = run && (C & anc_mask) == anc_mask;
       const unsigned V = group_bits(__ballot_sync(kFullMask, ver), gbase, L);
       const int w = 31 - __clz((int)(V | 1u));  // deepest verified node
       const int dw = node_depth(w);
@@ -869,22 +987,21 @@ __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Tra
         my_a0 = a0_s;
         my_j = j_s;
       }
-      // the new state: node w's state and its selection (not applied if it
-      // would leave the int32 range)
-      const int jw = __shfl_sync(kFullMask, jsel, w, L);
-      const int* roww = e.s_nu + jw * MAXS;
-      int xw[MAXS];
-      bool over = false;
+      // the new state: node w's state after its selection, or before it
+      // when that would leave the int32 range
+      const bool over = __shfl_sync(kFullMask, (int)over_me, w, L) != 0;
+      int xn_w[MAXS];
 #pragma unroll
       for (int s = 0; s < MAXS; ++s) {
-        xw[s] = __shfl_sync(kFullMask, xl[s], w, L);
-        over = over || (long long)xw[s] + roww[s] > kStateMax;
+        const int xb = __shfl_sync(kFullMask, xl[s], w, L);
+        const int xa = __shfl_sync(kFullMask, xpost[s], w, L);
+        xn_w[s] = over ? xb : xa;
       }
       if (run) {
         uint32_t dm = 0u;
 #pragma unroll
         for (int s = 0; s < MAXS; ++s) {
-          const int xn = over ? xw[s] : xw[s] + roww[s];
+          const int xn = xn_w[s];
           dm |= (xn != q.x[s]) ? e.s_rmask[s] : 0u;
           q.x[s] = xn;
         }
@@ -904,7 +1021,73 @@ __device__ __forceinline__ void coop_run(const RunArgs& a, const StepEnv& e, Tra
       default: settle_batch<2, LOG>(a, e, q, gl, gbase, base, nres, nb, my_a0, my_j, rr, blk, lg, tl); break;
     }
     owners = __ballot_sync(kFullMask, q.have && gl == 0);
+
+    // hand off one trajectory to a waiting warp: the one with the most
+    // expected remaining events, a0 (t_end - t)
+    if constexpr (!LOG) {
+      if (in_multi && __popc(owners) >= 2) {
+        bool claimed = false;
+        if (lane == 0 && avail_seen > 0ULL) claimed = pool_take_one(a.pool + kPoolAvail);
+        if (__shfl_sync(kFullMask, (int)claimed, 0) != 0) {
+          const bool cand = gl == 0 && q.have;
+          const float est = fmaxf((float)root_a0 * (float)(a.t_end - q.t), 0.f);
+          const unsigned key = cand ? (0x80000000u | (__float_as_uint(est) & 0x7FFFFFE0u) | (unsigned)lane) : 0u;
+          const int c = (int)(__reduce_max_sync(kFullMask, key) & 31u);
+          bool put = false;
+          if (lane == c) put = pool_put(a, q);
+          if (__shfl_sync(kFullMask, (int)put, c) != 0 && gbase == c) q.have = false;
+          owners = __ballot_sync(kFullMask, q.have && gl == 0);
+        }
+      }
+    }
   }
+  if constexpr (!LOG) {
+    if (in_multi && lane == 0) atomicAdd(a.pool + kPoolMulti, ~0ULL);
+  }
+  in_multi = false;
+}
+
+// For a warp with no trajectory left: waits for a handed-off trajectory and
+// puts it in lane 0 (returns 1, the owner mask) or returns 0 when the pool
+// closes for this warp (see the hand-off description above).
+template <int MAXM, int MAXS>
+__device__ __forceinline__ unsigned pool_take(const RunArgs& a, Traj<MAXM, MAXS>& q) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long* P = a.pool;
+  long long got = -1;  // the state taken; -2: leave
+  if (lane == 0) {
+    atomicAdd(P + kPoolAvail, 1ULL);  // register as waiting
+    unsigned ns = 256;
+    int idle = 0;
+    for (int it = 0; it < kPoolMaxPolls; ++it) {
+      const unsigned long long h = vload(P + kPoolHead);
+      if (h < vload(P + kPoolTail)) {
+        if (atomicCAS(P + kPoolHead, h, h + 1ULL) == h) {
+          got = (long long)h;
+          break;
+        }
+        continue;
+      }
+      if ((vload(P + kPoolMulti) == 0ULL || ++idle >= kPoolIdlePolls) && pool_take_one(P + kPoolAvail)) {
+        got = -2;
+        break;
+      }
+      __nanosleep(ns);
+      ns = min(ns * 2u, 8192u);
+    }
+    if (got == -1) atomicAdd(a.stats + kStatPoolError, 1ULL);
+    if (got >= 0 && !pool_get(a, (unsigned long long)got, q)) got = -1;
+  }
+  got = __shfl_sync(kFullMask, got, 0);
+  if (got < 0) return 0u;
+  q.have = lane == 0;
+  q.pend = false;
+  q.pend_over = false;
+  q.pend_j = 0;
+  q.pend_E = 0ULL;
+  q.pend_a0 = 1.0;
+  q.flags = 0;
+  return 1u;
 }
 
 template <int MAXM, int MAXS, bool SHARED_D, bool LOG>
@@ -994,6 +1177,14 @@ __global__ void __launch_bounds__(512, 1) k_ssa_thread(const RunArgs a, const Ev
   q.pend_a0 = 0.0;
   q.rnd = EventRandom{0ULL, 0ULL};
   bool exhausted = false;  // this lane saw the work counter run out
+  // a warp may hand off trajectories from its start until it runs at most one
+  bool in_multi = false;
+  if constexpr (!LOG) {
+    if (a.pool) {
+      if ((threadIdx.x & 31) == 0) atomicAdd(a.pool + kPoolMulti, 1ULL);
+      in_multi = true;
+    }
+  }
   ThreadLog tl{kLogSentinel, 0, false, 0ULL, 0ULL};
 
   // Every lane of the warp stays in this loop until the warp has no work, so
@@ -1011,10 +1202,7 @@ __global__ void __launch_bounds__(512, 1) k_ssa_thread(const RunArgs a, const Ev
     const unsigned act = __ballot_sync(kFullMask, q.have);
     if (act == 0u) break;
     const int nact = __popc(act);
-    if (nact <= kCoopMaxTraj && __any_sync(kFullMask, exhausted)) {
-      coop_run<LOG>(a, e, q, act, blk, lg, tl);
-      break;
-    }
+    if (nact <= kCoopMaxTraj && __any_sync(kFullMask, exhausted)) break;  // cooperative mode
     if (q.have) {
       const bool done = thread_step<LOG>(a, e, q, lg, tl);
       if (done) {
@@ -1022,6 +1210,20 @@ __global__ void __launch_bounds__(512, 1) k_ssa_thread(const RunArgs a, const Ev
         q.have = false;
       }
     }
+  }
+  // the cooperative tail of this warp's trajectories, then (with a pool)
+  // trajectories handed off by other warps
+  for (unsigned act = __ballot_sync(kFullMask, q.have);;) {
+    if (act != 0u) coop_run<LOG>(a, e, q, act, in_multi, blk, lg, tl);
+    if constexpr (!LOG) {
+      if (in_multi && (threadIdx.x & 31) == 0) atomicAdd(a.pool + kPoolMulti, ~0ULL);  // no trajectory to hand off
+    }
+    in_multi = false;
+    act = 0u;
+    if constexpr (!LOG) {
+      if (a.pool) act = pool_take(a, q);
+    }
+    if (act == 0u) break;
   }
 
   if constexpr (LOG) {

@@ -81,12 +81,27 @@ def test_launch_shape_and_reduction_placement_do_not_change_results(reduce, thre
 
 def test_hiv_shaped_full_size_bench_configuration():
     """The benchmark's workload (65,536 trajectories, 3001 grid points) in the
-    launch configuration bench.py times, against the full oracle."""
+    launch configuration bench.py times, against the full oracle.  Warps hand
+    trajectories to one another in that configuration."""
     w = W.workload_hiv_shaped()
     g = _gpu(w.net, w.n_traj, w.t_end, w.n_grid, w.seed)
     r, mean, var = _oracle(w.net, w.n_traj, w.t_end, w.n_grid, w.seed, threads=16)
     _assert_same(g, r, mean, var)
     assert r.truncated == 0 and r.overflowed == 0
+    assert g["stats"].handoffs > 0
+
+
+@pytest.mark.parametrize("n,seed,threads", [(16384, 21, 0), (4000, 22, 64), (9000, 23, 512)])
+def test_trajectories_handed_between_warps_stay_bit_exact(n, seed, threads):
+    """Heavy-tailed trajectory lengths leave warps idle while others still
+    run several trajectories; the idle warps take handed-off trajectories
+    (counted in the run's stats) and every per-trajectory result, grid sum
+    and moment stays equal to the oracle's."""
+    net = W.hiv_shaped()
+    g = _gpu(net, n, 30.0, 3001, seed, block_threads=threads)
+    r, mean, var = _oracle(net, n, 30.0, 3001, seed, threads=16)
+    _assert_same(g, r, mean, var)
+    assert g["stats"].handoffs > 0
 
 
 @pytest.mark.parametrize("case", range(3))

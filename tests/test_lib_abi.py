@@ -95,10 +95,10 @@ def test_struct_layout_matches_header():
 #include <stddef.h>
 #include "ssa.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ssa_run_opts), offsetof(ssa_run_opts, max_events),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ssa_run_opts), offsetof(ssa_run_opts, max_events),
          offsetof(ssa_run_opts, cuda_stream), offsetof(ssa_run_opts, workspace_bytes),
          offsetof(ssa_run_opts, traj_flags), sizeof(ssa_run_stats), offsetof(ssa_run_stats, kernel_ms),
-         offsetof(ssa_run_stats, schedule));
+         offsetof(ssa_run_stats, schedule), offsetof(ssa_run_stats, handoffs));
   return 0;
 }
 """
@@ -110,7 +110,8 @@ int main(void) {
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     R, S = binding.RunOpts, binding.RunStats
     assert vals == [ctypes.sizeof(R), R.max_events.offset, R.cuda_stream.offset, R.workspace_bytes.offset,
-                    R.traj_flags.offset, ctypes.sizeof(S), S.kernel_ms.offset, S.schedule.offset]
+                    R.traj_flags.offset, ctypes.sizeof(S), S.kernel_ms.offset, S.schedule.offset,
+                    S.handoffs.offset]
 
 
 def test_host_run_rejects_bad_arguments_before_touching_the_gpu():
