@@ -43,7 +43,7 @@ SMS_GB300 = 152
 # DRAM read + write bytes of one k_ssa_thread launch (from an ncu capture:
 # tables, grid and parameters; the difference sums stay in L2), independent of
 # the number of trajectories.
-SIM_KERNEL_DRAM_BYTES = 729856
+SIM_KERNEL_DRAM_BYTES = 835072
 # Bench workloads: the HIV-shaped model (the headline line) and the random
 # 32-species / 128-reaction network (one trajectory per warp).
 WORKLOADS = {
@@ -66,7 +66,7 @@ WORKLOADS = {
               "kernel": "k_ssa_thread (logging) + radix sort", "dram_bytes": None},
     "batch": {"factory": None, "name": "batch256_S4-64_M8-512_N1024-65536_G501_T10_fp32", "n_traj": None,
               "steps": 2, "e2e_steps": 1, "cpu_sample": 16, "ref_sample": 16,
-              "kernel": "k_ssa_batch", "dram_bytes": 40734720},
+              "kernel": "k_ssa_batch", "dram_bytes": 45735168},
 }
 FP64_OPS_PER_SM_CLK = 2.0  # 1.25 TFLOP/s dense FP64 (FMA = 2 flops) / (152 SMs * 2.07 GHz)
 
