@@ -39,8 +39,11 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int M, int S, int nnz, int 
 
 // MAXCH bounds the chunk ceil(M / 32); F32 selects the FP32-propensity mode;
 // LOG also writes the event log (selective memory along the time axis).
+// Chunks of at most 4 reactions per lane are held to 64 registers (four
+// 256-thread CTAs per SM; measured faster than 80-92 registers at three or
+// two).
 template <int MAXCH, bool F32, bool LOG>
-__global__ void __launch_bounds__(256) k_ssa_warp(const RunArgs a, const EventLog lg) {
+__global__ void __launch_bounds__(256, MAXCH <= 4 ? 4 : 1) k_ssa_warp(const RunArgs a, const EventLog lg) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long blk[4];
   __shared__ int s_nnz_max;

@@ -237,11 +237,15 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
     int nrec = 32;       // events whose time is formed: the applied ones and the one that stopped the draws
 #pragma unroll 1
     for (int b = 0; b < 32; ++b) {
-      // propensities of this lane's reactions that the last event touched
-#pragma unroll
-      for (int q = 0; q < MAXCH; ++q) {
-        if (q >= ch) break;
-        if ((dirty >> q) & 1u) {
+      // propensities of this lane's reactions that the last event touched: a
+      // loop over the lane's dirty slots, as many passes as the busiest lane
+      // needs (an unrolled pass per slot would run every slot that any lane
+      // needs), the value placed by a select chain so that the propensities
+      // stay in registers
+      for (uint32_t dm = dirty; __any_sync(kFullMask, dm != 0u);) {
+        if (dm != 0u) {
+          const int q = __ffs((int)dm) - 1;
+          dm &= dm - 1u;
           const int j = my0 + q;
           const int32_t w = net.rinfo[j];
           const int kind = rinfo_kind(w);
@@ -253,7 +257,9 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
           // products on the FP32 pipe (FP32 mode) or as exact integer
           // arithmetic (FP64 mode: the SM's FP64 unit binds the warp kernel)
           if constexpr (F32) {
-            af[q] = __fmul_rn(net.c32[j], __ll2float_rn(h));
+            const float v = __fmul_rn(net.c32[j], __ll2float_rn(h));
+#pragma unroll
+            for (int i = 0; i < MAXCH; ++i) af[i] = (i == q) ? v : af[i];
           } else {
             unsigned long long cb = net.cbits[j];
             if (net.mod_f != nullptr) {  // state-dependent rate: clamp(c + k x_f, lo, hi), FP64
@@ -266,7 +272,9 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
             }
             unsigned long long ab;
             if (!propensity_int(cb, h, ab)) ab = propensity_fp64(cb, h);
-            av[q] = __longlong_as_double((long long)ab);
+            const double v = __longlong_as_double((long long)ab);
+#pragma unroll
+            for (int i = 0; i < MAXCH; ++i) av[i] = (i == q) ? v : av[i];
           }
         }
       }
