@@ -103,11 +103,13 @@ struct GradSlots {
 };
 
 // g_j += B_j (SU - SU0_j) - h_j (SUG - SUG0_j): the intervals since B_j or h_j
-// last changed, all with the same B_j and h_j.
+// last changed, all with the same B_j and h_j.  The score's products and
+// sums are fused (one rounding per multiply-add, half the FP64 instructions
+// of separate ones; the contributions agree with the oracle's association
+// to rounding either way).
 __device__ __forceinline__ void flush_slot(const GradSlots& sl, int idx, double hj, double SU, double SUG) {
-  const double inc = __dsub_rn(__dmul_rn(sl.B[idx], __dsub_rn(SU, sl.su0[idx])),
-                               __dmul_rn(hj, __dsub_rn(SUG, sl.sug0[idx])));
-  sl.g[idx] = __dadd_rn(sl.g[idx], inc);
+  const double g1 = __fma_rn(sl.B[idx], __dsub_rn(SU, sl.su0[idx]), sl.g[idx]);
+  sl.g[idx] = __fma_rn(-hj, __dsub_rn(SUG, sl.sug0[idx]), g1);
   sl.su0[idx] = SU;
   sl.sug0[idx] = SUG;
 }
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(kGradThreads) k_ssa_grad(const GradArgs a) {
           if (j == fired) Bj = __dadd_rn(Bj, a.invc[j]);
           if (dj) {
             const long long hn = mass_action_h<MAXS>(a.sm.rinfo[j], x);
-            Bj = __dadd_rn(Bj, __dmul_rn(int_to_f64(hn - h[j]), t));
+            Bj = __fma_rn(int_to_f64(hn - h[j]), t, Bj);
             h[j] = hn;
             av[j] = __longlong_as_double((long long)propensity_fp64(a.sm.cbits[j], hn));
           }
@@ -196,8 +198,8 @@ __global__ void __launch_bounds__(kGradThreads) k_ssa_grad(const GradArgs a) {
         for (int s = 0; s < MAXS; ++s) {
           if (s < S) {
             const double xd = int_to_f64(x[s]);
-            U = __dadd_rn(U, __dmul_rn(xd, __dsub_rn(a.Pw[(size_t)k2 * S + s], a.Pw[(size_t)k * S + s])));
-            UG = __dadd_rn(UG, __dmul_rn(xd, __dsub_rn(a.Pgw[(size_t)k2 * S + s], a.Pgw[(size_t)k * S + s])));
+            U = __fma_rn(xd, __dsub_rn(a.Pw[(size_t)k2 * S + s], a.Pw[(size_t)k * S + s]), U);
+            UG = __fma_rn(xd, __dsub_rn(a.Pgw[(size_t)k2 * S + s], a.Pgw[(size_t)k * S + s]), UG);
           }
         }
         SU = __dadd_rn(SU, U);
@@ -237,8 +239,8 @@ __global__ void __launch_bounds__(kGradThreads) k_ssa_grad(const GradArgs a) {
       for (int s = 0; s < MAXS; ++s) {
         if (s < S) {
           const double xd = int_to_f64(x[s]);
-          U = __dadd_rn(U, __dmul_rn(xd, __dsub_rn(a.Pw[(size_t)G * S + s], a.Pw[(size_t)k * S + s])));
-          UG = __dadd_rn(UG, __dmul_rn(xd, __dsub_rn(a.Pgw[(size_t)G * S + s], a.Pgw[(size_t)k * S + s])));
+          U = __fma_rn(xd, __dsub_rn(a.Pw[(size_t)G * S + s], a.Pw[(size_t)k * S + s]), U);
+          UG = __fma_rn(xd, __dsub_rn(a.Pgw[(size_t)G * S + s], a.Pgw[(size_t)k * S + s]), UG);
         }
       }
       SU = __dadd_rn(SU, U);
