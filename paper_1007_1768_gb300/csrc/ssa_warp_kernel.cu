@@ -41,7 +41,9 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int M, int S, int nnz, int 
 // LOG also writes the event log (selective memory along the time axis).
 // Chunks of at most 4 reactions per lane are held to 64 registers (four
 // 256-thread CTAs per SM; measured faster than 80-92 registers at three or
-// two).
+// two); larger chunks take the registers the compiler chooses (a 512-reaction
+// FP64 network ran slower at two CTAs per SM under 128 registers than at one
+// with 162).
 template <int MAXCH, bool F32, bool LOG>
 __global__ void __launch_bounds__(256, MAXCH <= 4 ? 4 : 1) k_ssa_warp(const RunArgs a, const EventLog lg) {
   extern __shared__ __align__(16) unsigned char smem[];

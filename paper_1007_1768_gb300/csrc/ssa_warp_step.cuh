@@ -289,28 +289,16 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
       float excl32 = 0.0f;
       // loops over the chunk stop at ch (warp-uniform), the runtime chunk size
       if constexpr (F32) {
-        // binary32 selection sums
-        float v32 = af[0];
-        run32[0] = v32;
-#pragma unroll
-        for (int q = 1; q < MAXCH; ++q) {
-          if (q >= ch) break;
-          v32 = __fadd_rn(v32, af[q]);
-          run32[q] = v32;
-        }
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const float u = __shfl_up_sync(kFullMask, v32, off);
-          if (lane >= off) v32 = __fadd_rn(v32, u);
-        }
-        excl32 = __shfl_up_sync(kFullMask, v32, 1);
-        sel_total = widen(__shfl_sync(kFullMask, v32, 31));
         // a0, formed anew each event: the lane's chunk summed left to right in
         // binary32 with its rounding errors carried (cascaded TwoSum), kept as
         // the pair (cs, cerr); the lanes' pairs scanned in pair arithmetic
         // (the Kogge-Stone pattern; heads by TwoSum, error parts added in
         // binary32).  A past-the-end a_j = +0 leaves both parts unchanged.
+        // The head of TwoSum(a, b) is RN(a + b), so the heads are the binary32
+        // selection sums of schedule W32 (running sums in the chunk, the
+        // scan across lanes): one pass gives both.
         float cs = af[0], cerr = 0.0f;
+        run32[0] = cs;
 #pragma unroll
         for (int q = 1; q < MAXCH; ++q) {
           if (q >= ch) break;
@@ -320,6 +308,7 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
           const float d = __fadd_rn(__fsub_rn(cs, __fsub_rn(tt, bp)), __fsub_rn(x, bp));
           cerr = __fadd_rn(cerr, d);
           cs = tt;
+          run32[q] = tt;
         }
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -333,8 +322,10 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
             cs = tt;
           }
         }
+        excl32 = __shfl_up_sync(kFullMask, cs, 1);
         const float a0s = __shfl_sync(kFullMask, cs, 31);
         const float a0e = __shfl_sync(kFullMask, cerr, 31);
+        sel_total = widen(a0s);
         if (lane == b) {
           my_s = a0s;
           my_e = a0e;
