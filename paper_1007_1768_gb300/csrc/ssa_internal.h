@@ -114,7 +114,7 @@ struct RunArgs {
 // reaction's index), and the difference sums when they fit.
 constexpr int kLogCells = 512;
 struct ThreadSmem {
-  size_t log_inv, log_lnf, nu, depmask, rmask, d1, d2, total;
+  size_t log_inv, log_lnf, nu, depmask, rmask, rinfo, cbits, d1, d2, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -127,6 +127,8 @@ __host__ __device__ inline ThreadSmem thread_smem_layout(int maxm, int maxs, int
   L.nu = o; o += align_up((size_t)maxm * maxs * 4, 16);
   L.depmask = o; o += align_up((size_t)maxm * 4, 16);
   L.rmask = o; o += align_up((size_t)maxs * 4, 16);
+  L.rinfo = o; o += align_up((size_t)maxm * 4, 16);
+  L.cbits = o; o += align_up((size_t)maxm * 8, 16);
   if (shared_d) {
     L.d1 = o; o += (size_t)G * S * 8;
     L.d2 = o; o += (size_t)G * S * 8;

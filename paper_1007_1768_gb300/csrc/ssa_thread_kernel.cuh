@@ -266,6 +266,8 @@ struct StepEnv {
   const int32_t* s_nu;
   const uint32_t* s_depmask;
   const uint32_t* s_rmask;      // per species: the reactions whose propensity reads it
+  const int32_t* s_rinfo;       // reaction words (read with a runtime reaction index)
+  const unsigned long long* s_cbits;  // rates as double bit patterns (same)
   unsigned long long* d1;
   unsigned long long* d2;
 };
@@ -410,17 +412,30 @@ __device__ __forceinline__ void draw(const StepEnv& e, Traj<MAXM, MAXS>& q, doub
   q.dirty = apply ? e.s_depmask[jsel] : 0u;
 }
 
-// One thread-mode iteration.  Returns true when the trajectory has ended.
+// Thread mode: the propensities the last event touched, for every lane of
+// the warp together (lanes without a trajectory have none): a loop over each
+// lane's dirty reactions, as many passes as the busiest lane needs (a pass
+// per reaction that any lane needs would run most of the M products every
+// event), the value placed by a select chain so that the propensities stay
+// in registers.
+template <int MAXM, int MAXS>
+__device__ __forceinline__ void thread_propensities(const StepEnv& e, Traj<MAXM, MAXS>& q) {
+  for (uint32_t dm = q.have ? (q.dirty & ((1u << e.M) - 1u)) : 0u; __any_sync(kFullMask, dm != 0u);) {
+    if (dm != 0u) {
+      const int j = __ffs((int)dm) - 1;
+      dm &= dm - 1u;
+      const unsigned long long v = propensity_fp64(e.s_cbits[j], mass_action_h<MAXS>(e.s_rinfo[j], q.x));
+#pragma unroll
+      for (int i = 0; i < MAXM; ++i) q.av[i] = (i == j) ? v : q.av[i];
+    }
+  }
+}
+
+// One thread-mode iteration (after thread_propensities).  Returns true when
+// the trajectory has ended.
 template <bool LOG, int MAXM, int MAXS>
 __device__ __forceinline__ bool thread_step(const RunArgs& a, const StepEnv& e, Traj<MAXM, MAXS>& q,
                                             const EventLog& lg, ThreadLog& tl) {
-  // propensities the last event touched (hardware products: a warp runs the
-  // product of reaction j only when one of its lanes needs it)
-#pragma unroll
-  for (int j = 0; j < MAXM; ++j) {
-    if (j < e.M && ((q.dirty >> j) & 1u))
-      q.av[j] = propensity_fp64(a.sm.cbits[j], mass_action_h<MAXS>(a.sm.rinfo[j], q.x));
-  }
   // one straight-line block of independent chains: the pending event's
   // quotient, the prefix sums of the new state, and the random numbers of
   // the event after the one drawn below (index n + 2 once the pending event
@@ -1101,6 +1116,8 @@ __global__ void __launch_bounds__(512, 1) k_ssa_thread(const RunArgs a, const Ev
   int32_t* s_nu = reinterpret_cast<int32_t*>(smem + L.nu);
   uint32_t* s_depmask = reinterpret_cast<uint32_t*>(smem + L.depmask);
   uint32_t* s_rmask = reinterpret_cast<uint32_t*>(smem + L.rmask);
+  int32_t* s_rinfo = reinterpret_cast<int32_t*>(smem + L.rinfo);
+  unsigned long long* s_cbits = reinterpret_cast<unsigned long long*>(smem + L.cbits);
   unsigned long long* d1 = SHARED_D ? reinterpret_cast<unsigned long long*>(smem + L.d1) : a.D1;
   unsigned long long* d2 = SHARED_D ? reinterpret_cast<unsigned long long*>(smem + L.d2) : a.D2;
 
@@ -1112,7 +1129,11 @@ __global__ void __launch_bounds__(512, 1) k_ssa_thread(const RunArgs a, const Ev
     const int j = i / MAXS, s = i % MAXS;
     s_nu[i] = (j < M && s < S) ? a.sm.nu[j * kSmallMax + s] : 0;
   }
-  for (int j = tid; j < MAXM; j += T) s_depmask[j] = (j < M) ? a.sm.depmask[j] : 0u;
+  for (int j = tid; j < MAXM; j += T) {
+    s_depmask[j] = (j < M) ? a.sm.depmask[j] : 0u;
+    s_rinfo[j] = (j < M) ? a.sm.rinfo[j] : 0;
+    s_cbits[j] = (j < M) ? a.sm.cbits[j] : 0ULL;
+  }
   for (int s = tid; s < MAXS; s += T) {
     uint32_t m = 0u;
     for (int j = 0; j < M; ++j) {
@@ -1146,6 +1167,8 @@ __global__ void __launch_bounds__(512, 1) k_ssa_thread(const RunArgs a, const Ev
   e.s_nu = s_nu;
   e.s_depmask = s_depmask;
   e.s_rmask = s_rmask;
+  e.s_rinfo = s_rinfo;
+  e.s_cbits = s_cbits;
   e.d1 = d1;
   e.d2 = d2;
 
@@ -1203,6 +1226,7 @@ __global__ void __launch_bounds__(512, 1) k_ssa_thread(const RunArgs a, const Ev
     if (act == 0u) break;
     const int nact = __popc(act);
     if (nact <= kCoopMaxTraj && __any_sync(kFullMask, exhausted)) break;  // cooperative mode
+    thread_propensities(e, q);
     if (q.have) {
       const bool done = thread_step<LOG>(a, e, q, lg, tl);
       if (done) {
