@@ -367,10 +367,53 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
       const long long gb = obits(target);
       unsigned gf = 0;
       if constexpr (F32) gf = __float_as_uint(__double2float_rd(target));
+      int jsel = -1;
+      if constexpr (!F32 && MAXCH >= 4) {
+        // FP64 mode, chunks of 3 or more: a lane's prefixes do not decrease
+        // along its chunk, so only a lane whose last prefix exceeds the
+        // target can hold the first hit.  One addition per lane finds the
+        // first such lane; lanes q < ch then form that lane's prefix q, one
+        // each.  If that lane has no a_j > 0 past the target (rounding at a
+        // lane boundary) every lane's prefixes are formed below.  Two FP64
+        // additions per event instead of ch.
+        if (ch >= 3) {
+          double rl = run[0];
+#pragma unroll
+          for (int q = 1; q < MAXCH; ++q) {
+            if (q >= ch) break;
+            rl = run[q];
+          }
+          const double pl = (lane == 0) ? rl : __dadd_rn(excl, rl);
+          const unsigned cand = __ballot_sync(kFullMask, mine > 0 && obits(pl) > gb);
+          if (cand) {
+            const int h = __ffs(cand) - 1;
+            double rq = 0.0, aq = 0.0;
+#pragma unroll
+            for (int q = 0; q < MAXCH; ++q) {
+              if (q >= ch) break;
+              const double r_ = __shfl_sync(kFullMask, run[q], h);
+              const double a_ = __shfl_sync(kFullMask, av[q], h);
+              if (lane == q) {
+                rq = r_;
+                aq = a_;
+              }
+            }
+            const double ex = __shfl_sync(kFullMask, excl, h);
+            const int mine_h = max(0, min(ch, M - h * ch));
+            bool hq = false;
+            if (lane < mine_h) {
+              const double pre = (h == 0) ? rq : __dadd_rn(ex, rq);
+              hq = (obits(aq) > 0) && (obits(pre) > gb);
+            }
+            const unsigned hb = __ballot_sync(kFullMask, hq);
+            if (hb) jsel = h * ch + __ffs(hb) - 1;
+          }
+        }
+      }
       int myfirst = -1;
 #pragma unroll
       for (int q = 0; q < MAXCH; ++q) {
-        if (q >= ch) break;
+        if (jsel >= 0 || q >= ch) break;
         bool hitq;
         if constexpr (F32) {
           const float pre = (lane == 0) ? run32[q] : __fadd_rn(excl32, run32[q]);
@@ -381,9 +424,10 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
         }
         if (hitq && myfirst < 0 && q < mine) myfirst = my0 + q;
       }
-      const unsigned hit = __ballot_sync(kFullMask, myfirst >= 0);
-      int jsel;
-      if (hit) {
+      const unsigned hit = (jsel >= 0) ? 0u : __ballot_sync(kFullMask, myfirst >= 0);
+      if (jsel >= 0) {
+        // found by the candidate lane above
+      } else if (hit) {
         jsel = __shfl_sync(kFullMask, myfirst, __ffs(hit) - 1);
       } else {  // rounding left no j: the last reaction with a_j > 0
         int mylast = -1;
