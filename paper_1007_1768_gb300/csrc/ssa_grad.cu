@@ -94,12 +94,14 @@ __device__ __forceinline__ double int_to_f64(long long v) {
 }
 
 // Per-thread score state in shared memory, slot (j, tid) at j * 128 + tid:
-// B_j, the gradient g_j, and the running interval sums at g_j's last update.
+// B_j, the gradient g_j, the running interval sums at g_j's last update, and
+// the propensity factor h_j.
 struct GradSlots {
   double* B;
   double* g;
   double* su0;
   double* sug0;
+  long long* h;
 };
 
 // g_j += B_j (SU - SU0_j) - h_j (SUG - SUG0_j): the intervals since B_j or h_j
@@ -121,16 +123,24 @@ __global__ void __launch_bounds__(kGradThreads) k_ssa_grad(const GradArgs a) {
   uint64_t* s_lnf = s_inv + kLogCells;
   double* slots = reinterpret_cast<double*>(s_lnf + kLogCells);
   const int T = kGradThreads, tid = threadIdx.x;
-  GradSlots sl{slots, slots + MAXM * T, slots + 2 * MAXM * T, slots + 3 * MAXM * T};
-  // rows read with the fired reaction's index: net changes and dependency masks
-  int32_t* s_nu = reinterpret_cast<int32_t*>(slots + 4 * MAXM * T);  // [MAXM][MAXS]
+  GradSlots sl{slots, slots + MAXM * T, slots + 2 * MAXM * T, slots + 3 * MAXM * T,
+               reinterpret_cast<long long*>(slots + 4 * MAXM * T)};
+  // tables read with a runtime reaction index: rates (bits), net changes,
+  // dependency masks and reaction words
+  unsigned long long* s_cbits = reinterpret_cast<unsigned long long*>(slots + 5 * MAXM * T);  // [MAXM]
+  int32_t* s_nu = reinterpret_cast<int32_t*>(s_cbits + MAXM);       // [MAXM][MAXS]
   uint32_t* s_dep = reinterpret_cast<uint32_t*>(s_nu + MAXM * MAXS);  // [MAXM]
+  int32_t* s_rinfo = reinterpret_cast<int32_t*>(s_dep + MAXM);      // [MAXM]
   for (int i = tid; i < kLogCells; i += T) {
     s_inv[i] = d_log_tables.inv[i];
     s_lnf[i] = d_log_tables.lnf[i];
   }
   for (int i = tid; i < MAXM * MAXS; i += T) s_nu[i] = a.sm.nu[(i / MAXS) * kSmallMax + (i % MAXS)];
-  for (int j = tid; j < MAXM; j += T) s_dep[j] = a.sm.depmask[j];
+  for (int j = tid; j < MAXM; j += T) {
+    s_dep[j] = a.sm.depmask[j];
+    s_cbits[j] = a.sm.cbits[j];
+    s_rinfo[j] = a.sm.rinfo[j];
+  }
   __syncthreads();
   const int S = a.S, M = a.M, G = a.G;
   const uint32_t key0 = (uint32_t)a.seed, key1 = (uint32_t)(a.seed >> 32), sid = (uint32_t)a.stream_id;
@@ -142,11 +152,10 @@ __global__ void __launch_bounds__(kGradThreads) k_ssa_grad(const GradArgs a) {
     int x[MAXS];
 #pragma unroll
     for (int s = 0; s < MAXS; ++s) x[s] = (s < S) ? a.sm.x0[s] : 0;
-    long long h[MAXM];
     double av[MAXM];
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) {
-      h[j] = 0;
+      sl.h[j * T + tid] = 0;
       av[j] = 0.0;
       sl.B[j * T + tid] = 0.0;
       sl.g[j * T + tid] = 0.0;
@@ -162,23 +171,28 @@ __global__ void __launch_bounds__(kGradThreads) k_ssa_grad(const GradArgs a) {
     bool done = false;
     for (;;) {
       // the event at t: flush the score of the fired reaction and of every
-      // reaction whose propensity it changed, then update B and h
+      // reaction whose propensity it changed, then update B and h -- a loop
+      // over this lane's reactions (a pass per reaction any lane of the warp
+      // needs would run most of the M flushes every event); the propensity is
+      // placed by a select chain so that it stays in a register
+      const uint32_t dmask = dirty & ((1u << M) - 1u);
+      for (uint32_t dm = dmask | (fired >= 0 ? (1u << fired) : 0u); dm != 0u;) {
+        const int j = __ffs((int)dm) - 1;
+        dm &= dm - 1u;
+        const int idx = j * T + tid;
+        const long long hj = sl.h[idx];
+        flush_slot(sl, idx, int_to_f64(hj), SU, SUG);
+        double Bj = sl.B[idx];
+        if (j == fired) Bj = __dadd_rn(Bj, a.invc[j]);
+        if ((dmask >> j) & 1u) {
+          const long long hn = mass_action_h<MAXS>(s_rinfo[j], x);
+          Bj = __fma_rn(int_to_f64(hn - hj), t, Bj);
+          sl.h[idx] = hn;
+          const double v = __longlong_as_double((long long)propensity_fp64(s_cbits[j], hn));
 #pragma unroll
-      for (int j = 0; j < MAXM; ++j) {
-        const bool dj = j < M && ((dirty >> j) & 1u);
-        if (dj || j == fired) {
-          const int idx = j * T + tid;
-          flush_slot(sl, idx, int_to_f64(h[j]), SU, SUG);
-          double Bj = sl.B[idx];
-          if (j == fired) Bj = __dadd_rn(Bj, a.invc[j]);
-          if (dj) {
-            const long long hn = mass_action_h<MAXS>(a.sm.rinfo[j], x);
-            Bj = __fma_rn(int_to_f64(hn - h[j]), t, Bj);
-            h[j] = hn;
-            av[j] = __longlong_as_double((long long)propensity_fp64(a.sm.cbits[j], hn));
-          }
-          sl.B[idx] = Bj;
+          for (int i = 0; i < MAXM; ++i) av[i] = (i == j) ? v : av[i];
         }
+        sl.B[idx] = Bj;
       }
       if (done) break;
       // schedule L prefix sums
@@ -250,7 +264,7 @@ __global__ void __launch_bounds__(kGradThreads) k_ssa_grad(const GradArgs a) {
     for (int j = 0; j < MAXM; ++j) {
       if (j < M) {
         const int idx = j * T + tid;
-        flush_slot(sl, idx, int_to_f64(h[j]), SU, SUG);
+        flush_slot(sl, idx, int_to_f64(sl.h[idx]), SU, SUG);
         a.gtraj[(size_t)j * a.N + li] = sl.g[idx];
       }
     }
@@ -367,8 +381,8 @@ __global__ void k_order_scatter(const long long* ev, long long n, unsigned int* 
 // SM holds (*per_sm).
 template <int MAXM, int MAXS>
 cudaError_t launch_grad_t(const GradArgs& a, int blocks, cudaStream_t st, bool launch, int* per_sm) {
-  const size_t smem = (size_t)kLogCells * 16 + (size_t)4 * MAXM * kGradThreads * 8 + (size_t)MAXM * MAXS * 4 +
-                      (size_t)MAXM * 4;
+  const size_t smem = (size_t)kLogCells * 16 + (size_t)5 * MAXM * kGradThreads * 8 + (size_t)MAXM * 8 +
+                      (size_t)MAXM * MAXS * 4 + (size_t)MAXM * 4 + (size_t)MAXM * 4;
   cudaError_t e = cudaFuncSetAttribute(k_ssa_grad<MAXM, MAXS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (!launch)
