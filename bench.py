@@ -43,7 +43,7 @@ SMS_GB300 = 152
 # DRAM read + write bytes of one k_ssa_thread launch (from an ncu capture:
 # tables, grid and parameters; the difference sums stay in L2), independent of
 # the number of trajectories.
-SIM_KERNEL_DRAM_BYTES = 835072
+SIM_KERNEL_DRAM_BYTES = 537344
 # Bench workloads: the HIV-shaped model (the headline line) and the random
 # 32-species / 128-reaction network (one trajectory per warp).
 WORKLOADS = {
@@ -54,10 +54,10 @@ WORKLOADS = {
     # tables and grid; independent of the trajectory count)
     "random": {"factory": "workload_random", "name": "random_S32_M128_G1001_T10_netseed3", "n_traj": 262144,
                "steps": 10, "e2e_steps": 3, "cpu_sample": 2048, "ref_sample": 512,
-               "kernel": "k_ssa_warp", "dram_bytes": {"fp64": 1190000, "fp32": 1150000}},
+               "kernel": "k_ssa_warp", "dram_bytes": {"fp64": 604416, "fp32": 602112}},
     "grad": {"factory": "workload_hiv_shaped", "name": "hiv_shaped_grad_S4_M10_G3001_T30_loss_V", "n_traj": 1048576,
              "steps": 5, "e2e_steps": 2, "cpu_sample": 2048, "ref_sample": 1024,
-             "kernel": "k_ssa_grad", "dram_bytes": 257200000},
+             "kernel": "k_ssa_grad", "dram_bytes": 256360000},
     "paper_hiv": {"factory": "workload_paper_hiv", "name": "paper_hiv_S10_M27_G1001_T10_tnf_modifiers",
                   "n_traj": 4096, "steps": 3, "e2e_steps": 1, "cpu_sample": 48, "ref_sample": 16,
                   "kernel": "k_ssa_warp", "dram_bytes": None},
@@ -66,7 +66,7 @@ WORKLOADS = {
               "kernel": "k_ssa_thread (logging) + radix sort", "dram_bytes": None},
     "batch": {"factory": None, "name": "batch256_S4-64_M8-512_N1024-65536_G501_T10_fp32", "n_traj": None,
               "steps": 2, "e2e_steps": 1, "cpu_sample": 16, "ref_sample": 16,
-              "kernel": "k_ssa_batch", "dram_bytes": 45040000},
+              "kernel": "k_ssa_batch", "dram_bytes": 44585472},
 }
 FP64_OPS_PER_SM_CLK = 2.0  # 1.25 TFLOP/s dense FP64 (FMA = 2 flops) / (152 SMs * 2.07 GHz)
 

@@ -91,6 +91,16 @@ def test_hiv_shaped_full_size_bench_configuration():
     assert g["stats"].handoffs > 0
 
 
+def test_handoff_with_more_ctas_than_fit_at_once():
+    """A grid larger than one wave: CTAs that start after the first ones have
+    finished find the work counter empty and join the hand-off pool late (or
+    find it closed); every trajectory still ends once, equal to the oracle."""
+    net = W.hiv_shaped()
+    g = _gpu(net, 4000, 30.0, 601, 24, block_threads=64, grid_blocks=2000)
+    r, mean, var = _oracle(net, 4000, 30.0, 601, 24, threads=16)
+    _assert_same(g, r, mean, var)
+
+
 @pytest.mark.parametrize("n,seed,threads", [(16384, 21, 0), (4000, 22, 64), (9000, 23, 512)])
 def test_trajectories_handed_between_warps_stay_bit_exact(n, seed, threads):
     """Heavy-tailed trajectory lengths leave warps idle while others still
