@@ -47,7 +47,7 @@ typedef enum ssa_status {
   SSA_ECUDA = 3,        /* a CUDA runtime call failed */
   SSA_EOVERFLOW = 4,    /* a count would leave int32, or sum x^2 could leave int64 */
   SSA_ETRUNCATED = 5,   /* reserved: some trajectory hit max_events (reported in stats) */
-  SSA_ETIMEOUT = 6,     /* reserved for bounded device waits */
+  SSA_ETIMEOUT = 6,     /* a bounded device wait ran out (hand-off between warps) */
   SSA_EUNSUPPORTED = 7  /* valid request this build does not implement */
 } ssa_status;
 
@@ -238,9 +238,13 @@ ssa_status ssa_ensemble_workspace_size(const ssa_model* model, int64_t n_traj, i
  *   stats: host struct or NULL.
  * The results are bit-identical to the plain CPU statement of the same
  * arithmetic (the oracle shipped with the tests) for the precision and
- * summation schedule the run uses.
+ * summation schedule the run uses.  On the thread schedule warps pass
+ * trajectories to idle warps between batches of the cooperative tail (a pool
+ * of trajectory states in the workspace; stats->handoffs counts them); which
+ * warp runs which events does not change any result.
  * Errors: SSA_EINVAL, SSA_ENOMEM, SSA_ECUDA, SSA_EUNSUPPORTED,
- * SSA_EOVERFLOW (only detectable when the call waits: host memory or stats).
+ * SSA_EOVERFLOW, SSA_ETIMEOUT (a bounded wait of the hand-off ran out; both
+ * only detectable when the call waits: host memory or stats).
  */
 ssa_status ssa_ensemble_run(const ssa_model* model, int64_t n_traj, double t_end, int32_t n_grid,
                             const double* grid, uint64_t seed, const ssa_run_opts* opts,
