@@ -519,6 +519,7 @@ __device__ __forceinline__ bool pool_put(const RunArgs& a, const Traj<MAXM, MAXS
     atomicAdd(a.stats + kStatPoolError, 1ULL);
     return false;
   }
+  __threadfence();  // the previous state's reader is done before this state is written
   volatile unsigned long long* w = a.pool_slots + (size_t)slot * kPoolSlotWords;
   w[0] = (unsigned long long)obits(q.t);
   w[1] = q.hash;
