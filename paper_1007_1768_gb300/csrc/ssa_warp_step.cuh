@@ -296,16 +296,20 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
         // binary32).  A past-the-end a_j = +0 leaves both parts unchanged.
         // The head of TwoSum(a, b) is RN(a + b), so the heads are the binary32
         // selection sums of schedule W32 (running sums in the chunk, the
-        // scan across lanes): one pass gives both.
+        // scan across lanes): one pass gives both.  Every value here is a
+        // non-negative binary32, so the error of a sum is formed by Fast2Sum
+        // on (max, min) -- exact when the first operand is the larger, and
+        // the error of a rounded sum is unique, so the same bits as TwoSum's
+        // with one operation fewer.
         float cs = af[0], cerr = 0.0f;
         run32[0] = cs;
 #pragma unroll
         for (int q = 1; q < MAXCH; ++q) {
           if (q >= ch) break;
           const float x = af[q];
-          const float tt = __fadd_rn(cs, x);
-          const float bp = __fsub_rn(tt, cs);
-          const float d = __fadd_rn(__fsub_rn(cs, __fsub_rn(tt, bp)), __fsub_rn(x, bp));
+          const float hi = fmaxf(cs, x), lo = fminf(cs, x);
+          const float tt = __fadd_rn(hi, lo);
+          const float d = __fsub_rn(lo, __fsub_rn(tt, hi));
           cerr = __fadd_rn(cerr, d);
           cs = tt;
           run32[q] = tt;
@@ -315,9 +319,9 @@ __device__ __forceinline__ WarpTraj warp_trajectory(const WarpNet& net, int32_t*
           const float us = __shfl_up_sync(kFullMask, cs, off);
           const float ue = __shfl_up_sync(kFullMask, cerr, off);
           if (lane >= off) {
-            const float tt = __fadd_rn(cs, us);
-            const float bp = __fsub_rn(tt, cs);
-            const float d = __fadd_rn(__fsub_rn(cs, __fsub_rn(tt, bp)), __fsub_rn(us, bp));
+            const float hi = fmaxf(cs, us), lo = fminf(cs, us);
+            const float tt = __fadd_rn(hi, lo);
+            const float d = __fsub_rn(lo, __fsub_rn(tt, hi));
             cerr = __fadd_rn(__fadd_rn(cerr, ue), d);
             cs = tt;
           }
